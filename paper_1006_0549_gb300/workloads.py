@@ -1,0 +1,377 @@
+"""Seeded synthetic inputs for the particle time step: meshes, node fields, particle states.
+
+This module generates *inputs* only. It holds none of the method's arithmetic (no SDE, no
+barycentric location, no statistics), so the CUDA path and the CPU oracle can both consume
+what it produces without sharing any of the method's code.
+
+Workloads (the paper's two testcases, Section "Two testcases"):
+  * channel: fully developed 2D channel, x periodic with period L = fl32(2*pi), walls at
+    y = 0 and y = 2 (half-height 1), Re_tau = 180 (nu = 1/180, u_tau = h = 1); unstructured
+    triangles refined toward both walls (tanh stretching), interior nodes jittered, each cell
+    split along a seeded random diagonal.
+  * cavity: lid-driven unit square, walls on all sides, lid (y = 1) moving with U_w = (1, 0, 0),
+    Re = 1e4 (nu = 1e-4); cosine clustering toward all four walls, jittered interior.
+
+All node coordinates are FP32 values (stored as float64 that are exactly FP32), because the
+particle state is FP32 and exact point location works on those exact values.
+
+Edge tags (per element, edge k runs from vertex k to vertex (k+1) % 3):
+  0 interior, 1 wall (U_w = 0), 2 moving wall (lid), 3 periodic boundary.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+EDGE_INTERIOR = 0
+EDGE_WALL = 1
+EDGE_MOVING_WALL = 2
+EDGE_PERIODIC = 3
+
+PERIOD_CHANNEL = float(np.float32(2.0 * math.pi))  # 6.2831854820251465
+
+# Node-field layout on the hot path (per node, FP32). Index names follow Eq. 4, 5, 6, 9.
+F_U, F_V, F_W = 0, 1, 2                          # <U_i>
+F_DUDX, F_DUDY, F_DVDX, F_DVDY, F_DWDX, F_DWDY = 3, 4, 5, 6, 7, 8   # d<U_i>/dx_j
+F_LAPU, F_LAPV, F_LAPW = 9, 10, 11               # laplacian of <U_i>
+F_DPDX, F_DPDY = 12, 13                          # d<P>/dx_j / rho
+F_G11, F_G12, F_G21, F_G22, F_G33 = 14, 15, 16, 17, 18   # G_ij (planar)
+F_C0EPS = 19                                     # C_0 * epsilon
+F_OMEGA = 20                                     # <omega>
+F_SOMEGA = 21                                    # S_omega, Eq. 6
+F_PHI0 = 22                                      # <phi_alpha>, alpha = 0..ns-1
+
+
+def n_fields(ns: int) -> int:
+    """Number of meaningful node fields for ns scalars."""
+    return 22 + ns
+
+
+def n_fields_padded(ns: int) -> int:
+    """Row stride of the node-field table (multiple of 4 floats = 16 bytes)."""
+    return (n_fields(ns) + 3) // 4 * 4
+
+
+@dataclasses.dataclass
+class Mesh:
+    """A 2D triangle mesh in the form the library and the oracle both accept."""
+    node_xy: np.ndarray      # (N, 2) float64, every value exactly representable in FP32
+    tri: np.ndarray          # (E, 3) int32, counter-clockwise
+    edge_tag: np.ndarray     # (E, 3) int32
+    period_x: float          # 0.0 when not periodic
+    box: tuple               # (x0, x1, y0, y1) domain bounds (FP32 values)
+    kind: str
+    nx: int
+    ny: int
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.node_xy.shape[0])
+
+    @property
+    def n_tri(self) -> int:
+        return int(self.tri.shape[0])
+
+
+def _f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def _triangulate(X: np.ndarray, Y: np.ndarray, rng: np.random.Generator):
+    """Split each cell of an (nx+1) x (ny+1) node grid into two CCW triangles.
+
+    Node (i, j) has index i*(ny+1) + j; element (i, j, d) has index 2*(i*ny + j) + d, so
+    elements of one column are contiguous and neighbours are close in index.
+    """
+    nx, ny = X.shape[0] - 1, X.shape[1] - 1
+    nid = lambda i, j: i * (ny + 1) + j
+    diag = rng.integers(0, 2, size=(nx, ny))
+    tri = np.empty((2 * nx * ny, 3), dtype=np.int64)
+    for i in range(nx):
+        for j in range(ny):
+            a, b, c, d = nid(i, j), nid(i + 1, j), nid(i + 1, j + 1), nid(i, j + 1)
+            e = 2 * (i * ny + j)
+            if diag[i, j] == 0:      # diagonal a-c
+                tri[e] = (a, b, c)
+                tri[e + 1] = (a, c, d)
+            else:                     # diagonal b-d
+                tri[e] = (a, b, d)
+                tri[e + 1] = (b, c, d)
+    xy = np.stack([X.reshape(-1), Y.reshape(-1)], axis=1)
+    # orientation check (CCW, strictly positive area)
+    p0, p1, p2 = xy[tri[:, 0]], xy[tri[:, 1]], xy[tri[:, 2]]
+    area2 = (p1[:, 0] - p0[:, 0]) * (p2[:, 1] - p0[:, 1]) - (p1[:, 1] - p0[:, 1]) * (p2[:, 0] - p0[:, 0])
+    if not np.all(area2 > 0):
+        raise ValueError("mesh generator produced a non-CCW or degenerate triangle")
+    return xy, tri.astype(np.int32)
+
+
+def _edge_tags(xy, tri, box, periodic_x: bool, lid: bool):
+    x0, x1, y0, y1 = box
+    E = tri.shape[0]
+    tags = np.zeros((E, 3), dtype=np.int32)
+    for k in range(3):
+        a = xy[tri[:, k]]
+        b = xy[tri[:, (k + 1) % 3]]
+        bottom = (a[:, 1] == y0) & (b[:, 1] == y0)
+        top = (a[:, 1] == y1) & (b[:, 1] == y1)
+        left = (a[:, 0] == x0) & (b[:, 0] == x0)
+        right = (a[:, 0] == x1) & (b[:, 0] == x1)
+        tags[bottom, k] = EDGE_WALL
+        tags[top, k] = EDGE_MOVING_WALL if lid else EDGE_WALL
+        if periodic_x:
+            tags[left | right, k] = EDGE_PERIODIC
+        else:
+            tags[left | right, k] = EDGE_WALL
+    return tags
+
+
+def channel_mesh(nx: int, ny: int, seed: int, gamma: float = 2.0, jitter: float = 0.2) -> Mesh:
+    """Wall-refined channel [0, L) x [0, 2], L = fl32(2 pi), x periodic.
+
+    nx*ny cells, E = 2*nx*ny triangles. Rows are tanh-clustered toward both walls; interior
+    nodes are moved by up to +-jitter of the local spacing. The two periodic columns
+    (x = 0 and x = L) carry identical y values so their edges pair exactly.
+    """
+    rng = np.random.default_rng(seed)
+    L = PERIOD_CHANNEL
+    s = np.linspace(-1.0, 1.0, ny + 1)
+    yrow = 1.0 + np.tanh(gamma * s) / np.tanh(gamma)
+    yrow[0], yrow[-1] = 0.0, 2.0
+    xcol = np.linspace(0.0, L, nx + 1)
+    X = np.repeat(xcol[:, None], ny + 1, axis=1).astype(np.float64)
+    Y = np.repeat(yrow[None, :], nx + 1, axis=0).astype(np.float64)
+    dx = L / nx
+    dy = np.diff(yrow)
+    dyloc = np.minimum(np.r_[dy[0], dy], np.r_[dy, dy[-1]])  # local row spacing
+    jx = rng.uniform(-jitter, jitter, size=X.shape) * dx
+    jy = rng.uniform(-jitter, jitter, size=Y.shape) * dyloc[None, :]
+    jx[0, :] = 0.0
+    jx[-1, :] = 0.0
+    jy[:, 0] = 0.0
+    jy[:, -1] = 0.0
+    jy[-1, :] = jy[0, :]          # periodic pair columns share y
+    X = X + jx
+    Y = Y + jy
+    X[-1, :] = L
+    X, Y = _f32(X), _f32(Y)
+    xy, tri = _triangulate(X, Y, rng)
+    box = (0.0, L, 0.0, 2.0)
+    tags = _edge_tags(xy, tri, box, periodic_x=True, lid=False)
+    return Mesh(xy, tri, tags, L, box, "channel", nx, ny)
+
+
+def cavity_mesh(nx: int, ny: int, seed: int, jitter: float = 0.2) -> Mesh:
+    """Lid-driven unit cavity [0, 1] x [0, 1]; cosine clustering toward all walls; lid on top."""
+    rng = np.random.default_rng(seed)
+    xs = 0.5 * (1.0 - np.cos(np.pi * np.arange(nx + 1) / nx))
+    ys = 0.5 * (1.0 - np.cos(np.pi * np.arange(ny + 1) / ny))
+    xs[0], xs[-1], ys[0], ys[-1] = 0.0, 1.0, 0.0, 1.0
+    X = np.repeat(xs[:, None], ny + 1, axis=1).astype(np.float64)
+    Y = np.repeat(ys[None, :], nx + 1, axis=0).astype(np.float64)
+    dxs, dys = np.diff(xs), np.diff(ys)
+    dxl = np.minimum(np.r_[dxs[0], dxs], np.r_[dxs, dxs[-1]])
+    dyl = np.minimum(np.r_[dys[0], dys], np.r_[dys, dys[-1]])
+    jx = rng.uniform(-jitter, jitter, size=X.shape) * dxl[:, None]
+    jy = rng.uniform(-jitter, jitter, size=Y.shape) * dyl[None, :]
+    jx[0, :] = jx[-1, :] = 0.0
+    jy[:, 0] = jy[:, -1] = 0.0
+    jx[:, 0] = jx[:, -1] = 0.0     # keep boundary rows straight
+    jy[0, :] = jy[-1, :] = 0.0
+    X, Y = _f32(X + jx), _f32(Y + jy)
+    xy, tri = _triangulate(X, Y, rng)
+    box = (0.0, 1.0, 0.0, 1.0)
+    tags = _edge_tags(xy, tri, box, periodic_x=False, lid=True)
+    return Mesh(xy, tri, tags, 0.0, box, "cavity", nx, ny)
+
+
+# --------------------------------------------------------------------------------------
+# Synthetic node fields. They have the structure of the channel / cavity fields (log-law
+# mean profile, wall-damped gradients, negative-definite G_ij, positive C_0 eps and <omega>)
+# but are not a solution of anything; they are inputs for parity and throughput runs.
+# --------------------------------------------------------------------------------------
+
+def _loglaw(yw, re_tau=180.0):
+    yp = re_tau * yw
+    return np.where(yp < 11.0, yp, np.log(np.maximum(yp, 1e-30)) / 0.41 + 5.2)
+
+
+def synthetic_node_fields(mesh: Mesh, ns: int, seed: int, noise: float = 0.05) -> np.ndarray:
+    """(N, n_fields_padded(ns)) float32 node fields for parity / throughput runs."""
+    rng = np.random.default_rng(seed)
+    N = mesh.n_nodes
+    nfp = n_fields_padded(ns)
+    F = np.zeros((N, nfp), dtype=np.float64)
+    x, y = mesh.node_xy[:, 0], mesh.node_xy[:, 1]
+    if mesh.kind == "channel":
+        yw = np.minimum(y, 2.0 - y)
+        U = _loglaw(yw)
+        F[:, F_U] = U
+        sgn = np.where(y < 1.0, 1.0, -1.0)
+        F[:, F_DUDY] = sgn * np.where(180 * yw < 11.0, 180.0, 1.0 / (0.41 * np.maximum(yw, 1e-3)))
+        F[:, F_LAPU] = -sgn * 0.0 + np.where(180 * yw < 11.0, 0.0, -1.0 / (0.41 * np.maximum(yw, 1e-2) ** 2)) * 1e-2
+        F[:, F_DPDX] = -1.0                       # -d<P>/dx / rho = +1 drives the flow
+        om = 1.0 / (0.3 * 0.41 * np.maximum(yw, 10.0 / 180.0))
+        k = 1.0 + 3.0 * np.exp(-((180 * yw - 15.0) / 30.0) ** 2)
+    else:
+        F[:, F_U] = (y ** 3) * (1.0 - 0.5 * np.cos(2 * np.pi * x))
+        F[:, F_V] = -0.2 * np.sin(np.pi * x) * np.sin(np.pi * y)
+        F[:, F_DUDX] = np.pi * (y ** 3) * np.sin(2 * np.pi * x)
+        F[:, F_DUDY] = 3 * y ** 2 * (1.0 - 0.5 * np.cos(2 * np.pi * x))
+        F[:, F_DVDX] = -0.2 * np.pi * np.cos(np.pi * x) * np.sin(np.pi * y)
+        F[:, F_DVDY] = -0.2 * np.pi * np.sin(np.pi * x) * np.cos(np.pi * y)
+        F[:, F_LAPU] = 6 * y * (1.0 - 0.5 * np.cos(2 * np.pi * x)) + 2 * np.pi ** 2 * y ** 3 * np.cos(2 * np.pi * x)
+        F[:, F_DPDX] = 0.05 * np.sin(np.pi * x)
+        F[:, F_DPDY] = 0.05 * np.cos(np.pi * y)
+        om = 1.0 + 2.0 * np.exp(-10 * np.minimum.reduce([x, 1 - x, y, 1 - y]))
+        k = 0.01 * (1.0 + y)
+    a = 0.5 + 0.75 * 2.1
+    F[:, F_G11] = -a * om * (1.0 + noise * rng.standard_normal(N))
+    F[:, F_G22] = -a * om * (1.0 + noise * rng.standard_normal(N))
+    F[:, F_G33] = -a * om * (1.0 + noise * rng.standard_normal(N))
+    F[:, F_G12] = 0.1 * om * noise * rng.standard_normal(N)
+    F[:, F_G21] = 0.1 * om * noise * rng.standard_normal(N)
+    F[:, F_C0EPS] = 2.1 * k * om
+    F[:, F_OMEGA] = om
+    F[:, F_SOMEGA] = 0.73 - 0.5 * np.clip(0.5 + 0.2 * rng.standard_normal(N), 0.0, 1.5)
+    for a_ in range(ns):
+        F[:, F_PHI0 + a_] = np.clip(0.1 + 0.05 * rng.standard_normal(N), 0.0, 1.0)
+    # small smooth-ish noise on gradients so that every term of Eq. 4 is exercised
+    for f in (F_DVDX, F_DVDY, F_DWDX, F_DWDY, F_LAPV, F_LAPW, F_V, F_W):
+        F[:, f] += noise * rng.standard_normal(N)
+    if mesh.period_x > 0.0:
+        # periodic duplicate nodes (x = L) carry the same values as their x = 0 partners
+        L = mesh.period_x
+        right = np.nonzero(mesh.node_xy[:, 0] == L)[0]
+        left = np.nonzero(mesh.node_xy[:, 0] == 0.0)[0]
+        ly = {float(mesh.node_xy[i, 1]): i for i in left}
+        for i in right:
+            F[i] = F[ly[float(mesh.node_xy[i, 1])]]
+    return F.astype(np.float32)
+
+
+def node_init_fields(mesh: Mesh, sigma: float = 1.0, re_tau: float = 180.0) -> np.ndarray:
+    """(N, 8) float32 initial-condition fields per node: <U>, <V>, <W>, sigma_u, <omega>, pad.
+
+    Channel: log-law mean (U = y+ for y+ < 11, else ln(y+)/0.41 + 5.2, y+ = Re_tau * y_wall),
+    sigma = 1, <omega> = 1/(0.3 * 0.41 * max(y_wall, 10/Re_tau)).
+    Cavity: U = 0, sigma = 0.1, <omega> = 1.
+    """
+    N = mesh.n_nodes
+    out = np.zeros((N, 8), dtype=np.float64)
+    y = mesh.node_xy[:, 1]
+    if mesh.kind == "channel":
+        yw = np.minimum(y, 2.0 - y)
+        out[:, 0] = _loglaw(yw, re_tau)
+        out[:, 3] = sigma
+        out[:, 4] = 1.0 / (0.3 * 0.41 * np.maximum(yw, 10.0 / re_tau))
+    else:
+        out[:, 3] = 0.1
+        out[:, 4] = 1.0
+    return out.astype(np.float32)
+
+
+@dataclasses.dataclass
+class State:
+    """SoA particle state (host copy). Positions and all fields are FP32."""
+    x: np.ndarray
+    y: np.ndarray
+    u: np.ndarray
+    v: np.ndarray
+    w: np.ndarray
+    omega: np.ndarray
+    psi: np.ndarray          # (ns, P)
+    elem: np.ndarray         # int32
+    pid: np.ndarray          # uint32
+
+    @property
+    def n(self) -> int:
+        return int(self.x.shape[0])
+
+    def copy(self) -> "State":
+        return State(*(np.array(getattr(self, f.name), copy=True) for f in dataclasses.fields(self)))
+
+
+def synthetic_state(mesh: Mesh, n_per_elem: int, ns: int, seed: int, margin: float = 0.01,
+                    speed: float = 1.0) -> State:
+    """Particles strictly inside their elements (every barycentric >= margin), sorted by element.
+
+    Velocities are N(interpolation-free guess, 1): U from a log-law in the channel, small in the
+    cavity; omega ~ Gamma(4, 1/4) * <omega> guess; psi ~ U[0, 1]. Strict interiority makes the
+    owning element known by construction, so no point location is needed to build the input.
+    """
+    rng = np.random.default_rng(seed)
+    E = mesh.n_tri
+    P = E * n_per_elem
+    elem = np.repeat(np.arange(E, dtype=np.int32), n_per_elem)
+    r = rng.uniform(margin, 1.0 - 2 * margin, size=(P, 3))
+    r = r / r.sum(axis=1, keepdims=True)
+    r = np.clip(r, margin, None)
+    r = r / r.sum(axis=1, keepdims=True)
+    v = mesh.node_xy[mesh.tri[elem]]          # (P, 3, 2)
+    xy = np.einsum("pk,pkd->pd", r, v)
+    x = xy[:, 0].astype(np.float32)
+    y = xy[:, 1].astype(np.float32)
+    if mesh.kind == "channel":
+        yw = np.minimum(y, 2.0 - y).astype(np.float64)
+        U0 = _loglaw(yw)
+        om0 = 1.0 / (0.3 * 0.41 * np.maximum(yw, 10.0 / 180.0))
+    else:
+        U0 = np.zeros(P)
+        om0 = np.ones(P)
+    u = (speed * U0 + rng.standard_normal(P)).astype(np.float32)
+    vv = rng.standard_normal(P).astype(np.float32)
+    w = rng.standard_normal(P).astype(np.float32)
+    omega = (om0 * rng.gamma(4.0, 0.25, size=P)).astype(np.float32)
+    psi = rng.uniform(0.0, 1.0, size=(ns, P)).astype(np.float32)
+    pid = np.arange(P, dtype=np.uint32)
+    return State(x, y, u, vv, w, omega, psi, elem, pid)
+
+
+# --------------------------------------------------------------------------------------
+# Named workloads (sizes of the channel and cavity configurations).
+# --------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    mesh: Mesh
+    n_per_elem: int
+    ns: int
+    nu: float
+    dt: float
+    seed: int
+    lid_u: float
+    sources: list            # [(x, y, r, alpha), ...]
+
+    @property
+    def n_particles(self) -> int:
+        return self.mesh.n_tri * self.n_per_elem
+
+
+def channel_small(seed: int = 1006054901) -> Workload:
+    """~1,000-triangle channel, 50 particles per element (~50k particles), one scalar."""
+    m = channel_mesh(25, 20, seed)
+    return Workload("channel-1k-50k", m, 50, 1, 1.0 / 180.0, 1e-3, seed, 0.0, [(0.25, 0.67, 0.02, 0)])
+
+
+def channel_25m(seed: int = 1006054902) -> Workload:
+    """50,000-triangle wall-refined channel, 500 particles per element (25M particles), one scalar."""
+    m = channel_mesh(250, 100, seed)
+    return Workload("channel-50k-25M", m, 500, 1, 1.0 / 180.0, 1e-3, seed, 0.0, [(0.25, 0.67, 0.02, 0)])
+
+
+def cavity_20m(seed: int = 1006054903) -> Workload:
+    """~200,000-triangle lid-driven cavity, 100 particles per element (~20M), four scalars."""
+    m = cavity_mesh(316, 316, seed)
+    src = [(0.25, 0.25, 0.01, 0), (0.75, 0.25, 0.01, 1), (0.5, 0.5, 0.01, 2), (0.5, 0.8, 0.01, 3)]
+    return Workload("cavity-200k-20M", m, 100, 4, 1e-4, 1e-3, seed, 1.0, src)
+
+
+def cavity_small(seed: int = 1006054903) -> Workload:
+    """Small cavity (2,048 triangles, 50 per element) with the cavity's physics, for parity."""
+    m = cavity_mesh(32, 32, seed)
+    src = [(0.25, 0.25, 0.02, 0), (0.75, 0.25, 0.02, 1), (0.5, 0.5, 0.02, 2), (0.5, 0.8, 0.02, 3)]
+    return Workload("cavity-2k-100k", m, 50, 4, 1e-4, 1e-3, seed, 1.0, src)
