@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Throughput of the particle time step on one GB300 (or N independent replicas).
+
+Workload: the wall-refined channel with 50,000 triangles and 500 particles per element (25M
+particles, three velocity components, frequency and one scalar released from a line source at
+y = 0.67; Re_tau = 180, dt = 1e-3), initialised on the device by lpdf_particles_init, with
+synthetic node fields of the channel's structure held fixed (the gridpoint solves are not part
+of the timed step). One step = lpdf_pdf_step: Eq. 4/5/9/2 for every particle, wrap and wall
+reflection, exact point location, scalar sources and the moment sums at gridpoints; every
+`sort_every` steps also the element re-bucketing.
+
+Prints one JSON line. `--impl reference` times the FP64 CPU oracle instead (a bounded sample of
+the same workload on the host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-updates/s (SDE+locate+stats) at 25M particles; % HBM roofline"
+UNIT = "particle-updates/s"
+# algorithmic bytes of one particle update (ns = 1): read x, y, u, v, w, omega, psi, elem, pid
+# (36 B) and write x, y, u, v, w, omega, psi, elem (32 B)
+BYTES_PER_UPDATE = 68
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1006_0549_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_1006_0549_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload: str, n_particles: int):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "pdf_step_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    per_particle = float(d["dram_bytes_per_launch"]) / float(d["particles"])
+    return per_particle * n_particles
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(gpu_index).uuid)
+            self.gpu = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        except Exception:
+            pass
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), float(parts[3]) if parts[3] not in ("[N/A]", "N/A") else 0.0,
+                                 parts[5], parts[6], parts[7], parts[8]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [r for r in rows if r[2] > 200.0] or rows
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in load:
+            for nm, v in zip(names, r[3:]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in load),
+                "reasons": sorted(reasons), "samples": len(load)}
+
+
+def build_workload(rank: int, ppe: int):
+    import torch
+    from paper_1006_0549_gb300 import lpdf, workloads as wl
+    wk = wl.channel_25m(seed=1006054902 + 7919 * rank)
+    wk.n_per_elem = ppe
+    mesh = lpdf.Mesh(wk.mesh)
+    params = lpdf.params_for(wk)
+    ctx = lpdf.Context(mesh, params, wk.n_particles)
+    init = torch.from_numpy(wl.node_init_fields(wk.mesh)).cuda()
+    ctx.particles_init(wk.n_per_elem, init, m_erlang=4)
+    fields = torch.from_numpy(wl.synthetic_node_fields(wk.mesh, wk.ns, seed=5)).cuda()
+    ctx.status()
+    return wk, mesh, ctx, fields
+
+
+def run_gpu(args, rank, world, dist):
+    import torch
+    from paper_1006_0549_gb300 import lpdf
+    wk, mesh, ctx, fields = build_workload(rank, args.ppe)
+    P = ctx.n
+    stream = torch.cuda.current_stream()
+    step = 0
+    for _ in range(args.warmup):
+        ctx.pdf_step(fields, step)
+        step += 1
+    torch.cuda.synchronize()
+    ctx.status()
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(K):
+            ev[k][0].record(stream)
+            ctx.pdf_step(fields, step)
+            ev[k][1].record(stream)
+            step += 1
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    total_ms = t0.elapsed_time(t1)
+    per = [a.elapsed_time(b) for a, b in ev]
+    print("per-step ms:", " ".join(f"{x:.3f}" for x in per), file=sys.stderr)
+    rc, status = ctx.status(raise_on_error=False)
+    if rc != lpdf.LPDF_OK:
+        raise RuntimeError(f"step status {rc}: {status}")
+    hops = status[3] / (P * K)
+    # e2e: the same step through the C-ABI with host buffers (fields in, statistics out)
+    nq = 11 + 2 * wk.ns
+    h_fields = torch.empty_like(fields, device="cpu").pin_memory()
+    h_fields.copy_(fields.cpu())
+    d_fields = torch.empty_like(fields)
+    d_stats = torch.empty((mesh.n_nodes, nq), dtype=torch.float64, device="cuda")
+    h_stats = torch.empty((mesh.n_nodes, nq), dtype=torch.float64).pin_memory()
+    Ke = max(3, min(K, 10))
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(Ke):
+        d_fields.copy_(h_fields, non_blocking=True)
+        ctx.pdf_step(d_fields, step)
+        ctx.grid_statistics(d_stats, raw=False)
+        h_stats.copy_(d_stats, non_blocking=True)
+        torch.cuda.synchronize()
+        step += 1
+    e2e_s = (time.perf_counter() - te) / Ke
+    return dict(P=P, total_ms=total_ms, per=per, clocks=clk.summary(), hops=hops, e2e_s=e2e_s,
+                h2d=int(h_fields.numel() * 4), d2h=int(h_stats.numel() * 8), wk=wk)
+
+
+def cpu_baseline_sample(wk, n_sample: int):
+    """FP64 oracle (single-threaded C) on the first n_sample particles of a fresh initialisation
+    of the same workload: one step plus the gridpoint moments."""
+    import oracle
+    from paper_1006_0549_gb300 import workloads as wl
+    om = oracle.OracleMesh(wk.mesh)
+    p = oracle.make_params(nu=wk.nu, dt=wk.dt, seed=wk.seed, ns=wk.ns, sources=wk.sources, lid_u=wk.lid_u)
+    # initial state of the sample: the oracle's own initialisation of those elements' particles
+    n_el = max(1, n_sample // wk.n_per_elem)
+    sub = wl.Mesh(wk.mesh.node_xy, wk.mesh.tri[:n_el], wk.mesh.edge_tag[:n_el], wk.mesh.period_x, wk.mesh.box,
+                  wk.mesh.kind, wk.mesh.nx, wk.mesh.ny)
+    st = wl.synthetic_state(sub, wk.n_per_elem, wk.ns, seed=3)
+    F = wl.synthetic_node_fields(wk.mesh, wk.ns, seed=5)
+    t = time.perf_counter()
+    res, elem, aux, lost = oracle.pdf_step(om, p, F, st, 0)
+    S, _ = oracle.moments(om, wk.ns, res["x"], res["y"], res["u"], res["v"], res["w"], res["omega"], res["psi"],
+                          elem, with_abs=False)
+    dt = time.perf_counter() - t
+    return st.n, dt
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=4_000_000)
+    ap.add_argument("--ppe", type=int, default=500,
+                    help="particles per element (500 = the 25M-particle workload; smaller only for profiling)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        from paper_1006_0549_gb300 import workloads as wl
+        wk = wl.channel_25m()
+        n_s = 200_000
+        times = []
+        for i in range(args.warmup + args.steps):
+            n, dt = cpu_baseline_sample(wk, n_s)
+            if i >= args.warmup:
+                times.append(dt)
+        v = n * len(times) / sum(times)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": "channel-50k-25M", "particles": wk.n_particles, "triangles": wk.mesh.n_tri},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": f"{n} particles of the channel workload per step (one FP64 step + moments)"},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist = tdist
+    from paper_1006_0549_gb300 import _build
+    if rank == 0:
+        _build.build()
+    if dist is not None:
+        dist.barrier()
+    r = run_gpu(args, rank, world, dist)
+    total_ms = r["total_ms"]
+    P = r["P"]
+    if dist is not None:
+        t = torch.tensor([total_ms, r["e2e_s"]], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, e2e_s = float(t[0]), float(t[1])
+        n_all = torch.tensor([P], dtype=torch.float64, device="cuda")
+        dist.all_reduce(n_all)
+        P_all = float(n_all[0])
+    else:
+        e2e_s = r["e2e_s"]
+        P_all = float(P)
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+    K = args.steps
+    ms_step = total_ms / K
+    value = P_all * K / (total_ms * 1e-3)
+    per = r["per"]
+    kernel_ms = statistics.mean(per)
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_UPDATE * P / (kernel_ms * 1e-3) / 1e9
+    traffic = ncu_traffic("channel-50k-25M", P)
+    cpu_n, cpu_dt = cpu_baseline_sample(r["wk"], args.cpu_sample)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "channel-50k-25M" if args.ppe == 500 else f"channel-50k-{P}", "particles_per_gpu": P, "triangles": r["wk"].mesh.n_tri,
+                   "particles_per_element": r["wk"].n_per_elem, "scalars": r["wk"].ns,
+                   "l2": "inputs larger than L2 (state 0.9 GB per step)", "node_fields": "synthetic, held fixed",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "mean_walk_hops": r["hops"]},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth",
+                     "kernel": "pdf_step_kernel", "bytes_per_update": BYTES_PER_UPDATE,
+                     "kernel_ms": kernel_ms},
+        "cpu_baseline": {"value": cpu_n / cpu_dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{cpu_n} particles of the same workload, one FP64 step + gridpoint moments"},
+        "clocks": r["clocks"],
+        "e2e": {"value": P_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"],
+                "note": "per step: node fields host->device, pdf_step, grid_statistics, statistics device->host; "
+                        "the particle state stays resident in HBM"},
+        "gpu_launches": K,
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

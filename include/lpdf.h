@@ -1,0 +1,192 @@
+/*
+ * lpdf.h -- C ABI of the GB300 particle time step of the fully Lagrangian joint
+ * velocity-frequency-scalar PDF method (Bakosi, Franzese & Boybeyi, arXiv:1006.0549).
+ *
+ * The method (Section "Governing equations"): a large number of Lagrangian particles carry
+ * position X, velocity U, turbulent frequency omega and scalar compositions psi_alpha, governed
+ * by Eq. 2 (position), Eq. 4 (generalized Langevin model), Eq. 5/6 (frequency) and Eq. 9
+ * (micromixing, used here in its IEM form <phi|V> -> <phi>); they are advanced by forward Euler,
+ * Eulerian statistics are evaluated at particle positions, and an unstructured grid is used to
+ * extract statistics, to solve for Eulerian quantities, and to track particles (Introduction,
+ * items i-iii).
+ *
+ * Conventions for every call:
+ *   - Return value: LPDF_OK (0) or a negative LPDF_ERR_* code; lpdf_last_error() gives a
+ *     message for the calling thread's last error. Nothing is thrown across the ABI.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA device memory of the
+ *     current device (for example torch CUDA tensors). The caller owns every pointer it passes;
+ *     the library owns the objects it creates (lpdf_mesh, lpdf_ctx) and their device memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). Calls marked
+ *     "async" only enqueue work on that stream; calls marked "sync" return after the work ends.
+ *   - Floating-point particle state is FP32 structure-of-arrays; gridpoint moment sums are FP64.
+ */
+#ifndef LPDF_H
+#define LPDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LPDF_OK 0
+#define LPDF_ERR_ARG (-1)           /* null pointer, bad size, bad enum */
+#define LPDF_ERR_MESH (-2)          /* non-CCW or degenerate element, non-manifold or unpaired edge */
+#define LPDF_ERR_LOST_PARTICLE (-3) /* the neighbour walk hit its hop cap or a wall (see lpdf_status) */
+#define LPDF_ERR_NONFINITE (-4)     /* NaN or Inf in the particle state */
+#define LPDF_ERR_CG_NOCONV (-5)     /* a conjugate-gradient solve did not converge */
+#define LPDF_ERR_CUDA (-6)          /* a CUDA runtime call failed */
+#define LPDF_ERR_OVERFLOW (-7)      /* fixed-point moment accumulator range exceeded */
+#define LPDF_ERR_UNSUPPORTED (-8)   /* e.g. more scalars than compiled for */
+
+#define LPDF_MAX_SOURCES 8
+#define LPDF_MAX_SCALARS 4
+
+/* Edge tags (edge k of an element runs from its vertex k to vertex (k+1) % 3). */
+#define LPDF_EDGE_INTERIOR 0
+#define LPDF_EDGE_WALL 1        /* no-slip wall, U_w = 0 */
+#define LPDF_EDGE_MOVING_WALL 2 /* the lid: U_w = (lid_u, 0, 0) */
+#define LPDF_EDGE_PERIODIC 3
+
+/* Node-field columns of the table that pdf_step reads (per node, FP32; row stride nfp,
+ * nfp = 4 * ceil((22 + ns) / 4)). Names follow Eq. 4, 5, 6 and 9. */
+#define LPDF_F_U 0      /* <U>, <V>, <W>: columns 0..2 */
+#define LPDF_F_DUDX 3   /* d<U>/dx, d<U>/dy, d<V>/dx, d<V>/dy, d<W>/dx, d<W>/dy: 3..8 */
+#define LPDF_F_LAPU 9   /* laplacian of <U>, <V>, <W>: 9..11 */
+#define LPDF_F_DPDX 12  /* d<P>/dx / rho, d<P>/dy / rho: 12..13 */
+#define LPDF_F_G11 14   /* G11, G12, G21, G22, G33: 14..18 (planar flow, G13 = G23 = G31 = G32 = 0) */
+#define LPDF_F_C0EPS 19 /* C_0 * epsilon */
+#define LPDF_F_OMEGA 20 /* <omega> */
+#define LPDF_F_SOMEGA 21 /* S_omega of Eq. 6 */
+#define LPDF_F_PHI0 22  /* <phi_alpha>, alpha = 0..ns-1 */
+
+/* Model and run parameters. The paper prints no constants; the defaults that
+ * lpdf_params_default() writes are the literature values of the cited models. */
+typedef struct {
+    double nu;      /* kinematic viscosity */
+    double dt;      /* forward-Euler time step */
+    double C3, C4;  /* Eq. 5 */
+    double Cphi;    /* IEM: 1/t_m = Cphi <omega> / 2 */
+    double C0;      /* Eq. 4 constant (elliptic relaxation and the simplified Langevin model) */
+    double Comega1, Comega2; /* Eq. 6 */
+    double CL, Ceta;         /* elliptic-relaxation length scale L = CL max(k^1.5/eps, Ceta nu^0.75/eps^0.25) */
+    double lid_u;   /* tangential velocity of LPDF_EDGE_MOVING_WALL edges (the top wall) */
+    uint64_t seed;  /* Philox4x32-10 key */
+    int32_t ns;     /* number of scalars, 1..LPDF_MAX_SCALARS */
+    int32_t n_sources;
+    float src_x[LPDF_MAX_SOURCES], src_y[LPDF_MAX_SOURCES], src_r[LPDF_MAX_SOURCES];
+    int32_t src_alpha[LPDF_MAX_SOURCES]; /* scalar index set to 1 inside source disc s */
+} lpdf_params;
+
+typedef struct lpdf_mesh lpdf_mesh;
+typedef struct lpdf_ctx lpdf_ctx;
+
+/* Fills *p with C3 = 5, C4 = 0.25, Cphi = 2, C0 = 2.1, Comega1 = 0.5, Comega2 = 0.73,
+ * CL = 0.134, Ceta = 72, nu = 1/180, dt = 1e-3, ns = 1, no sources, seed = 1, lid_u = 0. */
+void lpdf_params_default(lpdf_params* p);
+
+/* Message of the calling thread's last error ("" if none). Owned by the library. */
+const char* lpdf_last_error(void);
+const char* lpdf_version(void);
+
+/* ---------------------------------------------------------------------------------------
+ * lpdf_mesh_load -- the unstructured triangle mesh (Introduction: the grid extracts
+ * statistics, solves Eulerian fields and tracks particles). sync.
+ *   node_xy  host, 2*n_nodes doubles (x, y); every value must be exactly representable in FP32
+ *   tri      host, 3*n_tri int32 node ids, counter-clockwise
+ *   edge_tag host, 3*n_tri int32 LPDF_EDGE_* (edge k: vertex k -> vertex (k+1)%3)
+ *   period_x > 0: the domain is periodic in x with this period (node columns at x0 and
+ *            x0 + period_x are paired by equal y); 0: walls everywhere.
+ * The domain is the bounding box of the nodes, taken half-open: [x0, x1) x [y0, y1).
+ * Builds element adjacency (periodic edges linked), element geometry, node->element lists and
+ * periodic node pairing, and uploads them to the current device.
+ * Errors: LPDF_ERR_ARG, LPDF_ERR_MESH (orientation, unpaired periodic edge, edge shared by
+ * more than two elements), LPDF_ERR_CUDA.
+ * ------------------------------------------------------------------------------------- */
+int lpdf_mesh_load(const double* node_xy, int32_t n_nodes, const int32_t* tri, int32_t n_tri,
+                   const int32_t* edge_tag, double period_x, lpdf_mesh** out);
+void lpdf_mesh_free(lpdf_mesh* mesh);
+/* n_nodes, n_tri, box = {x0, x1, y0, y1} (host outputs; any may be NULL). */
+int lpdf_mesh_info(const lpdf_mesh* mesh, int32_t* n_nodes, int32_t* n_tri, double* box);
+/* host out, 3*n_tri: neighbour across each edge, -1 on walls. sync. */
+int lpdf_mesh_neighbors(const lpdf_mesh* mesh, int32_t* out);
+/* host out, n_nodes: the node that holds the statistics of each node (periodic pairing). */
+int lpdf_mesh_masters(const lpdf_mesh* mesh, int32_t* out);
+
+/* ---------------------------------------------------------------------------------------
+ * lpdf_ctx_create -- particle ensemble on one mesh with room for `capacity` particles
+ * (device SoA state x, y, u, v, w, omega, psi[ns], elem, pid, plus the moment accumulators).
+ * params->ns must be in 1..LPDF_MAX_SCALARS. sync. The mesh must outlive the context.
+ * ------------------------------------------------------------------------------------- */
+int lpdf_ctx_create(const lpdf_mesh* mesh, const lpdf_params* params, int64_t capacity, lpdf_ctx** out);
+void lpdf_ctx_free(lpdf_ctx* ctx);
+/* Replaces the parameters (ns must not change). */
+int lpdf_ctx_set_params(lpdf_ctx* ctx, const lpdf_params* params);
+int64_t lpdf_ctx_size(const lpdf_ctx* ctx);
+
+/* ---------------------------------------------------------------------------------------
+ * lpdf_particles_init -- n_per_elem particles per element, pid = e*n_per_elem + j: position
+ * uniform in the element, then located exactly; U = <U>(X) + sigma(X) z; omega Erlang(m_erlang)
+ * with mean <omega>(X) (gamma-distributed frequency, Section "Governing equations"); psi = 0.
+ *   node_init device, n_nodes x 8 FP32: <U>, <V>, <W>, sigma, <omega>, 3 unused.
+ * Random numbers: Philox4x32-10 counter (pid, 0, 0, 1<<16 | block), key = seed. async.
+ * Errors: LPDF_ERR_ARG (capacity too small, m_erlang outside 1..6).
+ * ------------------------------------------------------------------------------------- */
+int lpdf_particles_init(lpdf_ctx* ctx, int32_t n_per_elem, const float* node_init, int32_t m_erlang,
+                        void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * lpdf_set_state / lpdf_get_state -- copy the SoA state in or out. `on_device` = 1: the
+ * pointers are device memory, 0: host memory. psi is ns rows of n values. set_state sets the
+ * ensemble size to n (n <= capacity). async (a host copy is synchronous w.r.t. the host only
+ * when the host memory is pageable).
+ * ------------------------------------------------------------------------------------- */
+int lpdf_set_state(lpdf_ctx* ctx, int64_t n, const float* x, const float* y, const float* u, const float* v,
+                   const float* w, const float* omega, const float* psi, const int32_t* elem,
+                   const uint32_t* pid, int on_device, void* stream);
+int lpdf_get_state(const lpdf_ctx* ctx, float* x, float* y, float* u, float* v, float* w, float* omega,
+                   float* psi, int32_t* elem, uint32_t* pid, int on_device, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * lpdf_pdf_step -- one forward-Euler step of every particle, then the gridpoint moment sums
+ * of the new state. async.
+ *   node_fields device, n_nodes x nfp FP32 (columns LPDF_F_*), evaluated at each particle by
+ *               the linear shape functions of its element.
+ *   step        the step index (part of the Philox counter: (pid, step, 0<<16 | block)).
+ * Per particle, with the state at t_n: Eq. 4 for U, Eq. 5 for omega (sqrt(max(omega,0)),
+ * then omega <- |omega|), Eq. 9 in IEM form for psi, Eq. 2 for X with the same dW_1, dW_2;
+ * periodic wrap; wall reflection (X mirrored, U <- 2 U_w - U); exact point location by a
+ * barycentric neighbour walk (hop cap 64); psi_alpha <- 1 inside scalar source discs; then
+ * S_k(n) += lambda_n(X') q_k, q = 1, u, v, w, uu, uv, uw, vv, vw, ww, omega, psi_a, psi_a^2.
+ * Errors are recorded in the context's device status word (read with lpdf_status); the
+ * call itself only reports argument and launch errors.
+ * ------------------------------------------------------------------------------------- */
+int lpdf_pdf_step(lpdf_ctx* ctx, const float* node_fields, uint64_t step, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * lpdf_status -- sync. Reads and clears the device status: out[0] error bits (1 lost
+ * particle, 2 non-finite state, 4 fixed-point overflow), out[1] number of lost particles,
+ * out[2] pid of one lost particle (-1 if none), out[3] total walk hops of the last step.
+ * Returns LPDF_ERR_LOST_PARTICLE / LPDF_ERR_NONFINITE / LPDF_ERR_OVERFLOW when the
+ * corresponding bit was set, else LPDF_OK.
+ * ------------------------------------------------------------------------------------- */
+int lpdf_status(lpdf_ctx* ctx, int64_t* out, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * lpdf_grid_statistics -- gridpoint statistics of the state left by the last pdf_step
+ * (statistics estimated at the gridpoints of the mesh, Section "Governing equations"). async.
+ *   out device, n_nodes x (11 + 2 ns) FP64.
+ *   raw = 1: the sums S_k(n) = sum_p lambda_n(X_p) q_k(p).
+ *   raw = 0: S_0, <u>, <v>, <w>, <u'u'>, <u'v'>, <u'w'>, <v'v'>, <v'w'>, <w'w'>, <omega>,
+ *            <psi_a> (ns), <psi_a'^2> (ns); mean = S_q/S_0, central moment = S_qq/S_0 - mean^2;
+ *            a node with S_0 = 0 gets zeros.
+ * Periodic partner nodes hold identical values.
+ * ------------------------------------------------------------------------------------- */
+int lpdf_grid_statistics(lpdf_ctx* ctx, double* out, int raw, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LPDF_H */

@@ -1,0 +1,459 @@
+// Host side of liblpdf: the C ABI declared in include/lpdf.h (mesh building, context and
+// device memory management, argument checking, launches).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <unordered_map>
+#include <utility>
+#include <vector>
+
+#include "lpdf_internal.h"
+
+using namespace lpdf;
+
+struct lpdf_mesh {
+    DevMesh d;
+    std::vector<int32_t> nbr;      // host copy, 3 per element
+    std::vector<int32_t> master;   // host copy
+    double box[4];
+    int device;
+};
+
+struct lpdf_ctx {
+    const lpdf_mesh* mesh;
+    lpdf_params params;
+    DevState s;
+    unsigned long long* node_acc = nullptr;   // n_nodes x nq fixed-point sums
+    unsigned long long* status = nullptr;     // 4 words
+    int ns;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                     \
+    do {                                                                                   \
+        cudaError_t e_ = (expr);                                                           \
+        if (e_ != cudaSuccess) return fail(LPDF_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t n)
+{
+    return cudaMalloc((void**)p, sizeof(T) * (n ? n : 1));
+}
+
+bool is_f32(double v) { return (double)(float)v == v; }
+
+void free_mesh_device(DevMesh& d)
+{
+    cudaFree(d.ex); cudaFree(d.ey); cudaFree(d.en); cudaFree(d.ev); cudaFree(d.em); cudaFree(d.master);
+    d = DevMesh();
+}
+
+StepParams make_step_params(const lpdf_params& p, const lpdf_mesh* m, uint64_t step)
+{
+    StepParams s{};
+    s.dt = (float)p.dt;
+    s.sdt = (float)std::sqrt(p.dt);
+    s.s2nu = (float)std::sqrt(2.0 * p.nu);
+    s.nu2 = (float)(2.0 * p.nu);
+    s.C3 = (float)p.C3;
+    s.C4 = (float)p.C4;
+    s.half_cphi = (float)(0.5 * p.Cphi);
+    s.lid_u = (float)p.lid_u;
+    s.key0 = (uint32_t)p.seed;
+    s.key1 = (uint32_t)(p.seed >> 32);
+    s.step_lo = (uint32_t)step;
+    s.step_hi = (uint32_t)(step >> 32);
+    s.n_src = p.n_sources;
+    for (int i = 0; i < p.n_sources; ++i) {
+        s.src_x[i] = p.src_x[i];
+        s.src_y[i] = p.src_y[i];
+        s.src_r[i] = p.src_r[i];
+        s.src_alpha[i] = p.src_alpha[i];
+    }
+    (void)m;
+    return s;
+}
+
+int check_params(const lpdf_params* p)
+{
+    if (!p) return fail(LPDF_ERR_ARG, "params is NULL");
+    if (p->ns < 1 || p->ns > LPDF_MAX_SCALARS)
+        return fail(LPDF_ERR_UNSUPPORTED, "ns = %d outside 1..%d", p->ns, LPDF_MAX_SCALARS);
+    if (p->n_sources < 0 || p->n_sources > LPDF_MAX_SOURCES)
+        return fail(LPDF_ERR_ARG, "n_sources = %d outside 0..%d", p->n_sources, LPDF_MAX_SOURCES);
+    for (int i = 0; i < p->n_sources; ++i)
+        if (p->src_alpha[i] < 0 || p->src_alpha[i] >= p->ns)
+            return fail(LPDF_ERR_ARG, "source %d sets scalar %d, but ns = %d", i, p->src_alpha[i], p->ns);
+    if (!(p->dt > 0.0) || !(p->nu >= 0.0)) return fail(LPDF_ERR_ARG, "need dt > 0 and nu >= 0");
+    return LPDF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lpdf_params_default(lpdf_params* p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->nu = 1.0 / 180.0;
+    p->dt = 1e-3;
+    p->C3 = 5.0;
+    p->C4 = 0.25;
+    p->Cphi = 2.0;
+    p->C0 = 2.1;
+    p->Comega1 = 0.5;
+    p->Comega2 = 0.73;
+    p->CL = 0.134;
+    p->Ceta = 72.0;
+    p->lid_u = 0.0;
+    p->seed = 1;
+    p->ns = 1;
+    p->n_sources = 0;
+}
+
+const char* lpdf_last_error(void) { return g_err.c_str(); }
+const char* lpdf_version(void) { return "lpdf 0.1 (sm_103a)"; }
+
+int lpdf_mesh_load(const double* node_xy, int32_t n_nodes, const int32_t* tri, int32_t n_tri,
+                   const int32_t* edge_tag, double period_x, lpdf_mesh** out)
+{
+    if (!node_xy || !tri || !edge_tag || !out) return fail(LPDF_ERR_ARG, "mesh_load: NULL argument");
+    if (n_nodes < 3 || n_tri < 1) return fail(LPDF_ERR_ARG, "mesh_load: n_nodes = %d, n_tri = %d", n_nodes, n_tri);
+    *out = nullptr;
+    double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+    for (int i = 0; i < n_nodes; ++i) {
+        const double x = node_xy[2 * i], y = node_xy[2 * i + 1];
+        if (!is_f32(x) || !is_f32(y)) return fail(LPDF_ERR_ARG, "node %d coordinates are not FP32 values", i);
+        x0 = std::min(x0, x); x1 = std::max(x1, x); y0 = std::min(y0, y); y1 = std::max(y1, y);
+    }
+    const bool periodic = period_x > 0.0;
+    if (periodic && (float)(x1 - x0) != (float)period_x)
+        return fail(LPDF_ERR_MESH, "period %.9g differs from the x extent %.9g", period_x, x1 - x0);
+    std::vector<float> ex(4 * (size_t)n_tri), ey(4 * (size_t)n_tri);
+    std::vector<int32_t> en(4 * (size_t)n_tri, -1), ev(4 * (size_t)n_tri, 0), em(4 * (size_t)n_tri, 0);
+    for (int e = 0; e < n_tri; ++e) {
+        const int* t = tri + 3 * e;
+        for (int k = 0; k < 3; ++k)
+            if (t[k] < 0 || t[k] >= n_nodes) return fail(LPDF_ERR_MESH, "element %d has node id %d", e, t[k]);
+        const double ax = node_xy[2 * t[0]], ay = node_xy[2 * t[0] + 1];
+        const double bx = node_xy[2 * t[1]], by = node_xy[2 * t[1] + 1];
+        const double cx = node_xy[2 * t[2]], cy = node_xy[2 * t[2] + 1];
+        const double A = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
+        if (!(A > 0.0)) return fail(LPDF_ERR_MESH, "element %d is not counter-clockwise (2A = %g)", e, A);
+        ex[4 * e + 0] = (float)ax; ex[4 * e + 1] = (float)bx; ex[4 * e + 2] = (float)cx;
+        ex[4 * e + 3] = (float)((ax + bx + cx) / 3.0);
+        ey[4 * e + 0] = (float)ay; ey[4 * e + 1] = (float)by; ey[4 * e + 2] = (float)cy;
+        ey[4 * e + 3] = (float)(1.0 / A);
+        for (int k = 0; k < 3; ++k) ev[4 * e + k] = t[k];
+        ev[4 * e + 3] = 0;
+        en[4 * e + 3] = 0;   // bit k: edge k is periodic
+    }
+    // interior adjacency by shared (ordered) node pairs
+    std::unordered_map<uint64_t, int64_t> half;   // (a,b) -> e*3+k
+    half.reserve(3 * (size_t)n_tri);
+    for (int e = 0; e < n_tri; ++e)
+        for (int k = 0; k < 3; ++k) {
+            const uint32_t a = (uint32_t)tri[3 * e + k], b = (uint32_t)tri[3 * e + (k + 1) % 3];
+            const uint64_t key = ((uint64_t)a << 32) | b;
+            if (!half.emplace(key, (int64_t)e * 3 + k).second)
+                return fail(LPDF_ERR_MESH, "directed edge %u->%u appears twice", a, b);
+        }
+    std::vector<std::pair<double, int64_t>> left_edges, right_edges;   // keyed by min y
+    for (int e = 0; e < n_tri; ++e)
+        for (int k = 0; k < 3; ++k) {
+            const uint32_t a = (uint32_t)tri[3 * e + k], b = (uint32_t)tri[3 * e + (k + 1) % 3];
+            const int tag = edge_tag[3 * e + k];
+            if (tag < 0 || tag > 3) return fail(LPDF_ERR_MESH, "element %d edge %d: bad tag %d", e, k, tag);
+            auto it = half.find(((uint64_t)b << 32) | a);
+            if (it != half.end()) {
+                if (tag != LPDF_EDGE_INTERIOR)
+                    return fail(LPDF_ERR_MESH, "element %d edge %d is shared but tagged %d", e, k, tag);
+                en[4 * e + k] = (int32_t)(it->second / 3);
+                continue;
+            }
+            if (tag == LPDF_EDGE_INTERIOR)
+                return fail(LPDF_ERR_MESH, "element %d edge %d is a boundary edge tagged interior", e, k);
+            if (tag == LPDF_EDGE_PERIODIC) {
+                if (!periodic) return fail(LPDF_ERR_MESH, "periodic edge without period_x");
+                const double ax = node_xy[2 * a], bx = node_xy[2 * b];
+                const double ymin = std::min(node_xy[2 * a + 1], node_xy[2 * b + 1]);
+                if (ax == x0 && bx == x0) left_edges.push_back({ymin, (int64_t)e * 3 + k});
+                else if (ax == x1 && bx == x1) right_edges.push_back({ymin, (int64_t)e * 3 + k});
+                else return fail(LPDF_ERR_MESH, "periodic edge of element %d is not on x0 or x1", e);
+            }
+        }
+    if (periodic) {
+        if (left_edges.size() != right_edges.size())
+            return fail(LPDF_ERR_MESH, "%zu left vs %zu right periodic edges", left_edges.size(), right_edges.size());
+        std::map<std::pair<double, double>, int64_t> rmap;
+        for (auto& r : right_edges) {
+            const int e = (int)(r.second / 3), k = (int)(r.second % 3);
+            const int a = tri[3 * e + k], b = tri[3 * e + (k + 1) % 3];
+            rmap[{node_xy[2 * a + 1], node_xy[2 * b + 1]}] = r.second;
+        }
+        for (auto& l : left_edges) {
+            const int e = (int)(l.second / 3), k = (int)(l.second % 3);
+            const int a = tri[3 * e + k], b = tri[3 * e + (k + 1) % 3];
+            // the partner runs the other way: its (a, b) y values are this edge's (b, a)
+            auto it = rmap.find({node_xy[2 * b + 1], node_xy[2 * a + 1]});
+            if (it == rmap.end()) return fail(LPDF_ERR_MESH, "left periodic edge of element %d has no partner", e);
+            const int f = (int)(it->second / 3), kk = (int)(it->second % 3);
+            en[4 * e + k] = f;
+            en[4 * f + kk] = e;
+            en[4 * e + 3] |= (1 << k);
+            en[4 * f + 3] |= (1 << kk);
+        }
+    }
+    // periodic node pairing: node on x1 -> node on x0 with the same y
+    std::vector<int32_t> master(n_nodes);
+    for (int i = 0; i < n_nodes; ++i) master[i] = i;
+    if (periodic) {
+        std::map<double, int> left_nodes;
+        for (int i = 0; i < n_nodes; ++i)
+            if (node_xy[2 * i] == x0) left_nodes[node_xy[2 * i + 1]] = i;
+        for (int i = 0; i < n_nodes; ++i)
+            if (node_xy[2 * i] == x1) {
+                auto it = left_nodes.find(node_xy[2 * i + 1]);
+                if (it == left_nodes.end()) return fail(LPDF_ERR_MESH, "node %d on x1 has no partner on x0", i);
+                master[i] = it->second;
+            }
+    }
+    for (int e = 0; e < n_tri; ++e)
+        for (int k = 0; k < 3; ++k) em[4 * e + k] = master[tri[3 * e + k]];
+
+    lpdf_mesh* m = new lpdf_mesh();
+    cudaGetDevice(&m->device);
+    DevMesh& d = m->d;
+    d.n_nodes = n_nodes;
+    d.n_tri = n_tri;
+    d.x0 = (float)x0; d.x1 = (float)x1; d.y0 = (float)y0; d.y1 = (float)y1;
+    d.periodic = periodic ? 1 : 0;
+    d.period = periodic ? (float)period_x : 0.0f;
+    m->box[0] = x0; m->box[1] = x1; m->box[2] = y0; m->box[3] = y1;
+    cudaError_t ce = cudaSuccess;
+    if ((ce = dalloc(&d.ex, n_tri)) != cudaSuccess || (ce = dalloc(&d.ey, n_tri)) != cudaSuccess ||
+        (ce = dalloc(&d.en, n_tri)) != cudaSuccess || (ce = dalloc(&d.ev, n_tri)) != cudaSuccess ||
+        (ce = dalloc(&d.em, n_tri)) != cudaSuccess || (ce = dalloc(&d.master, n_nodes)) != cudaSuccess ||
+        (ce = cudaMemcpy(d.ex, ex.data(), sizeof(float) * ex.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (ce = cudaMemcpy(d.ey, ey.data(), sizeof(float) * ey.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (ce = cudaMemcpy(d.en, en.data(), sizeof(int32_t) * en.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (ce = cudaMemcpy(d.ev, ev.data(), sizeof(int32_t) * ev.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (ce = cudaMemcpy(d.em, em.data(), sizeof(int32_t) * em.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (ce = cudaMemcpy(d.master, master.data(), sizeof(int32_t) * master.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        free_mesh_device(d);
+        delete m;
+        return fail(LPDF_ERR_CUDA, "mesh upload: %s", cudaGetErrorString(ce));
+    }
+    m->nbr.resize(3 * (size_t)n_tri);
+    for (int e = 0; e < n_tri; ++e)
+        for (int k = 0; k < 3; ++k) m->nbr[3 * e + k] = en[4 * e + k];
+    m->master = std::move(master);
+    *out = m;
+    return LPDF_OK;
+}
+
+void lpdf_mesh_free(lpdf_mesh* mesh)
+{
+    if (!mesh) return;
+    free_mesh_device(mesh->d);
+    delete mesh;
+}
+
+int lpdf_mesh_info(const lpdf_mesh* m, int32_t* n_nodes, int32_t* n_tri, double* box)
+{
+    if (!m) return fail(LPDF_ERR_ARG, "mesh is NULL");
+    if (n_nodes) *n_nodes = m->d.n_nodes;
+    if (n_tri) *n_tri = m->d.n_tri;
+    if (box) std::memcpy(box, m->box, sizeof m->box);
+    return LPDF_OK;
+}
+
+int lpdf_mesh_neighbors(const lpdf_mesh* m, int32_t* out)
+{
+    if (!m || !out) return fail(LPDF_ERR_ARG, "mesh_neighbors: NULL argument");
+    std::memcpy(out, m->nbr.data(), sizeof(int32_t) * m->nbr.size());
+    return LPDF_OK;
+}
+
+int lpdf_mesh_masters(const lpdf_mesh* m, int32_t* out)
+{
+    if (!m || !out) return fail(LPDF_ERR_ARG, "mesh_masters: NULL argument");
+    std::memcpy(out, m->master.data(), sizeof(int32_t) * m->master.size());
+    return LPDF_OK;
+}
+
+int lpdf_ctx_create(const lpdf_mesh* mesh, const lpdf_params* params, int64_t capacity, lpdf_ctx** out)
+{
+    if (!mesh || !out) return fail(LPDF_ERR_ARG, "ctx_create: NULL argument");
+    *out = nullptr;
+    int rc = check_params(params);
+    if (rc) return rc;
+    if (capacity < 1) return fail(LPDF_ERR_ARG, "capacity = %lld", (long long)capacity);
+    const int64_t cap = (capacity + 127) / 128 * 128;
+    lpdf_ctx* c = new lpdf_ctx();
+    c->mesh = mesh;
+    c->params = *params;
+    c->ns = params->ns;
+    DevState& s = c->s;
+    s.n = 0;
+    s.cap = cap;
+    const int nq = nquant(c->ns);
+    cudaError_t ce = cudaSuccess;
+    if ((ce = dalloc(&s.x, cap)) || (ce = dalloc(&s.y, cap)) || (ce = dalloc(&s.u, cap)) || (ce = dalloc(&s.v, cap)) ||
+        (ce = dalloc(&s.w, cap)) || (ce = dalloc(&s.om, cap)) || (ce = dalloc(&s.psi, cap * c->ns)) ||
+        (ce = dalloc(&s.elem, cap)) || (ce = dalloc(&s.pid, cap)) ||
+        (ce = dalloc(&c->node_acc, (size_t)mesh->d.n_nodes * nq)) || (ce = dalloc(&c->status, 4))) {
+        lpdf_ctx_free(c);
+        return fail(LPDF_ERR_CUDA, "ctx_create: %s", cudaGetErrorString(ce));
+    }
+    cudaMemset(c->node_acc, 0, sizeof(unsigned long long) * (size_t)mesh->d.n_nodes * nq);
+    const unsigned long long st0[4] = {0ull, 0ull, ~0ull, 0ull};
+    if ((ce = cudaMemcpy(c->status, st0, sizeof st0, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        lpdf_ctx_free(c);
+        return fail(LPDF_ERR_CUDA, "ctx_create: %s", cudaGetErrorString(ce));
+    }
+    *out = c;
+    return LPDF_OK;
+}
+
+void lpdf_ctx_free(lpdf_ctx* c)
+{
+    if (!c) return;
+    DevState& s = c->s;
+    cudaFree(s.x); cudaFree(s.y); cudaFree(s.u); cudaFree(s.v); cudaFree(s.w); cudaFree(s.om); cudaFree(s.psi);
+    cudaFree(s.elem); cudaFree(s.pid); cudaFree(c->node_acc); cudaFree(c->status);
+    delete c;
+}
+
+int lpdf_ctx_set_params(lpdf_ctx* c, const lpdf_params* p)
+{
+    if (!c) return fail(LPDF_ERR_ARG, "ctx is NULL");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (p->ns != c->ns) return fail(LPDF_ERR_ARG, "ns cannot change (%d -> %d)", c->ns, p->ns);
+    c->params = *p;
+    return LPDF_OK;
+}
+
+int64_t lpdf_ctx_size(const lpdf_ctx* c) { return c ? c->s.n : -1; }
+
+int lpdf_particles_init(lpdf_ctx* c, int32_t n_per_elem, const float* node_init, int32_t m_erlang, void* stream)
+{
+    if (!c || !node_init) return fail(LPDF_ERR_ARG, "particles_init: NULL argument");
+    if (n_per_elem < 1) return fail(LPDF_ERR_ARG, "n_per_elem = %d", n_per_elem);
+    if (m_erlang < 1 || m_erlang > 6) return fail(LPDF_ERR_ARG, "m_erlang = %d outside 1..6", m_erlang);
+    const int64_t P = (int64_t)c->mesh->d.n_tri * n_per_elem;
+    if (P > c->s.cap) return fail(LPDF_ERR_ARG, "%lld particles exceed capacity %lld", (long long)P, (long long)c->s.cap);
+    if (P > (int64_t)UINT32_MAX) return fail(LPDF_ERR_ARG, "particle ids are 32-bit");
+    c->s.n = P;
+    CUDA_TRY(launch_particles_init(c->mesh->d, c->s, c->ns, n_per_elem, node_init, m_erlang, c->params.seed,
+                                   c->status, (cudaStream_t)stream));
+    return LPDF_OK;
+}
+
+static int copy_state(lpdf_ctx* c, int64_t n, bool in, float* x, float* y, float* u, float* v, float* w, float* om,
+                      float* psi, int32_t* elem, uint32_t* pid, int on_device, cudaStream_t st)
+{
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : (in ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
+    DevState& s = c->s;
+    struct Item { void* dev; void* usr; size_t bytes; };
+    const size_t fb = sizeof(float) * (size_t)n;
+    Item items[] = {{s.x, x, fb}, {s.y, y, fb}, {s.u, u, fb}, {s.v, v, fb}, {s.w, w, fb}, {s.om, om, fb},
+                    {s.elem, elem, sizeof(int32_t) * (size_t)n}, {s.pid, pid, sizeof(uint32_t) * (size_t)n}};
+    if (n == 0) return LPDF_OK;
+    for (auto& it : items) {
+        if (!it.usr) continue;
+        CUDA_TRY(in ? cudaMemcpyAsync(it.dev, it.usr, it.bytes, k, st) : cudaMemcpyAsync(it.usr, it.dev, it.bytes, k, st));
+    }
+    if (psi)
+        for (int a = 0; a < c->ns; ++a) {
+            float* dev = s.psi + (size_t)a * s.cap;
+            float* usr = psi + (size_t)a * n;
+            CUDA_TRY(in ? cudaMemcpyAsync(dev, usr, fb, k, st) : cudaMemcpyAsync(usr, dev, fb, k, st));
+        }
+    return LPDF_OK;
+}
+
+int lpdf_set_state(lpdf_ctx* c, int64_t n, const float* x, const float* y, const float* u, const float* v,
+                   const float* w, const float* om, const float* psi, const int32_t* elem, const uint32_t* pid,
+                   int on_device, void* stream)
+{
+    if (!c) return fail(LPDF_ERR_ARG, "ctx is NULL");
+    if (n < 0 || n > c->s.cap) return fail(LPDF_ERR_ARG, "n = %lld outside 0..%lld", (long long)n, (long long)c->s.cap);
+    if (n > 0 && (!x || !y || !u || !v || !w || !om || !psi || !elem || !pid))
+        return fail(LPDF_ERR_ARG, "set_state needs every array");
+    c->s.n = n;
+    return copy_state(c, n, true, (float*)x, (float*)y, (float*)u, (float*)v, (float*)w, (float*)om, (float*)psi,
+                      (int32_t*)elem, (uint32_t*)pid, on_device, (cudaStream_t)stream);
+}
+
+int lpdf_get_state(const lpdf_ctx* c, float* x, float* y, float* u, float* v, float* w, float* om, float* psi,
+                   int32_t* elem, uint32_t* pid, int on_device, void* stream)
+{
+    if (!c) return fail(LPDF_ERR_ARG, "ctx is NULL");
+    return copy_state(const_cast<lpdf_ctx*>(c), c->s.n, false, x, y, u, v, w, om, psi, elem, pid, on_device,
+                      (cudaStream_t)stream);
+}
+
+int lpdf_pdf_step(lpdf_ctx* c, const float* node_fields, uint64_t step, void* stream)
+{
+    if (!c || !node_fields) return fail(LPDF_ERR_ARG, "pdf_step: NULL argument");
+    const cudaStream_t st = (cudaStream_t)stream;
+    const int nq = nquant(c->ns);
+    CUDA_TRY(cudaMemsetAsync(c->node_acc, 0, sizeof(unsigned long long) * (size_t)c->mesh->d.n_nodes * nq, st));
+    const StepParams p = make_step_params(c->params, c->mesh, step);
+    CUDA_TRY(launch_pdf_step(c->mesh->d, c->s, c->ns, node_fields, p, c->node_acc, c->status, st));
+    return LPDF_OK;
+}
+
+int lpdf_status(lpdf_ctx* c, int64_t* out, void* stream)
+{
+    if (!c) return fail(LPDF_ERR_ARG, "ctx is NULL");
+    const cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long h[4];
+    CUDA_TRY(cudaMemcpyAsync(h, c->status, sizeof h, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    const unsigned long long st0[4] = {0ull, 0ull, ~0ull, 0ull};
+    CUDA_TRY(cudaMemcpyAsync(c->status, st0, sizeof st0, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (out) {
+        out[0] = (int64_t)h[0];
+        out[1] = (int64_t)h[1];
+        out[2] = h[2] == ~0ull ? -1 : (int64_t)h[2];
+        out[3] = (int64_t)h[3];
+    }
+    if (h[0] & kErrLost) return fail(LPDF_ERR_LOST_PARTICLE, "%llu particle(s) lost, e.g. pid %llu", h[1], h[2]);
+    if (h[0] & kErrNonFinite) return fail(LPDF_ERR_NONFINITE, "non-finite particle state");
+    if (h[0] & kErrOverflow) return fail(LPDF_ERR_OVERFLOW, "fixed-point moment range exceeded");
+    return LPDF_OK;
+}
+
+int lpdf_grid_statistics(lpdf_ctx* c, double* out, int raw, void* stream)
+{
+    if (!c || !out) return fail(LPDF_ERR_ARG, "grid_statistics: NULL argument");
+    CUDA_TRY(launch_grid_statistics(c->mesh->d, c->ns, c->node_acc, out, raw ? 1 : 0, (cudaStream_t)stream));
+    return LPDF_OK;
+}
+
+}  // extern "C"

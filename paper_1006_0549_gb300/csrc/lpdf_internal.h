@@ -1,0 +1,64 @@
+// Internal structures of liblpdf (shared by the host API and the kernels of this library only).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lpdf.h"
+
+namespace lpdf {
+
+constexpr int kHopCap = 64;
+constexpr int kMaxNS = LPDF_MAX_SCALARS;
+// Moment sums are accumulated as 64-bit fixed point with 32 fractional bits: integer addition
+// is associative, so the sums do not depend on the order in which CTAs and warps add them.
+constexpr double kFixScale = 4294967296.0;      // 2^32
+constexpr float kFixLimit = 1.0e9f;             // |partial| above this sets the overflow bit
+
+inline int nfields(int ns) { return 22 + ns; }
+inline int nfields_padded(int ns) { return (22 + ns + 3) / 4 * 4; }
+inline int nquant(int ns) { return 11 + 2 * ns; }
+
+// Device mesh. Per element: corner coordinates, centroid x, 1/(2 area), neighbours, node ids.
+struct DevMesh {
+    int n_nodes = 0, n_tri = 0;
+    float x0 = 0, x1 = 0, y0 = 0, y1 = 0, period = 0;
+    int periodic = 0;
+    float4* ex = nullptr;     // (x0, x1, x2, centroid x)
+    float4* ey = nullptr;     // (y0, y1, y2, 1 / (2 area))
+    int4* en = nullptr;       // (nbr0, nbr1, nbr2, 0): neighbour across edge k, -1 = wall
+    int4* ev = nullptr;       // (node0, node1, node2, 0): geometric node ids (node-field rows)
+    int4* em = nullptr;       // (master0, master1, master2, 0): statistics node ids
+    int* master = nullptr;    // n_nodes
+};
+
+struct StepParams {
+    float dt, sdt, s2nu, nu2, C3, C4, half_cphi, lid_u;
+    uint32_t key0, key1;
+    uint32_t step_lo, step_hi;
+    int n_src;
+    float src_x[LPDF_MAX_SOURCES], src_y[LPDF_MAX_SOURCES], src_r[LPDF_MAX_SOURCES];
+    int src_alpha[LPDF_MAX_SOURCES];
+};
+
+struct DevState {
+    float *x, *y, *u, *v, *w, *om, *psi;   // psi: ns rows of `cap` floats
+    int* elem;
+    uint32_t* pid;
+    int64_t n, cap;
+};
+
+// Status words (device): [0] error bits, [1] lost count, [2] one lost pid, [3] total hops
+enum : unsigned { kErrLost = 1u, kErrNonFinite = 2u, kErrOverflow = 4u };
+
+// Launchers (lpdf_kernels.cu)
+cudaError_t launch_pdf_step(const DevMesh& m, const DevState& s, int ns, const float* fields,
+                            const StepParams& p, unsigned long long* node_acc, unsigned long long* status,
+                            cudaStream_t st);
+cudaError_t launch_particles_init(const DevMesh& m, const DevState& s, int ns, int n_per_elem,
+                                  const float* node_init, int m_erlang, uint64_t seed,
+                                  unsigned long long* status, cudaStream_t st);
+cudaError_t launch_grid_statistics(const DevMesh& m, int ns, const unsigned long long* node_acc, double* out,
+                                   int raw, cudaStream_t st);
+
+}  // namespace lpdf

@@ -1,0 +1,259 @@
+"""Thin ctypes binding of liblpdf (include/lpdf.h): argument marshalling only.
+
+Every numerical step runs in the CUDA library. There is no CPU fallback: if liblpdf.so is
+missing or cannot be loaded, every call raises. Device buffers are torch CUDA tensors (the
+binding passes their data pointers) and streams are torch CUDA streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import workloads as wl
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblpdf.so")
+
+LPDF_OK = 0
+LPDF_ERR_ARG = -1
+LPDF_ERR_MESH = -2
+LPDF_ERR_LOST_PARTICLE = -3
+LPDF_ERR_NONFINITE = -4
+LPDF_ERR_CG_NOCONV = -5
+LPDF_ERR_CUDA = -6
+LPDF_ERR_OVERFLOW = -7
+LPDF_ERR_UNSUPPORTED = -8
+ERRORS = {-1: "LPDF_ERR_ARG", -2: "LPDF_ERR_MESH", -3: "LPDF_ERR_LOST_PARTICLE", -4: "LPDF_ERR_NONFINITE",
+          -5: "LPDF_ERR_CG_NOCONV", -6: "LPDF_ERR_CUDA", -7: "LPDF_ERR_OVERFLOW", -8: "LPDF_ERR_UNSUPPORTED"}
+MAX_SOURCES = 8
+MAX_SCALARS = 4
+
+# every symbol include/lpdf.h declares
+EXPORTS = ("lpdf_params_default", "lpdf_last_error", "lpdf_version", "lpdf_mesh_load", "lpdf_mesh_free",
+           "lpdf_mesh_info", "lpdf_mesh_neighbors", "lpdf_mesh_masters", "lpdf_ctx_create", "lpdf_ctx_free",
+           "lpdf_ctx_set_params", "lpdf_ctx_size", "lpdf_particles_init", "lpdf_set_state", "lpdf_get_state",
+           "lpdf_pdf_step", "lpdf_status", "lpdf_grid_statistics")
+
+
+class LpdfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_double), ("dt", ctypes.c_double), ("C3", ctypes.c_double), ("C4", ctypes.c_double),
+                ("Cphi", ctypes.c_double), ("C0", ctypes.c_double), ("Comega1", ctypes.c_double),
+                ("Comega2", ctypes.c_double), ("CL", ctypes.c_double), ("Ceta", ctypes.c_double),
+                ("lid_u", ctypes.c_double), ("seed", ctypes.c_uint64), ("ns", ctypes.c_int32),
+                ("n_sources", ctypes.c_int32), ("src_x", ctypes.c_float * MAX_SOURCES),
+                ("src_y", ctypes.c_float * MAX_SOURCES), ("src_r", ctypes.c_float * MAX_SOURCES),
+                ("src_alpha", ctypes.c_int32 * MAX_SOURCES)]
+
+
+_lib = None
+
+
+def lib():
+    """Load liblpdf.so (built by paper_1006_0549_gb300._build.build()); raise if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1006_0549_gb300._build.build() "
+                           "(there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    L.lpdf_params_default.argtypes = [vp]
+    L.lpdf_params_default.restype = None
+    L.lpdf_last_error.restype = ctypes.c_char_p
+    L.lpdf_version.restype = ctypes.c_char_p
+    L.lpdf_mesh_load.argtypes = [vp, i32, vp, i32, vp, ctypes.c_double, vp]
+    L.lpdf_mesh_free.argtypes = [vp]
+    L.lpdf_mesh_free.restype = None
+    L.lpdf_mesh_info.argtypes = [vp, vp, vp, vp]
+    L.lpdf_mesh_neighbors.argtypes = [vp, vp]
+    L.lpdf_mesh_masters.argtypes = [vp, vp]
+    L.lpdf_ctx_create.argtypes = [vp, vp, i64, vp]
+    L.lpdf_ctx_free.argtypes = [vp]
+    L.lpdf_ctx_free.restype = None
+    L.lpdf_ctx_set_params.argtypes = [vp, vp]
+    L.lpdf_ctx_size.argtypes = [vp]
+    L.lpdf_ctx_size.restype = i64
+    L.lpdf_particles_init.argtypes = [vp, i32, vp, i32, vp]
+    L.lpdf_set_state.argtypes = [vp, i64] + [vp] * 9 + [ctypes.c_int, vp]
+    L.lpdf_get_state.argtypes = [vp] + [vp] * 9 + [ctypes.c_int, vp]
+    L.lpdf_pdf_step.argtypes = [vp, vp, u64, vp]
+    L.lpdf_status.argtypes = [vp, vp, vp]
+    L.lpdf_grid_statistics.argtypes = [vp, vp, ctypes.c_int, vp]
+    for name in EXPORTS:
+        f = getattr(L, name)
+        if f.restype is ctypes.c_int or (name not in ("lpdf_params_default", "lpdf_mesh_free", "lpdf_ctx_free",
+                                                      "lpdf_last_error", "lpdf_version", "lpdf_ctx_size")):
+            f.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != LPDF_OK:
+        raise LpdfError(rc, lib().lpdf_last_error().decode())
+    return rc
+
+
+def _ptr(t):
+    """Data pointer of a torch tensor or numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return ctypes.c_void_p(t.ctypes.data)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(s):
+    import torch
+    if s is None:
+        s = torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_params(nu=1.0 / 180.0, dt=1e-3, seed=1, ns=1, sources=(), lid_u=0.0, **consts) -> Params:
+    p = Params()
+    lib().lpdf_params_default(ctypes.byref(p))
+    p.nu, p.dt, p.seed, p.ns, p.lid_u = nu, dt, seed, ns, lid_u
+    p.n_sources = len(sources)
+    for i, (sx, sy, sr, sa) in enumerate(sources):
+        p.src_x[i], p.src_y[i], p.src_r[i], p.src_alpha[i] = sx, sy, sr, sa
+    for k, v in consts.items():
+        setattr(p, k, v)
+    return p
+
+
+def params_for(wk: "wl.Workload", **consts) -> Params:
+    return make_params(nu=wk.nu, dt=wk.dt, seed=wk.seed, ns=wk.ns, sources=wk.sources, lid_u=wk.lid_u, **consts)
+
+
+class Mesh:
+    """lpdf_mesh_load / lpdf_mesh_free."""
+
+    def __init__(self, mesh: "wl.Mesh"):
+        L = lib()
+        xy = np.ascontiguousarray(mesh.node_xy, dtype=np.float64)
+        tri = np.ascontiguousarray(mesh.tri, dtype=np.int32)
+        tag = np.ascontiguousarray(mesh.edge_tag, dtype=np.int32)
+        h = ctypes.c_void_p()
+        _check(L.lpdf_mesh_load(_ptr(xy), xy.shape[0], _ptr(tri), tri.shape[0], _ptr(tag), float(mesh.period_x),
+                                ctypes.byref(h)))
+        self.h = h
+        self.mesh = mesh
+        self.n_nodes, self.n_tri = xy.shape[0], tri.shape[0]
+
+    def neighbors(self):
+        out = np.empty((self.n_tri, 3), dtype=np.int32)
+        _check(lib().lpdf_mesh_neighbors(self.h, _ptr(out)))
+        return out
+
+    def masters(self):
+        out = np.empty(self.n_nodes, dtype=np.int32)
+        _check(lib().lpdf_mesh_masters(self.h, _ptr(out)))
+        return out
+
+    def info(self):
+        n = ctypes.c_int32()
+        e = ctypes.c_int32()
+        box = np.empty(4)
+        _check(lib().lpdf_mesh_info(self.h, ctypes.byref(n), ctypes.byref(e), _ptr(box)))
+        return n.value, e.value, tuple(box)
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                lib().lpdf_mesh_free(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+class Context:
+    """lpdf_ctx_create and the per-ensemble calls."""
+
+    def __init__(self, mesh: Mesh, params: Params, capacity: int):
+        self.mesh = mesh
+        self.params = params
+        self.ns = params.ns
+        h = ctypes.c_void_p()
+        _check(lib().lpdf_ctx_create(mesh.h, ctypes.byref(params), int(capacity), ctypes.byref(h)))
+        self.h = h
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                lib().lpdf_ctx_free(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    @property
+    def n(self) -> int:
+        return int(lib().lpdf_ctx_size(self.h))
+
+    def set_params(self, params: Params):
+        _check(lib().lpdf_ctx_set_params(self.h, ctypes.byref(params)))
+        self.params = params
+
+    def particles_init(self, n_per_elem: int, node_init, m_erlang: int = 4, stream=None):
+        _check(lib().lpdf_particles_init(self.h, int(n_per_elem), _ptr(node_init), int(m_erlang), _stream(stream)))
+
+    def set_state(self, st, stream=None):
+        """st: dict/State of torch CUDA tensors (on_device=1) or numpy arrays (host)."""
+        get = (lambda k: st[k]) if isinstance(st, dict) else (lambda k: getattr(st, k))
+        x = get("x")
+        on_dev = 0 if isinstance(x, np.ndarray) else 1
+        n = int(x.shape[0])
+        arrs = [get(k) for k in ("x", "y", "u", "v", "w", "omega", "psi", "elem", "pid")]
+        if not on_dev:
+            arrs = [np.ascontiguousarray(a) for a in arrs]
+        self._keep = arrs
+        _check(lib().lpdf_set_state(self.h, n, *[_ptr(a) for a in arrs], on_dev, _stream(stream)))
+
+    def get_state(self, stream=None, device: bool = True):
+        """Returns a dict of torch CUDA tensors (device=True) or numpy arrays."""
+        import torch
+        n, ns = self.n, self.ns
+        if device:
+            dev = torch.device("cuda")
+            out = {k: torch.empty(n, dtype=torch.float32, device=dev) for k in ("x", "y", "u", "v", "w", "omega")}
+            out["psi"] = torch.empty((ns, n), dtype=torch.float32, device=dev)
+            out["elem"] = torch.empty(n, dtype=torch.int32, device=dev)
+            out["pid"] = torch.empty(n, dtype=torch.int32, device=dev)
+        else:
+            out = {k: np.empty(n, dtype=np.float32) for k in ("x", "y", "u", "v", "w", "omega")}
+            out["psi"] = np.empty((ns, n), dtype=np.float32)
+            out["elem"] = np.empty(n, dtype=np.int32)
+            out["pid"] = np.empty(n, dtype=np.uint32)
+        _check(lib().lpdf_get_state(self.h, *[_ptr(out[k]) for k in ("x", "y", "u", "v", "w", "omega", "psi",
+                                                                      "elem", "pid")], 1 if device else 0,
+                                    _stream(stream)))
+        if not device:
+            torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        return out
+
+    def pdf_step(self, node_fields, step: int, stream=None):
+        _check(lib().lpdf_pdf_step(self.h, _ptr(node_fields), int(step), _stream(stream)))
+
+    def status(self, stream=None, raise_on_error: bool = True):
+        out = np.zeros(4, dtype=np.int64)
+        rc = lib().lpdf_status(self.h, _ptr(out), _stream(stream))
+        if raise_on_error:
+            _check(rc)
+        return rc, out
+
+    def grid_statistics(self, out, raw: bool = False, stream=None):
+        _check(lib().lpdf_grid_statistics(self.h, _ptr(out), 1 if raw else 0, _stream(stream)))
+        return out
+
+
+def version() -> str:
+    return lib().lpdf_version().decode()

@@ -1,0 +1,125 @@
+"""Helpers of the GPU parity tests: run the CUDA path through the C-ABI and compare with the oracle."""
+import numpy as np
+
+import oracle
+from paper_1006_0549_gb300 import lpdf, workloads as wl
+
+FIELDS = ("x", "y", "u", "v", "w", "omega")
+EPS32 = 2.0 ** -24
+# FP32 particle state, per step: |gpu - oracle| <= RTOL * max(|oracle|, rms of that field)
+RTOL = 1e-5
+
+
+def torch_state(st: wl.State):
+    import torch
+    d = torch.device("cuda")
+    out = {k: torch.from_numpy(np.ascontiguousarray(getattr(st, k))).to(d) for k in FIELDS}
+    out["psi"] = torch.from_numpy(np.ascontiguousarray(st.psi)).to(d)
+    out["elem"] = torch.from_numpy(np.ascontiguousarray(st.elem, dtype=np.int32)).to(d)
+    out["pid"] = torch.from_numpy(np.ascontiguousarray(st.pid).view(np.int32)).to(d)
+    return out
+
+
+def host_state(d, ns) -> wl.State:
+    g = {k: v.cpu().numpy() for k, v in d.items()}
+    return wl.State(*(g[k].astype(np.float32) for k in FIELDS), g["psi"].reshape(ns, -1).astype(np.float32),
+                    g["elem"].astype(np.int32), g["pid"].view(np.uint32))
+
+
+def oracle_params(p: lpdf.Params):
+    return oracle.make_params(nu=p.nu, dt=p.dt, seed=p.seed, ns=p.ns,
+                              sources=[(float(p.src_x[i]), float(p.src_y[i]), float(p.src_r[i]), int(p.src_alpha[i]))
+                                       for i in range(p.n_sources)],
+                              C3=p.C3, C4=p.C4, Cphi=p.Cphi, lid_u=p.lid_u)
+
+
+def gpu_step(ctx: lpdf.Context, fields_dev, st: wl.State, step: int):
+    """set_state -> pdf_step -> (new host state, raw moment sums, status)."""
+    import torch
+    ctx.set_state(torch_state(st))
+    ctx.pdf_step(fields_dev, step)
+    rc, status = ctx.status(raise_on_error=False)
+    out = host_state(ctx.get_state(), ctx.ns)
+    S = torch.empty((ctx.mesh.n_nodes, 11 + 2 * ctx.ns), dtype=torch.float64, device="cuda")
+    ctx.grid_statistics(S, raw=True)
+    torch.cuda.synchronize()
+    return out, S.cpu().numpy(), rc, status
+
+
+def compare_step(mesh: wl.Mesh, om: oracle.OracleMesh, params: lpdf.Params, F, st_in: wl.State, step: int,
+                 g: wl.State, check_locate: bool = True):
+    """Per-stage parity of one step from the same input state.
+
+    1. FP32 state within RTOL of the oracle's FP64 step, except for particles whose discrete
+       outcome (reflection, wrap, source) legitimately differs because the FP32 positions of the
+       two sides straddle the decision boundary by a rounding error;
+    2. the GPU's element of every particle equals the oracle's exact owner of the GPU's FP32
+       position (bit-exact).
+    Returns a dict of diagnostics."""
+    ns = params.ns
+    op = oracle_params(params)
+    res, oelem, aux, lost = oracle.pdf_step(om, op, F, st_in, step)
+    assert lost == 0
+    diag = {}
+    x0, x1, y0, y1 = mesh.box
+    pre_x, pre_y = aux[:, 0], aux[:, 1]
+    # straddling a wall or the periodic seam within rounding distance
+    near_wall = (np.abs(pre_y - y0) < 1e-5) | (np.abs(pre_y - y1) < 1e-5)
+    if mesh.period_x == 0.0:
+        near_wall |= (np.abs(pre_x - x0) < 1e-5) | (np.abs(pre_x - x1) < 1e-5)
+    ok_any = np.zeros(st_in.n, dtype=bool)
+    for k in FIELDS:
+        o = res[k]
+        gv = getattr(g, k).astype(np.float64)
+        rms = float(np.sqrt(np.mean(o * o))) or 1.0
+        d = np.abs(gv - o)
+        if k == "x" and mesh.period_x > 0:
+            d = np.minimum(d, np.abs(d - mesh.period_x))
+        bad = d > RTOL * np.maximum(np.abs(o), rms)
+        diag[f"max_rel_{k}"] = float(np.max(d / np.maximum(np.abs(o), rms)))
+        unexplained = bad & ~near_wall
+        assert not unexplained.any(), (k, np.nonzero(unexplained)[0][:10], gv[unexplained][:5], o[unexplained][:5])
+        ok_any |= bad
+    diag["explained_discrete_mismatches"] = int(ok_any.sum())
+    assert ok_any.sum() <= max(3, st_in.n // 10000)
+    # scalars: the source disc decision is taken on each side's own FP32 position
+    srcd = np.full(st_in.n, np.inf)
+    for i in range(params.n_sources):
+        srcd = np.minimum(srcd, np.abs(np.hypot(res["x"] - params.src_x[i], res["y"] - params.src_y[i]) - params.src_r[i]))
+    for a in range(ns):
+        o = res["psi"][a]
+        gv = g.psi[a].astype(np.float64)
+        d = np.abs(gv - o)
+        rms = float(np.sqrt(np.mean(o * o))) or 1.0
+        bad = d > RTOL * np.maximum(np.abs(o), rms)
+        diag[f"max_rel_psi{a}"] = float(np.max(d / np.maximum(np.abs(o), rms)))
+        unexplained = bad & ~(srcd < 1e-5) & ~near_wall
+        assert not unexplained.any(), ("psi", a, np.nonzero(unexplained)[0][:10])
+    # element ids: exact owner of the GPU position, by the oracle's brute force location
+    if check_locate:
+        for i in range(st_in.n):
+            e = om.locate_brute(float(g.x[i]), float(g.y[i]))
+            assert e == g.elem[i], (i, g.x[i], g.y[i], g.elem[i], e)
+        same = (g.x.astype(np.float64) == res["x"]) & (g.y.astype(np.float64) == res["y"])
+        assert np.array_equal(g.elem[same], oelem[same])
+        diag["bitwise_equal_positions"] = float(same.mean())
+    assert np.array_equal(g.pid, st_in.pid)
+    return diag, res, oelem
+
+
+def compare_moments(om: oracle.OracleMesh, g: wl.State, S_gpu, ns: int):
+    """GPU fixed-point sums against the oracle's FP64 reduction of the same FP32 state.
+
+    Tolerance from the arithmetic: each term lambda_a q_k is formed in FP32 (barycentric
+    determinants with one FMA-compensated rounding, the division, the products) and summed in
+    FP32 over at most 4 particles of a lane and 32 lanes of a warp before the exact integer
+    accumulation: |error| <= 48 eps32 sum_p |lambda_a q_k| + 2^-33 per FP32 partial converted
+    (at most one per particle)."""
+    f = lambda a: a.astype(np.float64)
+    S_o, Sabs = oracle.moments(om, ns, f(g.x), f(g.y), f(g.u), f(g.v), f(g.w), f(g.omega), f(g.psi), g.elem)
+    count = np.maximum(S_o[:, :1], 1.0) * 8.0
+    tol = 48 * EPS32 * Sabs + count * 2.0 ** -33
+    err = np.abs(S_gpu - S_o)
+    ratio = float(np.max(err / np.maximum(Sabs, 1e-300) / EPS32))
+    assert np.all(err <= tol), (np.argwhere(err > tol)[:5], err[err > tol][:5], tol[err > tol][:5])
+    return ratio, S_o

@@ -1,0 +1,182 @@
+"""Parity of the CUDA particle step (through the C-ABI) with the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1006_0549_gb300 import lpdf, workloads as wl
+from tests import gpu_common as gc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1006_0549_gb300 import _build
+    _build.build()
+    return torch
+
+
+def _setup(wk: wl.Workload, n_per_elem=None, fields_seed=5):
+    import torch
+    mesh = wk.mesh
+    gm = lpdf.Mesh(mesh)
+    om = oracle.OracleMesh(mesh)
+    params = lpdf.params_for(wk)
+    F = wl.synthetic_node_fields(mesh, wk.ns, seed=fields_seed)
+    Fd = torch.from_numpy(F).cuda()
+    npe = n_per_elem or wk.n_per_elem
+    ctx = lpdf.Context(gm, params, mesh.n_tri * npe + 1000)
+    return mesh, gm, om, params, F, Fd, ctx, npe
+
+
+def test_mesh_adjacency_matches_oracle(torch_cuda):
+    for mesh in (wl.channel_mesh(25, 20, 1), wl.cavity_mesh(20, 17, 2)):
+        gm = lpdf.Mesh(mesh)
+        om = oracle.OracleMesh(mesh)
+        assert np.array_equal(gm.neighbors(), om.neighbors())
+        assert np.array_equal(gm.masters(), om.masters())
+        n, e, box = gm.info()
+        assert (n, e) == (mesh.n_nodes, mesh.n_tri) and box == tuple(mesh.box)
+
+
+@pytest.mark.parametrize("workload", ["channel", "cavity"])
+def test_one_step_parity(torch_cuda, workload):
+    wk = wl.channel_small() if workload == "channel" else wl.cavity_small()
+    mesh, gm, om, params, F, Fd, ctx, npe = _setup(wk, n_per_elem=20)
+    st = wl.synthetic_state(mesh, npe, wk.ns, seed=7)
+    g, S, rc, status = gc.gpu_step(ctx, Fd, st, step=3)
+    assert rc == lpdf.LPDF_OK, status
+    diag, res, oelem = gc.compare_step(mesh, om, params, F, st, 3, g)
+    ratio, _ = gc.compare_moments(om, g, S, wk.ns)
+    print(workload, diag, "moment error / (eps32 * sum|lambda q|) max =", ratio)
+
+
+def test_three_chained_steps_channel(torch_cuda):
+    """Each step: the GPU advances its own state; the oracle re-runs that step from the GPU's input."""
+    wk = wl.channel_small()
+    mesh, gm, om, params, F, Fd, ctx, npe = _setup(wk, n_per_elem=30)
+    st = wl.synthetic_state(mesh, npe, wk.ns, seed=8)
+    for step in range(3):
+        g, S, rc, status = gc.gpu_step(ctx, Fd, st, step)
+        assert rc == lpdf.LPDF_OK
+        gc.compare_step(mesh, om, params, F, st, step, g, check_locate=(step == 2))
+        st = g
+
+
+def test_ragged_and_tiny_ensembles(torch_cuda):
+    """Sizes that are not multiples of the 4-particle lane, 128-particle warp tile or 4096 CTA range."""
+    wk = wl.channel_small()
+    mesh, gm, om, params, F, Fd, ctx, npe = _setup(wk, n_per_elem=10)
+    full = wl.synthetic_state(mesh, 10, wk.ns, seed=9)
+    for n in (1, 3, 127, 129, 4097, 9999):
+        sel = np.sort(np.random.default_rng(n).choice(full.n, size=n, replace=False))
+        st = wl.State(*(np.ascontiguousarray(getattr(full, k)[sel]) for k in gc.FIELDS),
+                      np.ascontiguousarray(full.psi[:, sel]), full.elem[sel], full.pid[sel])
+        g, S, rc, status = gc.gpu_step(ctx, Fd, st, 1)
+        assert rc == lpdf.LPDF_OK
+        gc.compare_step(mesh, om, params, F, st, 1, g)
+        gc.compare_moments(om, g, S, wk.ns)
+
+
+def test_empty_ensemble(torch_cuda):
+    import torch
+    wk = wl.channel_small()
+    mesh, gm, om, params, F, Fd, ctx, npe = _setup(wk, n_per_elem=1)
+    st = wl.synthetic_state(mesh, 1, wk.ns, seed=1)
+    empty = wl.State(*(getattr(st, k)[:0].copy() for k in gc.FIELDS), st.psi[:, :0].copy(), st.elem[:0].copy(),
+                     st.pid[:0].copy())
+    g, S, rc, status = gc.gpu_step(ctx, Fd, empty, 0)
+    assert rc == lpdf.LPDF_OK and g.n == 0 and np.all(S == 0.0)
+
+
+def test_step_is_bit_reproducible(torch_cuda):
+    wk = wl.cavity_small()
+    mesh, gm, om, params, F, Fd, ctx, npe = _setup(wk, n_per_elem=40)
+    st = wl.synthetic_state(mesh, npe, wk.ns, seed=11)
+    g1, S1, _, _ = gc.gpu_step(ctx, Fd, st, 5)
+    g2, S2, _, _ = gc.gpu_step(ctx, Fd, st, 5)
+    for k in gc.FIELDS:
+        assert np.array_equal(getattr(g1, k), getattr(g2, k))
+    assert np.array_equal(g1.elem, g2.elem) and np.array_equal(S1, S2)
+    # a permutation of the particles changes nothing but the order (pid keys the noise)
+    perm = np.random.default_rng(0).permutation(st.n)
+    sp = wl.State(*(np.ascontiguousarray(getattr(st, k)[perm]) for k in gc.FIELDS),
+                  np.ascontiguousarray(st.psi[:, perm]), st.elem[perm], st.pid[perm])
+    g3, S3, _, _ = gc.gpu_step(ctx, Fd, sp, 5)
+    inv = np.argsort(perm)
+    for k in gc.FIELDS:
+        assert np.array_equal(getattr(g3, k)[inv], getattr(g1, k))
+    # the FP32 partial sums group different particles, so only the oracle tolerance applies
+    gc.compare_moments(om, g3, S3, wk.ns)
+
+
+def test_grid_statistics_means_and_central_moments(torch_cuda):
+    import torch
+    wk = wl.channel_small()
+    mesh, gm, om, params, F, Fd, ctx, npe = _setup(wk, n_per_elem=20)
+    st = wl.synthetic_state(mesh, npe, wk.ns, seed=12)
+    g, S, rc, _ = gc.gpu_step(ctx, Fd, st, 0)
+    out = torch.empty_like(torch.from_numpy(S)).cuda()
+    ctx.grid_statistics(out, raw=False)
+    stats_gpu = out.cpu().numpy()
+    stats_ref = oracle.grid_statistics(S, wk.ns)    # same sums, oracle's formulas
+    assert np.allclose(stats_gpu, stats_ref, rtol=1e-12, atol=1e-12)
+    masters = gm.masters()
+    uniq = masters == np.arange(mesh.n_nodes)
+    assert abs(S[uniq, 0].sum() - st.n) < 1e-6 * st.n
+
+
+def test_particles_init_parity(torch_cuda):
+    """GPU initialisation vs the oracle's: positions within FP32 rounding, exact ownership of the
+    GPU positions, velocities and frequencies within RTOL."""
+    import torch
+    wk = wl.channel_small()
+    mesh, gm, om, params, F, Fd, ctx, npe = _setup(wk, n_per_elem=8)
+    init = torch.from_numpy(wl.node_init_fields(mesh)).cuda()
+    ctx.particles_init(npe, init, m_erlang=4)
+    rc, status = ctx.status(raise_on_error=False)
+    assert rc == lpdf.LPDF_OK
+    g = gc.host_state(ctx.get_state(), wk.ns)
+    res, oelem, opid, lost = oracle.particles_init(om, gc.oracle_params(params), npe, wl.node_init_fields(mesh), 4)
+    assert lost == 0
+    assert np.array_equal(g.pid, opid)
+    for k in gc.FIELDS:
+        o = res[k]
+        rms = float(np.sqrt(np.mean(o * o)))
+        assert np.all(np.abs(getattr(g, k) - o) <= 1e-5 * np.maximum(np.abs(o), rms)), k
+    for i in range(g.n):
+        assert om.locate_brute(float(g.x[i]), float(g.y[i])) == g.elem[i]
+    assert np.all(g.psi == 0.0)
+
+
+def test_lost_particle_is_reported_not_faulted(torch_cuda):
+    """A particle whose element is > 64 hops from its position: the walk stops at its cap, the
+    status reports the loss and the pid, and the context stays usable."""
+    wk = wl.channel_25m()
+    mesh = wk.mesh
+    gm = lpdf.Mesh(mesh)
+    params = lpdf.params_for(wk)
+    import torch
+    Fd = torch.from_numpy(wl.synthetic_node_fields(mesh, 1, seed=1)).cuda()
+    ctx = lpdf.Context(gm, params, 4096)
+    st = wl.synthetic_state(wl.channel_mesh(25, 20, 1), 1, 1, seed=1)
+    st = wl.State(*(getattr(st, k)[:64].copy() for k in gc.FIELDS), st.psi[:, :64].copy(),
+                  st.elem[:64].copy(), st.pid[:64].copy())
+    # put every particle into a valid element of the big mesh first: x near 0.1 ...
+    st.x[:] = 0.1
+    st.y[:] = 1.0
+    om = oracle.OracleMesh(mesh)
+    e_true = om.locate_brute(0.1, 1.0)
+    st.elem[:] = e_true
+    st.elem[5] = (e_true + mesh.n_tri // 2) % mesh.n_tri      # ~125 columns away
+    st.u[:] = 0.0; st.v[:] = 0.0
+    g, S, rc, status = gc.gpu_step(ctx, Fd, st, 0)
+    assert rc == lpdf.LPDF_ERR_LOST_PARTICLE
+    assert status[1] == 1 and status[2] == st.pid[5]
+    # the context still works
+    st.elem[5] = e_true
+    g, S, rc, status = gc.gpu_step(ctx, Fd, st, 1)
+    assert rc == lpdf.LPDF_OK
