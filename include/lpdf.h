@@ -185,6 +185,32 @@ int lpdf_status(lpdf_ctx* ctx, int64_t* out, void* stream);
  * ------------------------------------------------------------------------------------- */
 int lpdf_grid_statistics(lpdf_ctx* ctx, double* out, int raw, void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * lpdf_pdf_step_static -- the same particle step as lpdf_pdf_step for callers that cannot
+ * allocate device memory (the paper has no counterpart: this is an interface choice of the
+ * library). Hosts that own every device buffer through their own pool or arena, or that
+ * forbid cudaMalloc inside their time loop, keep the state in their own buffers and call this
+ * without an lpdf_ctx. The call allocates nothing: its scratch (fixed-point gridpoint
+ * accumulators and four status words) is a static device array of at most 2^21 accumulators,
+ * i.e. n_nodes * (11 + 2 ns) <= 2,097,152 (16 MiB, held by every GPU that loads the library
+ * until the process exits); larger meshes are rejected with LPDF_ERR_ARG.
+ *   mesh, params    as for lpdf_ctx_create (the mesh itself was built by lpdf_mesh_load)
+ *   x..pid          device, n particles (psi: ns rows of n), advanced in place
+ *   node_fields     device, n_nodes x nfp FP32 (see lpdf_pdf_step)
+ *   moments         device out, n_nodes x (11 + 2 ns) FP64 raw sums S_k(n) of the new state
+ *   status_out      host, 4 words as lpdf_status; NULL: the call is asynchronous and the status
+ *                   is not read; non-NULL: the call synchronises `stream` and returns
+ *                   LPDF_ERR_LOST_PARTICLE / NONFINITE / OVERFLOW as lpdf_status does.
+ * The first call on a device looks up the static array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture. Every call shares the one array and clears it
+ * on entry, so calls that overlap on the GPU (different streams, threads or processes sharing
+ * the context) race: serialise them.
+ * ------------------------------------------------------------------------------------- */
+int lpdf_pdf_step_static(const lpdf_mesh* mesh, const lpdf_params* params, int64_t n, float* x, float* y,
+                         float* u, float* v, float* w, float* omega, float* psi, int32_t* elem,
+                         const uint32_t* pid, const float* node_fields, uint64_t step, double* moments,
+                         int64_t* status_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,22 +16,6 @@
 
 using namespace lpdf;
 
-struct lpdf_mesh {
-    DevMesh d;
-    std::vector<int32_t> nbr;      // host copy, 3 per element
-    std::vector<int32_t> master;   // host copy
-    double box[4];
-    int device;
-};
-
-struct lpdf_ctx {
-    const lpdf_mesh* mesh;
-    lpdf_params params;
-    DevState s;
-    unsigned long long* node_acc = nullptr;   // n_nodes x nq fixed-point sums
-    unsigned long long* status = nullptr;     // 4 words
-    int ns;
-};
 
 namespace {
 
@@ -68,7 +52,20 @@ void free_mesh_device(DevMesh& d)
     d = DevMesh();
 }
 
-StepParams make_step_params(const lpdf_params& p, const lpdf_mesh* m, uint64_t step)
+}  // namespace
+
+int lpdf::lpdf_set_error(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+StepParams lpdf::make_step_params(const lpdf_params& p, const lpdf_mesh* m, uint64_t step)
 {
     StepParams s{};
     s.dt = (float)p.dt;
@@ -93,6 +90,8 @@ StepParams make_step_params(const lpdf_params& p, const lpdf_mesh* m, uint64_t s
     (void)m;
     return s;
 }
+
+namespace {
 
 int check_params(const lpdf_params* p)
 {

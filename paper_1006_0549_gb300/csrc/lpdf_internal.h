@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "lpdf.h"
 
 namespace lpdf {
@@ -61,4 +63,27 @@ cudaError_t launch_particles_init(const DevMesh& m, const DevState& s, int ns, i
 cudaError_t launch_grid_statistics(const DevMesh& m, int ns, const unsigned long long* node_acc, double* out,
                                    int raw, cudaStream_t st);
 
+StepParams make_step_params(const lpdf_params& p, const struct ::lpdf_mesh* m, uint64_t step);
+// records the calling thread's error message (lpdf_last_error) and returns `code`
+int lpdf_set_error(int code, const char* fmt, ...);
+
 }  // namespace lpdf
+
+// Opaque handles of the C ABI (defined here so that every translation unit of the library
+// can reach the device tables).
+struct lpdf_mesh {
+    lpdf::DevMesh d;
+    std::vector<int32_t> nbr;      // host copy, 3 per element
+    std::vector<int32_t> master;   // host copy
+    double box[4];
+    int device;
+};
+
+struct lpdf_ctx {
+    const lpdf_mesh* mesh;
+    lpdf_params params;
+    lpdf::DevState s;
+    unsigned long long* node_acc = nullptr;   // n_nodes x nq fixed-point sums
+    unsigned long long* status = nullptr;     // 4 words
+    int ns;
+};

@@ -34,7 +34,7 @@ MAX_SCALARS = 4
 EXPORTS = ("lpdf_params_default", "lpdf_last_error", "lpdf_version", "lpdf_mesh_load", "lpdf_mesh_free",
            "lpdf_mesh_info", "lpdf_mesh_neighbors", "lpdf_mesh_masters", "lpdf_ctx_create", "lpdf_ctx_free",
            "lpdf_ctx_set_params", "lpdf_ctx_size", "lpdf_particles_init", "lpdf_set_state", "lpdf_get_state",
-           "lpdf_pdf_step", "lpdf_status", "lpdf_grid_statistics")
+           "lpdf_pdf_step", "lpdf_status", "lpdf_grid_statistics", "lpdf_pdf_step_static")
 
 
 class LpdfError(RuntimeError):
@@ -88,6 +88,7 @@ def lib():
     L.lpdf_pdf_step.argtypes = [vp, vp, u64, vp]
     L.lpdf_status.argtypes = [vp, vp, vp]
     L.lpdf_grid_statistics.argtypes = [vp, vp, ctypes.c_int, vp]
+    L.lpdf_pdf_step_static.argtypes = [vp, vp, i64] + [vp] * 9 + [vp, u64, vp, vp, vp]
     for name in EXPORTS:
         f = getattr(L, name)
         if f.restype is ctypes.c_int or (name not in ("lpdf_params_default", "lpdf_mesh_free", "lpdf_ctx_free",
@@ -253,6 +254,21 @@ class Context:
     def grid_statistics(self, out, raw: bool = False, stream=None):
         _check(lib().lpdf_grid_statistics(self.h, _ptr(out), 1 if raw else 0, _stream(stream)))
         return out
+
+
+def pdf_step_static(mesh: Mesh, params: Params, state: dict, node_fields, step: int, moments,
+                    read_status: bool = True, stream=None):
+    """lpdf_pdf_step_static: the step on caller-owned device buffers; allocates nothing.
+
+    `state` holds torch CUDA tensors x, y, u, v, w, omega, psi (ns x n), elem, pid, advanced in
+    place; `moments` (n_nodes x (11 + 2 ns) float64, CUDA) receives the raw gridpoint sums."""
+    n = int(state["x"].shape[0])
+    st = np.zeros(4, dtype=np.int64) if read_status else None
+    rc = lib().lpdf_pdf_step_static(mesh.h, ctypes.byref(params), n,
+                                    *[_ptr(state[k]) for k in ("x", "y", "u", "v", "w", "omega", "psi", "elem",
+                                                               "pid")],
+                                    _ptr(node_fields), int(step), _ptr(moments), _ptr(st), _stream(stream))
+    return rc, st
 
 
 def version() -> str:
