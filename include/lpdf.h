@@ -77,13 +77,16 @@ typedef struct {
     int32_t n_sources;
     float src_x[LPDF_MAX_SOURCES], src_y[LPDF_MAX_SOURCES], src_r[LPDF_MAX_SOURCES];
     int32_t src_alpha[LPDF_MAX_SOURCES]; /* scalar index set to 1 inside source disc s */
+    int32_t sort_every; /* > 0: lpdf_pdf_step re-buckets the particles by element (lpdf_sort)
+                           before every sort_every-th step; 0: only on explicit lpdf_sort calls */
 } lpdf_params;
 
 typedef struct lpdf_mesh lpdf_mesh;
 typedef struct lpdf_ctx lpdf_ctx;
 
 /* Fills *p with C3 = 5, C4 = 0.25, Cphi = 2, C0 = 2.1, Comega1 = 0.5, Comega2 = 0.73,
- * CL = 0.134, Ceta = 72, nu = 1/180, dt = 1e-3, ns = 1, no sources, seed = 1, lid_u = 0. */
+ * CL = 0.134, Ceta = 72, nu = 1/180, dt = 1e-3, ns = 1, no sources, seed = 1, lid_u = 0,
+ * sort_every = 0. */
 void lpdf_params_default(lpdf_params* p);
 
 /* Message of the calling thread's last error ("" if none). Owned by the library. */
@@ -165,11 +168,22 @@ int lpdf_get_state(const lpdf_ctx* ctx, float* x, float* y, float* u, float* v, 
 int lpdf_pdf_step(lpdf_ctx* ctx, const float* node_fields, uint64_t step, void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * lpdf_sort -- re-buckets the ensemble by element: afterwards the particles of every element
+ * are contiguous, ordered by element and then by their previous position (a deterministic
+ * counting sort; pid travels with each particle). Particles are never lost or duplicated;
+ * the pdf_step results do not depend on the order except through FP32 summation order of the
+ * moment partials. async. Uses the context's second state buffer (allocated by ctx_create).
+ * ------------------------------------------------------------------------------------- */
+int lpdf_sort(lpdf_ctx* ctx, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * lpdf_status -- sync. Reads and clears the device status: out[0] error bits (1 lost
- * particle, 2 non-finite state, 4 fixed-point overflow), out[1] number of lost particles,
+ * particle, 2 non-finite state, 4 fixed-point overflow, 8 a bounded wait on a bulk copy gave up, 16 an internal
+ * consistency check of the step kernel failed),
+ * out[1] number of lost particles,
  * out[2] pid of one lost particle (-1 if none), out[3] total walk hops of the last step.
  * Returns LPDF_ERR_LOST_PARTICLE / LPDF_ERR_NONFINITE / LPDF_ERR_OVERFLOW when the
- * corresponding bit was set, else LPDF_OK.
+ * corresponding bit was set (LPDF_ERR_CUDA for bits 8 and 16), else LPDF_OK.
  * ------------------------------------------------------------------------------------- */
 int lpdf_status(lpdf_ctx* ctx, int64_t* out, void* stream);
 

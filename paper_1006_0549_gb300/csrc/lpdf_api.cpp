@@ -104,6 +104,7 @@ int check_params(const lpdf_params* p)
         if (p->src_alpha[i] < 0 || p->src_alpha[i] >= p->ns)
             return fail(LPDF_ERR_ARG, "source %d sets scalar %d, but ns = %d", i, p->src_alpha[i], p->ns);
     if (!(p->dt > 0.0) || !(p->nu >= 0.0)) return fail(LPDF_ERR_ARG, "need dt > 0 and nu >= 0");
+    if (p->sort_every < 0) return fail(LPDF_ERR_ARG, "sort_every = %d", p->sort_every);
     return LPDF_OK;
 }
 
@@ -319,9 +320,18 @@ int lpdf_ctx_create(const lpdf_mesh* mesh, const lpdf_params* params, int64_t ca
     s.cap = cap;
     const int nq = nquant(c->ns);
     cudaError_t ce = cudaSuccess;
+    DevState& s2 = c->s2;
+    s2.n = 0;
+    s2.cap = cap;
+    const size_t E = (size_t)mesh->d.n_tri;
     if ((ce = dalloc(&s.x, cap)) || (ce = dalloc(&s.y, cap)) || (ce = dalloc(&s.u, cap)) || (ce = dalloc(&s.v, cap)) ||
         (ce = dalloc(&s.w, cap)) || (ce = dalloc(&s.om, cap)) || (ce = dalloc(&s.psi, cap * c->ns)) ||
         (ce = dalloc(&s.elem, cap)) || (ce = dalloc(&s.pid, cap)) ||
+        (ce = dalloc(&s2.x, cap)) || (ce = dalloc(&s2.y, cap)) || (ce = dalloc(&s2.u, cap)) || (ce = dalloc(&s2.v, cap)) ||
+        (ce = dalloc(&s2.w, cap)) || (ce = dalloc(&s2.om, cap)) || (ce = dalloc(&s2.psi, cap * c->ns)) ||
+        (ce = dalloc(&s2.elem, cap)) || (ce = dalloc(&s2.pid, cap)) ||
+        (ce = dalloc(&c->sort.cnt, E + 1)) || (ce = dalloc(&c->sort.cursor, E + 1)) ||
+        (ce = dalloc(&c->sort.start, E + 2)) || (ce = dalloc(&c->sort.perm, cap)) ||
         (ce = dalloc(&c->node_acc, (size_t)mesh->d.n_nodes * nq)) || (ce = dalloc(&c->status, 4))) {
         lpdf_ctx_free(c);
         return fail(LPDF_ERR_CUDA, "ctx_create: %s", cudaGetErrorString(ce));
@@ -339,9 +349,12 @@ int lpdf_ctx_create(const lpdf_mesh* mesh, const lpdf_params* params, int64_t ca
 void lpdf_ctx_free(lpdf_ctx* c)
 {
     if (!c) return;
-    DevState& s = c->s;
-    cudaFree(s.x); cudaFree(s.y); cudaFree(s.u); cudaFree(s.v); cudaFree(s.w); cudaFree(s.om); cudaFree(s.psi);
-    cudaFree(s.elem); cudaFree(s.pid); cudaFree(c->node_acc); cudaFree(c->status);
+    for (DevState* s : {&c->s, &c->s2}) {
+        cudaFree(s->x); cudaFree(s->y); cudaFree(s->u); cudaFree(s->v); cudaFree(s->w); cudaFree(s->om);
+        cudaFree(s->psi); cudaFree(s->elem); cudaFree(s->pid);
+    }
+    cudaFree(c->sort.cnt); cudaFree(c->sort.cursor); cudaFree(c->sort.start); cudaFree(c->sort.perm);
+    cudaFree(c->node_acc); cudaFree(c->status);
     delete c;
 }
 
@@ -415,10 +428,24 @@ int lpdf_get_state(const lpdf_ctx* c, float* x, float* y, float* u, float* v, fl
                       (cudaStream_t)stream);
 }
 
+int lpdf_sort(lpdf_ctx* c, void* stream)
+{
+    if (!c) return fail(LPDF_ERR_ARG, "sort: NULL argument");
+    c->s2.n = c->s.n;
+    CUDA_TRY(launch_sort(c->mesh->d, c->s, c->ns, c->s2, c->sort, c->status, (cudaStream_t)stream));
+    std::swap(c->s, c->s2);
+    return LPDF_OK;
+}
+
 int lpdf_pdf_step(lpdf_ctx* c, const float* node_fields, uint64_t step, void* stream)
 {
     if (!c || !node_fields) return fail(LPDF_ERR_ARG, "pdf_step: NULL argument");
     const cudaStream_t st = (cudaStream_t)stream;
+    if (c->params.sort_every > 0 && c->nsteps % c->params.sort_every == 0) {
+        const int rc = lpdf_sort(c, stream);
+        if (rc) return rc;
+    }
+    ++c->nsteps;
     const int nq = nquant(c->ns);
     CUDA_TRY(cudaMemsetAsync(c->node_acc, 0, sizeof(unsigned long long) * (size_t)c->mesh->d.n_nodes * nq, st));
     const StepParams p = make_step_params(c->params, c->mesh, step);
@@ -445,6 +472,8 @@ int lpdf_status(lpdf_ctx* c, int64_t* out, void* stream)
     if (h[0] & kErrLost) return fail(LPDF_ERR_LOST_PARTICLE, "%llu particle(s) lost, e.g. pid %llu", h[1], h[2]);
     if (h[0] & kErrNonFinite) return fail(LPDF_ERR_NONFINITE, "non-finite particle state");
     if (h[0] & kErrOverflow) return fail(LPDF_ERR_OVERFLOW, "fixed-point moment range exceeded");
+    if (h[0] & kErrTimeout) return fail(LPDF_ERR_CUDA, "a bulk-copy wait in the step kernel timed out");
+    if (h[0] & kErrCheck) return fail(LPDF_ERR_CUDA, "an internal consistency check of the step kernel failed");
     return LPDF_OK;
 }
 

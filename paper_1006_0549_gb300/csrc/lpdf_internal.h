@@ -51,7 +51,7 @@ struct DevState {
 };
 
 // Status words (device): [0] error bits, [1] lost count, [2] one lost pid, [3] total hops
-enum : unsigned { kErrLost = 1u, kErrNonFinite = 2u, kErrOverflow = 4u };
+enum : unsigned { kErrLost = 1u, kErrNonFinite = 2u, kErrOverflow = 4u, kErrTimeout = 8u, kErrCheck = 16u };
 
 // Launchers (lpdf_kernels.cu)
 cudaError_t launch_pdf_step(const DevMesh& m, const DevState& s, int ns, const float* fields,
@@ -62,6 +62,16 @@ cudaError_t launch_particles_init(const DevMesh& m, const DevState& s, int ns, i
                                   unsigned long long* status, cudaStream_t st);
 cudaError_t launch_grid_statistics(const DevMesh& m, int ns, const unsigned long long* node_acc, double* out,
                                    int raw, cudaStream_t st);
+
+// scratch of the element re-bucketing: counts, cursors, bucket starts (E+1 buckets), permutation
+struct SortScratch {
+    int* cnt = nullptr;
+    int* cursor = nullptr;
+    int* start = nullptr;
+    int* perm = nullptr;
+};
+cudaError_t launch_sort(const DevMesh& m, const DevState& s, int ns, const DevState& dst, SortScratch& w,
+                        unsigned long long* status, cudaStream_t st);
 
 StepParams make_step_params(const lpdf_params& p, const struct ::lpdf_mesh* m, uint64_t step);
 // records the calling thread's error message (lpdf_last_error) and returns `code`
@@ -82,8 +92,11 @@ struct lpdf_mesh {
 struct lpdf_ctx {
     const lpdf_mesh* mesh;
     lpdf_params params;
-    lpdf::DevState s;
+    lpdf::DevState s;                         // current particle state
+    lpdf::DevState s2;                        // second buffer (target of the re-bucketing)
+    lpdf::SortScratch sort;
     unsigned long long* node_acc = nullptr;   // n_nodes x nq fixed-point sums
     unsigned long long* status = nullptr;     // 4 words
     int ns;
+    int64_t nsteps = 0;                       // pdf_step calls so far
 };

@@ -59,14 +59,29 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 // (w + 1/2) 2^-32, rounded to FP32
 __device__ __forceinline__ float u01(uint32_t w) { return fmaf((float)w, 0x1p-32f, 0x1p-33f); }
 
-// Box-Muller (1958): r = sqrt(-2 ln u0), angle 2 pi u1
+// Box-Muller (1958) on the special-function unit: r^2 = -2 ln u0 (lg2.approx: absolute error
+// ~2^-22 in log2), r = r^2 * rsqrt(r^2), angle theta = 2 pi u1 - pi in [-pi, pi), where the SFU
+// sine and cosine are accurate to ~2^-21.4 absolute; cos(theta + pi) = -cos(theta) and
+// sin(theta + pi) = -sin(theta), so z0 = r cos(2 pi u1), z1 = r sin(2 pi u1) as in the oracle.
 __device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float& z0, float& z1)
 {
+    const float r2 = -2.0f * __logf(u01(w0));
+    const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
+    const float th = fmaf(6.28318530717958648f, u01(w1), -3.14159265358979324f);
+    float sn, cs;
+    __sincosf(th, &sn, &cs);
+    z0 = -r * cs;
+    z1 = -r * sn;
+}
+
+// accurate variant for the initialisation kernel (not on the hot path)
+__device__ __forceinline__ void box_muller_accurate(uint32_t w0, uint32_t w1, float& z0, float& z1)
+{
     const float r = sqrtf(-2.0f * logf(u01(w0)));
-    float s, c;
-    sincospif(2.0f * u01(w1), &s, &c);
-    z0 = r * c;
-    z1 = r * s;
+    float sn, cs;
+    sincospif(2.0f * u01(w1), &sn, &cs);
+    z0 = r * cs;
+    z1 = r * sn;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -114,17 +129,21 @@ __device__ __noinline__ int orient_exact(double ax, double ay, double bx, double
     return h[nh - 1] > 0.0 ? 1 : -1;
 }
 
-// orientation of p relative to directed edge a->b, (bx-ax)(py-ay) - (by-ay)(px-ax): FP32
-// value for navigation and its exact sign (error-bounded FP32 filter, exact FP64 fallback).
+// orientation of p relative to directed edge a->b, (bx-ax)(py-ay) - (by-ay)(px-ax): the FP32
+// value (Kahan's FMA determinant: at most 1.5 ulp of the result beyond the rounding of the four
+// differences) and its exact sign. Filter: every rounding above is bounded by 3.5 eps32 (|t1| +
+// |t2|) (eps32 = 2^-24); 4e-7 (~6.7 eps32) also covers the rounding of the bound. Undecided
+// cases go to the exact FP64 expansion.
 __device__ __forceinline__ float orient_sign(float ax, float ay, float bx, float by, float px, float py, int& sgn)
 {
     const float dx1 = __fsub_rn(bx, ax), dy1 = __fsub_rn(by, ay);
     const float dx2 = __fsub_rn(px, ax), dy2 = __fsub_rn(py, ay);
-    const float t1 = __fmul_rn(dx1, dy2), t2 = __fmul_rn(dy1, dx2);
-    const float val = __fsub_rn(t1, t2);
-    const float detsum = __fadd_rn(fabsf(t1), fabsf(t2));
-    // (3 + 16 eps) eps with eps = 2^-24 is 1.79e-7; 2e-7 leaves room for the rounding of the bound
-    const float bound = 2.0e-7f * detsum;
+    const float w = dy1 * dx2;
+    const float e = fmaf(-dy1, dx2, w);
+    const float f = fmaf(dx1, dy2, -w);
+    const float val = f + e;
+    const float detsum = fmaf(fabsf(dx1), fabsf(dy2), fabsf(w));
+    const float bound = 4.0e-7f * detsum;
     if (detsum > 1e-25f && val > bound) { sgn = 1; return val; }
     if (detsum > 1e-25f && -val > bound) { sgn = -1; return val; }
     sgn = orient_exact((double)bx, (double)by, (double)px, (double)py, (double)ax, (double)ay);
@@ -139,8 +158,9 @@ __device__ __forceinline__ bool edge_owns(float ax, float ay, float bx, float by
 
 // Barycentric neighbour walk from element e to the unique owner of (px, py). Exact inside
 // tests in the element's own frame; in a periodic image frame only navigation. Returns the
-// owner, -1 on a wall exit, -2 at the hop cap.
-__device__ int locate_walk(const DevMesh& M, int e, float px, float py, int& hops)
+// owner (and its barycentrics, from the orientation values of the last test), -1 on a wall
+// exit, -2 at the hop cap.
+__device__ int locate_walk(const DevMesh& M, int e, float px, float py, int& hops, float lam[3])
 {
     for (int h = 0; h <= kHopCap; ++h) {
         const float4 X = __ldg(&M.ex[e]);
@@ -148,24 +168,37 @@ __device__ int locate_walk(const DevMesh& M, int e, float px, float py, int& hop
         const int4 N = __ldg(&M.en[e]);
         const float xs[3] = {X.x, X.y, X.z}, ys[3] = {Y.x, Y.y, Y.z};
         const int nb[3] = {N.x, N.y, N.z};
+        // nearest periodic image of the point relative to this element (elements are much
+        // smaller than the period, so |centroid - x| > period/2 means the other image)
         float sh = 0.0f;
-        if (M.periodic) sh = rintf((X.w - px) / M.period) * M.period;
+        if (M.periodic) {
+            const float d = X.w - px;
+            if (fabsf(d) > 0.5f * M.period) sh = copysignf(M.period, d);
+        }
         int best = -1;
         float bestv = 0.0f;
-        bool all_in = true;
         if (sh == 0.0f) {
+            bool all_in = true;
+            float vv[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const int a = k, b = (k + 1) % 3;
                 int s;
-                const float val = orient_sign(xs[a], ys[a], xs[b], ys[b], px, py, s);
+                vv[k] = orient_sign(xs[a], ys[a], xs[b], ys[b], px, py, s);
                 const bool in = s > 0 || (s == 0 && edge_owns(xs[a], ys[a], xs[b], ys[b]));
                 if (!in) {
                     all_in = false;
-                    if (best < 0 || val < bestv) { best = k; bestv = val; }
+                    if (best < 0 || vv[k] < bestv) { best = k; bestv = vv[k]; }
                 }
             }
-            if (all_in) { hops = h; return e; }
+            if (all_in) {
+                // edge k = (v_k, v_k+1) is opposite vertex k+2: lambda_{k+2} = orient_k / (2 area)
+                lam[2] = vv[0] * Y.w;
+                lam[0] = vv[1] * Y.w;
+                lam[1] = vv[2] * Y.w;
+                hops = h;
+                return e;
+            }
         } else {
             const float qx = px + sh;
 #pragma unroll
@@ -274,7 +307,11 @@ __device__ __forceinline__ bool advance(const DevMesh& M, const float* __restric
     // Eq. 2 with the velocity at t_n and the same dW_1, dW_2
     float qx = s.x + s.u * P.dt + P.s2nu * dW1;
     float qy = s.y + s.v * P.dt + P.s2nu * dW2;
-    if (M.periodic) qx -= floorf((qx - M.x0) / M.period) * M.period;
+    if (M.periodic) {
+        if (qx < M.x0) qx += M.period;
+        else if (qx >= M.x1) qx -= M.period;
+        if (qx < M.x0 || qx >= M.x1) qx -= floorf((qx - M.x0) / M.period) * M.period;   // moves > one period
+    }
 #pragma unroll 1
     for (int it = 0; it < 8; ++it) {
         if (qy < M.y0) { qy = 2.0f * M.y0 - qy; un = -un; vn = -vn; wn = -wn; }
@@ -287,10 +324,14 @@ __device__ __forceinline__ bool advance(const DevMesh& M, const float* __restric
     if (qx >= M.x1) qx = M.periodic ? M.x0 : nextafterf(M.x1, -CUDART_INF_F);
     if (qy >= M.y1) qy = nextafterf(M.y1, -CUDART_INF_F);
     int h = 0;
-    int ne = locate_walk(M, e, qx, qy, h);
+    int ne = locate_walk(M, e, qx, qy, h, lam);
     hops += h;
     const bool lost = ne < 0 || bad_elem;
-    if (lost) { err |= kErrLost; if (ne < 0) ne = e; }
+    if (lost) {
+        err |= kErrLost;
+        if (ne < 0) ne = e;
+        barycentric(__ldg(&M.ex[ne]), __ldg(&M.ey[ne]), qx, qy, lam[0], lam[1], lam[2]);
+    }
     // concentrated scalar sources
     for (int q = 0; q < P.n_src; ++q)
         if (in_source(qx, qy, P.src_x[q], P.src_y[q], P.src_r[q])) {
@@ -300,10 +341,6 @@ __device__ __forceinline__ bool advance(const DevMesh& M, const float* __restric
         }
     if (!(isfinite(un) && isfinite(vn) && isfinite(wn) && isfinite(omn) && isfinite(qx) && isfinite(qy)))
         err |= kErrNonFinite;
-    // shape functions at the new position for the moments
-    const float4 X2 = __ldg(&M.ex[ne]);
-    const float4 Y2 = __ldg(&M.ey[ne]);
-    barycentric(X2, Y2, qx, qy, lam[0], lam[1], lam[2]);
     s.x = qx; s.y = qy; s.u = un; s.v = vn; s.w = wn; s.om = omn; s.elem = ne;
     return lost;
 }
@@ -353,196 +390,521 @@ __device__ __forceinline__ void table_add(NodeTable<NQ, NT>& T, int slot, int no
 }
 
 // ------------------------------------------------------------------------------------------
+// Bulk-copy (TMA) and mbarrier helpers (inline PTX, sm_90+ forms valid on sm_103a).
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: gives up after ~2^22 polls (each poll may suspend the thread briefly)
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity)
+{
+#pragma unroll 1
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, unsigned long long* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Adds a whole 3 x NQ partial (corner-major) to the table: rare path, kept out of line so that
+// the hot loop stays small in the instruction cache.
+template <int NQ, int NT>
+__device__ __noinline__ void flush_partial(NodeTable<NQ, NT>& T, const float* acc, int4 nodes, const short* slots,
+                                           unsigned long long* __restrict__ node_acc, unsigned* err)
+{
+    const int nd[3] = {nodes.x, nodes.y, nodes.z};
+    for (int c = 0; c < 3; ++c)
+        for (int k = 0; k < NQ; ++k) table_add(T, (int)slots[c], nd[c], k, to_fixed(acc[c * NQ + k], *err), node_acc);
+}
+
+// ------------------------------------------------------------------------------------------
 // The fused step kernel.
 // ------------------------------------------------------------------------------------------
 template <int NS>
-struct StepSmem {
-    static constexpr int NV = 7 + NS;          // lambda0..2, u, v, w, omega, psi
+struct alignas(16) WarpTile {
+    static constexpr int NF = 8 + NS;          // x, y, u, v, w, omega, psi[NS], elem, pid
     static constexpr int NQ = 11 + 2 * NS;
     static constexpr int NK = 3 * NQ;          // columns: corner-major, quantity-minor
-    static constexpr int WB = (NV * kTile > 32 * NK) ? NV * kTile : 32 * NK;
-    static constexpr int NT = 256;
-    float wbuf[kWarps][WB];                    // reduction inputs (tile order), later lane partials
-    int wkey[kWarps][kTile];                   // new element of every tile particle (tile order)
-    unsigned char perm[kWarps][kTile];         // sorted position -> tile index
-    unsigned char wbin[kWarps][kTile];         // sorted position -> bin
-    int bkey[kWarps][kTile];                   // bin -> element
-    int blast[kWarps][32];
+    static constexpr int F_X = 0, F_Y = 1, F_U = 2, F_V = 3, F_W = 4, F_OM = 5, F_PSI = 6, F_ELEM = 6 + NS,
+                         F_PID = 7 + NS;
+    static constexpr int LAM = NF * kTile;     // 3 rows of lambda' after the state rows
+    static constexpr int KEY = LAM + 3 * kTile;
+    static constexpr int RAW = KEY + kTile;
+    static constexpr int WB = RAW > 32 * NK ? RAW : 32 * NK;   // the lane partials reuse it all
+    static constexpr int NL = NS == 1 ? 8 : (NS == 2 ? 4 : 2);   // parked partials of segments that end mid-chunk
+    alignas(16) float buf[WB];                 // bulk-copy rows start on 16-byte boundaries
+    int dkey[kTile];                           // this tile's distinct new elements, ascending
+    int blast[32];
+    float lpart[NL][NK];                       // parked partials
+    int lbin[NL];
+    int nlist;
+    int ndist;
+    unsigned long long bar;
+};
+
+// Internal consistency check of the binning: a failed check records kErrCheck in the status
+// word and the caller skips the access, so a logic error can never become a wild address.
+__device__ __forceinline__ bool consistent(bool ok, unsigned& err)
+{
+    if (!ok) err |= kErrCheck;
+    return ok;
+}
+
+// CTA-level binning of one 1024-particle sub-tile by new element
+constexpr int kMaxBins = 64;
+constexpr int kRows = kWarps * kPPL;            // (warp, j) rows of 32 particles
+
+template <int NS>
+struct StepSmem {
+    static constexpr int NQ = 11 + 2 * NS;
+    static constexpr int NT = 128;
+    WarpTile<NS> w[kWarps];
+    int binkey[kSubTile];                      // bin -> element (ascending)
+    short cslot[kMaxBins][3];                  // bin of the current pass -> node-table slot of each corner
+    int cnt[kMaxBins][kRows];                  // particles of bin b in row r, then exclusive offsets
+    unsigned short cperm[kSubTile];            // sorted position -> (warp << 7) | tile index
+    unsigned char cbin[kSubTile];              // sorted position -> bin
+    int nbins;
+    int ntot;
+    int wsum[kWarps];
     NodeTable<NQ, NT> table;
 };
+
+// Parked partials of the warp (segments that ended inside a lane's chunk): lane k adds column
+// k (and k + 32) of every entry to the node table. Each value is converted on its own, so the
+// order of the entries does not matter.
+template <int NS>
+__device__ __forceinline__ void flush_parked(const DevMesh& M, StepSmem<NS>& sm, WarpTile<NS>& W, int b0, int lane,
+                                             unsigned long long* __restrict__ node_acc, unsigned& err)
+{
+    constexpr int NQ = WarpTile<NS>::NQ, NK = WarpTile<NS>::NK;
+    const int nl = min(W.nlist, WarpTile<NS>::NL);
+    for (int k = lane; k < NK; k += 32) {
+        const int c = k / NQ, q = k - c * NQ;
+        for (int e = 0; e < nl; ++e) {
+            const int b = W.lbin[e];
+            if (!consistent(b >= 0 && b < kMaxBins && b0 + b < sm.nbins, err)) continue;
+            const int ek = sm.binkey[b0 + b];
+            if (!consistent(ek >= 0 && ek < M.n_tri, err)) continue;
+            const int4 mv = __ldg(&M.em[ek]);
+            table_add(sm.table, (int)sm.cslot[b][c], c == 0 ? mv.x : (c == 1 ? mv.y : mv.z), q,
+                      to_fixed(W.lpart[e][k], err), node_acc);
+        }
+    }
+}
+
+// Column combine of the lanes' last segments: lanes holding the same bin are contiguous; lane k
+// sums column k (and k + 32) over each run of lanes and adds it to the node table. The partials
+// go through `part` (32 x NK floats).
+template <int NS>
+__device__ __forceinline__ void combine_lanes(const DevMesh& M, StepSmem<NS>& sm, WarpTile<NS>& W, float* part,
+                                              const float* acc, int curb, int b0, int lane,
+                                              unsigned long long* __restrict__ node_acc, unsigned& err)
+{
+    constexpr int NQ = WarpTile<NS>::NQ, NK = WarpTile<NS>::NK;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) part[lane * NK + k] = acc[k];
+    W.blast[lane] = curb;
+    __syncwarp();
+    const int k0 = lane, k1 = lane + 32;
+    const bool has1 = k1 < NK;
+    const int c0 = k0 / NQ, q0 = k0 - c0 * NQ;
+    const int c1 = k1 / NQ, q1 = k1 - c1 * NQ;
+    auto put = [&](int b, int c, int q, float v) {
+        if (!consistent(b >= 0 && b < kMaxBins && b0 + b < sm.nbins, err)) return;
+        const int ek = sm.binkey[b0 + b];
+        if (!consistent(ek >= 0 && ek < M.n_tri, err)) return;
+        const int4 mv = __ldg(&M.em[ek]);
+        table_add(sm.table, (int)sm.cslot[b][c], c == 0 ? mv.x : (c == 1 ? mv.y : mv.z), q, to_fixed(v, err), node_acc);
+    };
+    float s0 = 0.0f, s1 = 0.0f;
+    int b = W.blast[0];
+#pragma unroll 4
+    for (int l = 0; l < 32; ++l) {
+        const int bl = W.blast[l];
+        if (bl != b) {
+            if (b >= 0) {
+                put(b, c0, q0, s0);
+                if (has1) put(b, c1, q1, s1);
+            }
+            b = bl;
+            s0 = 0.0f;
+            s1 = 0.0f;
+        }
+        s0 += part[l * NK + k0];
+        if (has1) s1 += part[l * NK + k1];
+    }
+    if (b >= 0) {
+        put(b, c0, q0, s0);
+        if (has1) put(b, c1, q1, s1);
+    }
+}
 
 template <int NS>
 __global__ void __launch_bounds__(kTPB, 2)
 pdf_step_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevState S, const float* __restrict__ F,
-                const __grid_constant__ StepParams P,
-                unsigned long long* __restrict__ node_acc, unsigned long long* __restrict__ status)
+                const __grid_constant__ StepParams P, unsigned long long* __restrict__ node_acc,
+                unsigned long long* __restrict__ status, int use_bulk)
 {
     using SM = StepSmem<NS>;
-    constexpr int NV = SM::NV, NQ = SM::NQ, NK = SM::NK, NT = SM::NT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using WT = WarpTile<NS>;
+    constexpr int NF = WT::NF, NQ = WT::NQ, NK = WT::NK, NT = SM::NT;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     SM& sm = *reinterpret_cast<SM*>(smem_raw);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    WT& W = sm.w[wid];
     for (int i = threadIdx.x; i < NT; i += kTPB) sm.table.key[i] = -1;
     for (int i = threadIdx.x; i < NT * NQ; i += kTPB) (&sm.table.acc[0][0])[i] = 0ull;
+    if (lane == 0) mbar_init(&W.bar, 1);
     __syncthreads();
 
     unsigned err = 0;
     int hops = 0;
+    uint32_t phase = 0;
+    bool abort = false;
     const int64_t range0 = (int64_t)blockIdx.x * kRange;
-    float* wb = sm.wbuf[wid];
-    int* wkey = sm.wkey[wid];
-    unsigned char* perm = sm.perm[wid];
-    unsigned char* wbin = sm.wbin[wid];
-    int* bkey = sm.bkey[wid];
+    float* const tile = W.buf;
+    float* const lamr = W.buf + WT::LAM;
+    float* const keyr = W.buf + WT::KEY;          // new element ids, as float bit patterns
+    // global row of field f (psi rows are `cap` apart)
+    auto grow = [&](int f) -> float* {
+        if (f == WT::F_X) return S.x;
+        if (f == WT::F_Y) return S.y;
+        if (f == WT::F_U) return S.u;
+        if (f == WT::F_V) return S.v;
+        if (f == WT::F_W) return S.w;
+        if (f == WT::F_OM) return S.om;
+        if (f == WT::F_ELEM) return reinterpret_cast<float*>(S.elem);
+        if (f == WT::F_PID) return reinterpret_cast<float*>(S.pid);
+        return S.psi + (size_t)(f - WT::F_PSI) * S.cap;
+    };
 
+    // the sub-tile loop is uniform over the CTA (it contains CTA barriers)
     for (int sub = 0; sub < kSubTilesPerCTA; ++sub) {
-        const int64_t tb = range0 + (int64_t)sub * kSubTile + (int64_t)wid * kTile;
-        if (tb >= S.n) break;
-        // ---- 1. advance 4 particles per lane (tile index j*32 + lane), store, stage inputs
+        const int64_t sb = range0 + (int64_t)sub * kSubTile;
+        if (sb >= S.n) break;
+        const int64_t tb = sb + (int64_t)wid * kTile;
+        const int64_t rem = S.n - tb;
+        int nvalid = rem <= 0 ? 0 : (rem < (int64_t)kTile ? (int)rem : kTile);
+        if (abort) nvalid = 0;
+        const bool bulk = use_bulk && nvalid == kTile;
+        // the previous tile's bulk store must have finished reading the buffer, and the generic
+        // reads and writes of the previous tile must be ordered before the next bulk load
+        if (lane == 0) bulk_wait_read_all();
+        fence_async_shared();
+        __syncwarp();
+        // ---- 1. stage the tile's state in shared memory ---------------------------------
+        if (bulk) {
+            if (lane == 0) {
+                mbar_expect_tx(&W.bar, (uint32_t)(NF * kTile * sizeof(float)));
+#pragma unroll
+                for (int f = 0; f < NF; ++f) bulk_load(tile + f * kTile, grow(f) + tb, kTile * sizeof(float), &W.bar);
+            }
+            if (mbar_wait_bounded(&W.bar, phase)) {
+                phase ^= 1u;
+            } else {
+                // give the copies in flight one more bounded wait, then stop this warp's work
+                err |= kErrTimeout;
+                mbar_wait_bounded(&W.bar, phase);
+                abort = true;
+                nvalid = 0;
+            }
+        } else if (nvalid > 0) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const float* g = grow(f) + tb;
+                for (int t = lane; t < nvalid; t += 32) tile[f * kTile + t] = g[t];
+            }
+            __syncwarp();
+        }
+        // ---- 2. advance; lane l takes tile particles l, l+32, l+64, l+96 -----------------
 #pragma unroll 1
         for (int j = 0; j < kPPL; ++j) {
             const int t = j * 32 + lane;
-            const int64_t i = tb + t;
             int key = INT_MAX;
-            if (i < S.n) {
+            if (t < nvalid) {
                 Particle<NS> p;
-                p.x = S.x[i]; p.y = S.y[i]; p.u = S.u[i]; p.v = S.v[i]; p.w = S.w[i]; p.om = S.om[i];
+                p.x = tile[WT::F_X * kTile + t]; p.y = tile[WT::F_Y * kTile + t];
+                p.u = tile[WT::F_U * kTile + t]; p.v = tile[WT::F_V * kTile + t];
+                p.w = tile[WT::F_W * kTile + t]; p.om = tile[WT::F_OM * kTile + t];
 #pragma unroll
-                for (int a = 0; a < NS; ++a) p.psi[a] = S.psi[(size_t)a * S.cap + i];
-                p.elem = S.elem[i];
-                const uint32_t pid = S.pid[i];
+                for (int a = 0; a < NS; ++a) p.psi[a] = tile[(WT::F_PSI + a) * kTile + t];
+                p.elem = __float_as_int(tile[WT::F_ELEM * kTile + t]);
+                const uint32_t pid = __float_as_uint(tile[WT::F_PID * kTile + t]);
                 float lam[3];
                 if (advance<NS>(M, F, P, pid, p, lam, err, hops)) {
                     atomicAdd(&status[1], 1ull);
                     atomicCAS(&status[2], ~0ull, (unsigned long long)pid);
                 }
-                S.x[i] = p.x; S.y[i] = p.y; S.u[i] = p.u; S.v[i] = p.v; S.w[i] = p.w; S.om[i] = p.om;
+                tile[WT::F_X * kTile + t] = p.x; tile[WT::F_Y * kTile + t] = p.y;
+                tile[WT::F_U * kTile + t] = p.u; tile[WT::F_V * kTile + t] = p.v;
+                tile[WT::F_W * kTile + t] = p.w; tile[WT::F_OM * kTile + t] = p.om;
 #pragma unroll
-                for (int a = 0; a < NS; ++a) S.psi[(size_t)a * S.cap + i] = p.psi[a];
-                S.elem[i] = p.elem;
+                for (int a = 0; a < NS; ++a) tile[(WT::F_PSI + a) * kTile + t] = p.psi[a];
+                tile[WT::F_ELEM * kTile + t] = __int_as_float(p.elem);
+                lamr[t] = lam[0]; lamr[kTile + t] = lam[1]; lamr[2 * kTile + t] = lam[2];
                 key = p.elem;
-                wb[0 * kTile + t] = lam[0]; wb[1 * kTile + t] = lam[1]; wb[2 * kTile + t] = lam[2];
-                wb[3 * kTile + t] = p.u; wb[4 * kTile + t] = p.v; wb[5 * kTile + t] = p.w; wb[6 * kTile + t] = p.om;
-#pragma unroll
-                for (int a = 0; a < NS; ++a) wb[(7 + a) * kTile + t] = p.psi[a];
             }
-            wkey[t] = key;
+            keyr[t] = __int_as_float(key);
         }
-        __syncwarp();
-        // ---- 2. stable warp sort of the tile by new element: perm[sorted pos] = tile index
-        int n = 0, nb = 0;
+        // ---- 3. write the tile back (bulk store of every field but pid) -----------------
+        if (bulk && !abort) {
+            fence_async_shared();
+            __syncwarp();
+            if (lane == 0) {
+#pragma unroll
+                for (int f = 0; f < NF - 1; ++f) bulk_store(grow(f) + tb, tile + f * kTile, kTile * sizeof(float));
+                bulk_commit();
+            }
+        } else if (nvalid > 0) {
+            __syncwarp();
+#pragma unroll
+            for (int f = 0; f < NF - 1; ++f) {
+                float* g = grow(f) + tb;
+                for (int t = lane; t < nvalid; t += 32) g[t] = tile[f * kTile + t];
+            }
+        }
+        // ---- 4. the tile's distinct new elements, ascending (warp minimum loop) ------------
+        int key[kPPL];
+#pragma unroll
+        for (int j = 0; j < kPPL; ++j) key[j] = __float_as_int(keyr[j * 32 + lane]);
         {
-            int key[kPPL];
-#pragma unroll
-            for (int j = 0; j < kPPL; ++j) key[j] = wkey[j * 32 + lane];
-            int mn = min(min(key[0], key[1]), min(key[2], key[3]));
-            int cur = __reduce_min_sync(kFull, mn);
+            int nd = 0;
+            int cur = __reduce_min_sync(kFull, min(min(key[0], key[1]), min(key[2], key[3])));
             while (cur != INT_MAX) {
-                int c = 0;
-#pragma unroll
-                for (int j = 0; j < kPPL; ++j) c += (key[j] == cur);
-                int incl = c;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int tt = __shfl_up_sync(kFull, incl, o);
-                    if (lane >= o) incl += tt;
-                }
-                const int total = __shfl_sync(kFull, incl, 31);
-                int p0 = n + incl - c;
-#pragma unroll
-                for (int j = 0; j < kPPL; ++j)
-                    if (key[j] == cur) { perm[p0] = (unsigned char)(j * 32 + lane); wbin[p0] = (unsigned char)nb; ++p0; }
-                if (lane == 0) bkey[nb] = cur;
-                n += total;
-                ++nb;
+                if (lane == 0 && consistent(nd < kTile, err)) W.dkey[nd] = cur;
+                ++nd;
                 int nx = INT_MAX;
 #pragma unroll
                 for (int j = 0; j < kPPL; ++j)
                     if (key[j] > cur) nx = min(nx, key[j]);
                 cur = __reduce_min_sync(kFull, nx);
             }
+            if (lane == 0) W.ndist = nd;
         }
-        __syncwarp();
-        // ---- 3. per-lane serial accumulation over sorted positions 4l..4l+3 ------------
-        float acc[NK];
+        __syncthreads();
+        // ---- 5. merge the warps' sorted lists into the CTA bins (warp 0) ------------------
+        if (wid == 0) {
+            // lane l looks after list entries l and l+32 of every warp's list: a k-way merge by
+            // repeated minimum over the heads
+            int head[kWarps];
 #pragma unroll
-        for (int k = 0; k < NK; ++k) acc[k] = 0.0f;
-        int curb = -1;
-        const int pbeg = kPPL * lane;
-#pragma unroll 1
-        for (int p = pbeg; p < pbeg + kPPL && p < n; ++p) {
-            const int b = wbin[p];
-            if (b != curb) {
-                if (curb >= 0) {
-                    // a segment that ends inside this lane's chunk: straight to the node table
-                    const int4 mv = __ldg(&M.em[bkey[curb]]);
-                    const int s0 = table_slot(sm.table, mv.x), s1 = table_slot(sm.table, mv.y),
-                              s2 = table_slot(sm.table, mv.z);
+            for (int w = 0; w < kWarps; ++w) head[w] = 0;
+            int nbins = 0;
+            for (;;) {
+                int mn = INT_MAX;
 #pragma unroll
-                    for (int k = 0; k < NQ; ++k) {
-                        table_add(sm.table, s0, mv.x, k, to_fixed(acc[k], err), node_acc);
-                        table_add(sm.table, s1, mv.y, k, to_fixed(acc[NQ + k], err), node_acc);
-                        table_add(sm.table, s2, mv.z, k, to_fixed(acc[2 * NQ + k], err), node_acc);
-                        acc[k] = 0.0f; acc[NQ + k] = 0.0f; acc[2 * NQ + k] = 0.0f;
-                    }
-                }
-                curb = b;
+                for (int w = 0; w < kWarps; ++w)
+                    if (head[w] < sm.w[w].ndist) mn = min(mn, sm.w[w].dkey[head[w]]);
+                if (mn == INT_MAX) break;
+#pragma unroll
+                for (int w = 0; w < kWarps; ++w)
+                    if (head[w] < sm.w[w].ndist && sm.w[w].dkey[head[w]] == mn) ++head[w];
+                if (lane == 0 && consistent(nbins < kSubTile, err)) sm.binkey[nbins] = mn;
+                ++nbins;
             }
-            const int t = perm[p];
-            const float l0 = wb[0 * kTile + t], l1 = wb[1 * kTile + t], l2 = wb[2 * kTile + t];
-            float q[NQ];
-            const float u = wb[3 * kTile + t], v = wb[4 * kTile + t], w = wb[5 * kTile + t];
-            q[0] = 1.0f; q[1] = u; q[2] = v; q[3] = w;
-            q[4] = u * u; q[5] = u * v; q[6] = u * w; q[7] = v * v; q[8] = v * w; q[9] = w * w;
-            q[10] = wb[6 * kTile + t];
-#pragma unroll
-            for (int a = 0; a < NS; ++a) {
-                const float ps = wb[(7 + a) * kTile + t];
-                q[11 + a] = ps;
-                q[11 + NS + a] = ps * ps;
-            }
-#pragma unroll
-            for (int k = 0; k < NQ; ++k) {
-                acc[k] = fmaf(l0, q[k], acc[k]);
-                acc[NQ + k] = fmaf(l1, q[k], acc[NQ + k]);
-                acc[2 * NQ + k] = fmaf(l2, q[k], acc[2 * NQ + k]);
-            }
+            if (lane == 0) sm.nbins = nbins;
         }
-        __syncwarp();
-        // ---- 4. combine the lanes' last segments column by column ---------------------
-        float* part = wb;   // reuses the staged inputs: 32 x NK
+        __syncthreads();
+        const int nbins = sm.nbins;
+        int gbin[kPPL];
 #pragma unroll
-        for (int k = 0; k < NK; ++k) part[lane * NK + k] = acc[k];
-        sm.blast[wid][lane] = curb;
-        __syncwarp();
-#pragma unroll 1
-        for (int k = lane; k < NK; k += 32) {
-            const int c = k / NQ, qq = k - c * NQ;
-            float s = 0.0f;
+        for (int j = 0; j < kPPL; ++j) {
             int b = -1;
-#pragma unroll 1
-            for (int l = 0; l < 32; ++l) {
-                const int bl = sm.blast[wid][l];
-                if (bl != b) {
-                    if (b >= 0) {
-                        const int4 mv = __ldg(&M.em[bkey[b]]);
-                        const int node = c == 0 ? mv.x : (c == 1 ? mv.y : mv.z);
-                        table_add(sm.table, table_slot(sm.table, node), node, qq, to_fixed(s, err), node_acc);
-                    }
-                    b = bl;
-                    s = 0.0f;
+            if (key[j] != INT_MAX) {
+                int lo = 0, hi = nbins - 1;           // binary search: binkey is ascending
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (sm.binkey[mid] < key[j]) lo = mid + 1; else hi = mid;
                 }
-                s += part[l * NK + k];
+                b = lo;
             }
-            if (b >= 0) {
-                const int4 mv = __ldg(&M.em[bkey[b]]);
-                const int node = c == 0 ? mv.x : (c == 1 ? mv.y : mv.z);
-                table_add(sm.table, table_slot(sm.table, node), node, qq, to_fixed(s, err), node_acc);
+            gbin[j] = b;
+        }
+        // passes over ranges of at most kMaxBins bins (one pass unless the sub-tile is scattered)
+        for (int b0 = 0; b0 < nbins; b0 += kMaxBins) {
+            const int nbp = min(kMaxBins, nbins - b0);
+            const bool last = b0 + kMaxBins >= nbins;
+            // ---- 6. stable counting sort of this pass's particles by bin -----------------
+            for (int i = threadIdx.x; i < nbp * kRows; i += kTPB) (&sm.cnt[0][0])[i] = 0;
+            __syncthreads();
+            int bin[kPPL], rank[kPPL];
+#pragma unroll
+            for (int j = 0; j < kPPL; ++j) {
+                const int b = (gbin[j] >= b0 && gbin[j] < b0 + nbp) ? gbin[j] - b0 : -1;
+                const unsigned m = __match_any_sync(kFull, b);
+                rank[j] = __popc(m & lt);
+                bin[j] = b;
+                if (b >= 0 && rank[j] == 0) sm.cnt[b][wid * kPPL + j] = __popc(m);
+            }
+            __syncthreads();
+            // exclusive scan over (bin, row), bin-major: each thread owns a run of entries
+            {
+                constexpr int PER = (kMaxBins * kRows) / kTPB;
+                const int n = nbp * kRows;
+                const int e0 = threadIdx.x * PER;
+                int v[PER];
+                int sum = 0;
+#pragma unroll
+                for (int i = 0; i < PER; ++i) {
+                    v[i] = (e0 + i < n) ? (&sm.cnt[0][0])[e0 + i] : 0;
+                    sum += v[i];
+                }
+                int incl = sum;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int tt = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += tt;
+                }
+                if (lane == 31) sm.wsum[wid] = incl;
+                __syncthreads();
+                int woff = 0;
+#pragma unroll
+                for (int w = 0; w < kWarps; ++w) woff += (w < wid) ? sm.wsum[w] : 0;
+                if (threadIdx.x == kTPB - 1) sm.ntot = woff + incl;
+                int run = woff + incl - sum;
+#pragma unroll
+                for (int i = 0; i < PER; ++i) {
+                    if (e0 + i < n) (&sm.cnt[0][0])[e0 + i] = run;
+                    run += v[i];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < kPPL; ++j)
+                if (bin[j] >= 0) {
+                    const int pos = sm.cnt[bin[j]][wid * kPPL + j] + rank[j];
+                    if (!consistent(pos >= 0 && pos < kSubTile, err)) continue;
+                    sm.cperm[pos] = (unsigned short)((wid << 7) | (j * 32 + lane));
+                    sm.cbin[pos] = (unsigned char)bin[j];
+                }
+            // node-table slots of every bin's three corners
+            for (int i = threadIdx.x; i < 3 * nbp; i += kTPB) {
+                const int b = i / 3, c = i - 3 * (i / 3);
+                const int ek = sm.binkey[b0 + b];
+                if (!consistent(ek >= 0 && ek < M.n_tri, err)) { sm.cslot[b][c] = -1; continue; }
+                const int4 mv = __ldg(&M.em[ek]);
+                sm.cslot[b][c] = (short)table_slot(sm.table, c == 0 ? mv.x : (c == 1 ? mv.y : mv.z));
+            }
+            if (lane == 0) W.nlist = 0;
+            __syncthreads();
+            // ---- 7. warp w reduces sorted positions 128w .. 128w+127; lane l takes 4 --------
+            const int ntot = consistent(sm.ntot >= 0 && sm.ntot <= kSubTile, err) ? sm.ntot : 0;
+            float acc[NK];
+#pragma unroll
+            for (int k = 0; k < NK; ++k) acc[k] = 0.0f;
+            int curb = -1;
+            const int pbeg = wid * kTile + kPPL * lane;
+#pragma unroll 1
+            for (int p = pbeg; p < pbeg + kPPL && p < ntot; ++p) {
+                const int b = sm.cbin[p];
+                if (!consistent(b < nbp && sm.cperm[p] < kSubTile, err)) break;
+                if (b != curb) {
+                    if (curb >= 0) {
+                        // a segment that ends inside this lane's chunk: park its FP32 partial
+                        const int slot = atomicAdd(&W.nlist, 1);
+                        if (slot < WT::NL) {
+#pragma unroll
+                            for (int k = 0; k < NK; ++k) { W.lpart[slot][k] = acc[k]; acc[k] = 0.0f; }
+                            W.lbin[slot] = curb;
+                        } else {
+                            float spill[NK];
+#pragma unroll
+                            for (int k = 0; k < NK; ++k) { spill[k] = acc[k]; acc[k] = 0.0f; }
+                            flush_partial(sm.table, spill, __ldg(&M.em[sm.binkey[b0 + curb]]), sm.cslot[curb], node_acc,
+                                          &err);
+                        }
+                    }
+                    curb = b;
+                }
+                const int cp = sm.cperm[p];
+                const WT& Src = sm.w[cp >> 7];
+                const int t = cp & 127;
+                const float* sl = Src.buf + WT::LAM;
+                const float l0 = sl[t], l1 = sl[kTile + t], l2 = sl[2 * kTile + t];
+                float q[NQ];
+                const float u = Src.buf[WT::F_U * kTile + t], v = Src.buf[WT::F_V * kTile + t],
+                            w = Src.buf[WT::F_W * kTile + t];
+                q[0] = 1.0f; q[1] = u; q[2] = v; q[3] = w;
+                q[4] = u * u; q[5] = u * v; q[6] = u * w; q[7] = v * v; q[8] = v * w; q[9] = w * w;
+                q[10] = Src.buf[WT::F_OM * kTile + t];
+#pragma unroll
+                for (int a = 0; a < NS; ++a) {
+                    const float ps = Src.buf[(WT::F_PSI + a) * kTile + t];
+                    q[11 + a] = ps;
+                    q[11 + NS + a] = ps * ps;
+                }
+#pragma unroll
+                for (int k = 0; k < NQ; ++k) {
+                    acc[k] = fmaf(l0, q[k], acc[k]);
+                    acc[NQ + k] = fmaf(l1, q[k], acc[NQ + k]);
+                    acc[2 * NQ + k] = fmaf(l2, q[k], acc[2 * NQ + k]);
+                }
+            }
+            __syncwarp();
+            flush_parked<NS>(M, sm, W, b0, lane, node_acc, err);
+            if (last) {
+                // every warp has read the tiles it needs; the bulk stores must have read them too:
+                // then the lane partials may reuse this warp's tile buffer
+                if (lane == 0) bulk_wait_read_all();
+                __syncthreads();
+                combine_lanes<NS>(M, sm, W, W.buf, acc, curb, b0, lane, node_acc, err);
+            } else {
+                // more passes follow and still need the tiles: flush this lane's last segment
+                if (curb >= 0) {
+                    float spill[NK];
+#pragma unroll
+                    for (int k = 0; k < NK; ++k) spill[k] = acc[k];
+                    flush_partial(sm.table, spill, __ldg(&M.em[sm.binkey[b0 + curb]]), sm.cslot[curb], node_acc, &err);
+                }
+                __syncthreads();
             }
         }
         __syncwarp();
     }
-    // ---- 5. flush the CTA node table --------------------------------------------------
+    // every bulk store of this warp must be complete before the CTA exits
+    if (lane == 0) bulk_wait_all();
+    // ---- 9. flush the CTA node table ----------------------------------------------------
     __syncthreads();
     for (int i = threadIdx.x; i < NT * NQ; i += kTPB) {
         const int s = i / NQ, q = i - (i / NQ) * NQ;
@@ -572,7 +934,11 @@ static cudaError_t launch_step_ns(const DevMesh& m, const DevState& s, const flo
     }
     const int64_t grid = (s.n + kRange - 1) / kRange;
     if (grid == 0) return cudaSuccess;
-    pdf_step_kernel<NS><<<(unsigned)grid, kTPB, smem, st>>>(m, s, fields, p, node_acc, status);
+    // bulk copies need 16-byte aligned rows: every base pointer and the psi row stride
+    auto al = [](const void* q) { return ((uintptr_t)q & 15u) == 0; };
+    const int use_bulk = al(s.x) && al(s.y) && al(s.u) && al(s.v) && al(s.w) && al(s.om) && al(s.psi) && al(s.elem) &&
+                         al(s.pid) && (s.cap % 4 == 0);
+    pdf_step_kernel<NS><<<(unsigned)grid, kTPB, smem, st>>>(m, s, fields, p, node_acc, status, use_bulk);
     return cudaGetLastError();
 }
 
@@ -614,7 +980,8 @@ __global__ void particles_init_kernel(const __grid_constant__ DevMesh M, const _
         if (px >= M.x1) px = M.periodic ? M.x0 : nextafterf(M.x1, -CUDART_INF_F);
         if (py >= M.y1) py = nextafterf(M.y1, -CUDART_INF_F);
         int hops = 0;
-        int ne = locate_walk(M, e, px, py, hops);
+        float lw[3];
+        int ne = locate_walk(M, e, px, py, hops, lw);
         if (ne < 0) { err |= kErrLost; ne = e; }
         const float4 X2 = __ldg(&M.ex[ne]), Y2 = __ldg(&M.ey[ne]);
         const int4 V = __ldg(&M.ev[ne]);
@@ -625,8 +992,8 @@ __global__ void particles_init_kernel(const __grid_constant__ DevMesh M, const _
         for (int f = 0; f < 5; ++f)
             Fi[f] = fmaf(m0, __ldg(&init[(size_t)V.x * 8 + f]), fmaf(m1, __ldg(&init[(size_t)V.y * 8 + f]), m2 * __ldg(&init[(size_t)V.z * 8 + f])));
         float z0, z1, z2, z3;
-        box_muller(a.z, a.w, z0, z1);
-        box_muller(b.x, b.y, z2, z3);
+        box_muller_accurate(a.z, a.w, z0, z1);
+        box_muller_accurate(b.x, b.y, z2, z3);
         const uint32_t ew[6] = {b.z, b.w, c.x, c.y, c.z, c.w};
         float sum = 0.0f;
         for (int k = 0; k < m_erlang; ++k) sum += -logf(u01(ew[k]));

@@ -122,6 +122,14 @@ extern "C" int lpdf_pdf_step_static(const lpdf_mesh* mesh, const lpdf_params* pa
             lpdf_set_error(LPDF_ERR_NONFINITE, "non-finite particle state");
             return LPDF_ERR_NONFINITE;
         }
+        if (h[0] & kErrTimeout) {
+            lpdf_set_error(LPDF_ERR_CUDA, "a bulk-copy wait in the step kernel timed out");
+            return LPDF_ERR_CUDA;
+        }
+        if (h[0] & kErrCheck) {
+            lpdf_set_error(LPDF_ERR_CUDA, "an internal consistency check of the step kernel failed");
+            return LPDF_ERR_CUDA;
+        }
         if (h[0] & kErrOverflow) {
             lpdf_set_error(LPDF_ERR_OVERFLOW, "fixed-point moment range exceeded");
             return LPDF_ERR_OVERFLOW;

@@ -34,7 +34,7 @@ MAX_SCALARS = 4
 EXPORTS = ("lpdf_params_default", "lpdf_last_error", "lpdf_version", "lpdf_mesh_load", "lpdf_mesh_free",
            "lpdf_mesh_info", "lpdf_mesh_neighbors", "lpdf_mesh_masters", "lpdf_ctx_create", "lpdf_ctx_free",
            "lpdf_ctx_set_params", "lpdf_ctx_size", "lpdf_particles_init", "lpdf_set_state", "lpdf_get_state",
-           "lpdf_pdf_step", "lpdf_status", "lpdf_grid_statistics", "lpdf_pdf_step_static")
+           "lpdf_pdf_step", "lpdf_status", "lpdf_grid_statistics", "lpdf_pdf_step_static", "lpdf_sort")
 
 
 class LpdfError(RuntimeError):
@@ -50,7 +50,7 @@ class Params(ctypes.Structure):
                 ("lid_u", ctypes.c_double), ("seed", ctypes.c_uint64), ("ns", ctypes.c_int32),
                 ("n_sources", ctypes.c_int32), ("src_x", ctypes.c_float * MAX_SOURCES),
                 ("src_y", ctypes.c_float * MAX_SOURCES), ("src_r", ctypes.c_float * MAX_SOURCES),
-                ("src_alpha", ctypes.c_int32 * MAX_SOURCES)]
+                ("src_alpha", ctypes.c_int32 * MAX_SOURCES), ("sort_every", ctypes.c_int32)]
 
 
 _lib = None
@@ -86,6 +86,7 @@ def lib():
     L.lpdf_set_state.argtypes = [vp, i64] + [vp] * 9 + [ctypes.c_int, vp]
     L.lpdf_get_state.argtypes = [vp] + [vp] * 9 + [ctypes.c_int, vp]
     L.lpdf_pdf_step.argtypes = [vp, vp, u64, vp]
+    L.lpdf_sort.argtypes = [vp, vp]
     L.lpdf_status.argtypes = [vp, vp, vp]
     L.lpdf_grid_statistics.argtypes = [vp, vp, ctypes.c_int, vp]
     L.lpdf_pdf_step_static.argtypes = [vp, vp, i64] + [vp] * 9 + [vp, u64, vp, vp, vp]
@@ -240,6 +241,10 @@ class Context:
         if not device:
             torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
         return out
+
+    def sort(self, stream=None):
+        """lpdf_sort: re-bucket the particles by element (deterministic order)."""
+        _check(lib().lpdf_sort(self.h, _stream(stream)))
 
     def pdf_step(self, node_fields, step: int, stream=None):
         _check(lib().lpdf_pdf_step(self.h, _ptr(node_fields), int(step), _stream(stream)))

@@ -180,3 +180,48 @@ def test_lost_particle_is_reported_not_faulted(torch_cuda):
     st.elem[5] = e_true
     g, S, rc, status = gc.gpu_step(ctx, Fd, st, 1)
     assert rc == lpdf.LPDF_OK
+
+
+def test_sort_rebuckets_deterministically(torch_cuda):
+    """lpdf_sort: a permutation of the particles (every field travels with its pid), ordered by
+    element and, within an element, by previous position."""
+    wk = wl.channel_small()
+    mesh, gm, om, params, F, Fd, ctx, npe = _setup(wk, n_per_elem=12)
+    st = wl.synthetic_state(mesh, npe, wk.ns, seed=41)
+    perm = np.random.default_rng(1).permutation(st.n)
+    sp = wl.State(*(np.ascontiguousarray(getattr(st, k)[perm]) for k in gc.FIELDS),
+                  np.ascontiguousarray(st.psi[:, perm]), st.elem[perm], st.pid[perm])
+    ctx.set_state(gc.torch_state(sp))
+    ctx.sort()
+    g = gc.host_state(ctx.get_state(), wk.ns)
+    assert np.all(np.diff(g.elem) >= 0)
+    # within an element: previous positions ascending
+    where = {int(p): i for i, p in enumerate(sp.pid)}
+    prev = np.array([where[int(p)] for p in g.pid])
+    same = g.elem[1:] == g.elem[:-1]
+    assert np.all(prev[1:][same] > prev[:-1][same])
+    idx = np.array([where[int(p)] for p in g.pid])
+    for k in gc.FIELDS:
+        assert np.array_equal(getattr(g, k), getattr(sp, k)[idx])
+    assert np.array_equal(g.psi, sp.psi[:, idx])
+
+
+def test_step_with_periodic_rebucketing_matches_step_without(torch_cuda):
+    """sort_every only changes the order: per-pid state after 3 steps is bit-identical."""
+    wk = wl.channel_small()
+    mesh, gm, om, params, F, Fd, ctx, npe = _setup(wk, n_per_elem=10)
+    st = wl.synthetic_state(mesh, npe, wk.ns, seed=42)
+    p2 = lpdf.params_for(wk)
+    p2.sort_every = 2
+    ctx2 = lpdf.Context(gm, p2, st.n)
+    ctx.set_state(gc.torch_state(st))
+    ctx2.set_state(gc.torch_state(st))
+    for step in range(3):
+        ctx.pdf_step(Fd, step)
+        ctx2.pdf_step(Fd, step)
+    a = gc.host_state(ctx.get_state(), wk.ns)
+    b = gc.host_state(ctx2.get_state(), wk.ns)
+    ia, ib = np.argsort(a.pid), np.argsort(b.pid)
+    for k in gc.FIELDS:
+        assert np.array_equal(getattr(a, k)[ia], getattr(b, k)[ib])
+    assert np.array_equal(a.elem[ia], b.elem[ib])
