@@ -79,6 +79,11 @@ typedef struct {
     int32_t src_alpha[LPDF_MAX_SOURCES]; /* scalar index set to 1 inside source disc s */
     int32_t sort_every; /* > 0: lpdf_pdf_step re-buckets the particles by element (lpdf_sort)
                            before every sort_every-th step; 0: only on explicit lpdf_sort calls */
+    int32_t gmodel;         /* lpdf_elliptic_relax_solve: 0 elliptic relaxation, 1 simplified Langevin model */
+    int32_t pressure_solve; /* lpdf_elliptic_relax_solve: 1 solve for the mean pressure,
+                               0 gradient = (dpdx0, dpdy0) only */
+    int32_t reserved_;
+    double dpdx0, dpdy0;    /* fixed mean pressure gradient added to the solved one (channel: -1, 0) */
 } lpdf_params;
 
 typedef struct lpdf_mesh lpdf_mesh;
@@ -86,7 +91,7 @@ typedef struct lpdf_ctx lpdf_ctx;
 
 /* Fills *p with C3 = 5, C4 = 0.25, Cphi = 2, C0 = 2.1, Comega1 = 0.5, Comega2 = 0.73,
  * CL = 0.134, Ceta = 72, nu = 1/180, dt = 1e-3, ns = 1, no sources, seed = 1, lid_u = 0,
- * sort_every = 0. */
+ * sort_every = 0, gmodel = 0, pressure_solve = 0, dpdx0 = dpdy0 = 0. */
 void lpdf_params_default(lpdf_params* p);
 
 /* Message of the calling thread's last error ("" if none). Owned by the library. */
@@ -198,6 +203,35 @@ int lpdf_status(lpdf_ctx* ctx, int64_t* out, void* stream);
  * Periodic partner nodes hold identical values.
  * ------------------------------------------------------------------------------------- */
 int lpdf_grid_statistics(lpdf_ctx* ctx, double* out, int raw, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * lpdf_elliptic_relax_solve -- the gridpoint side: node fields for lpdf_pdf_step from gridpoint
+ * statistics (Introduction, item ii: Eulerian quantities are solved on the grid). sync (the
+ * conjugate-gradient convergence tests read residual norms back to the host).
+ *   stats   device, n_nodes x (11 + 2 ns) FP64 as lpdf_grid_statistics(raw = 0) writes them
+ *   fields  device out, n_nodes x nfp FP32 (columns LPDF_F_*)
+ *   tol     relative residual of each conjugate gradient: |r| <= tol |r_0|
+ *   maxit   iteration cap of each conjugate gradient
+ *   iters   host out (may be NULL), 2 ints: iterations of the elliptic-relaxation solve (its
+ *           four components at once) and of the pressure solve (0 when not run)
+ * With P1 finite elements on the mesh (periodic partners merged into one unknown):
+ *   gradients of <U_i> recovered at the nodes by area-weighted averaging of element gradients,
+ *   Laplacians as the recovered divergence of the recovered gradient; k = <u_i u_i>/2,
+ *   eps = k <omega> (the paragraph before Eq. 5); S_omega = C_omega2 - C_omega1 P/eps with
+ *   P = -<u_i u_j> d<U_i>/dx_j (Eq. 6); G_ij (the paragraph after Eq. 4): gmodel 0 solves
+ *   (M + L^2 K) wp = M (-3/4 C0 eps delta) with wp_ij = -4.5 eps n_i n_j on wall nodes,
+ *   L = CL max(k^1.5/eps, Ceta nu^0.75/eps^0.25), then G_ij = (wp_ij - eps delta_ij/2)/k and
+ *   C0 eps = max(0, -2/3 (eps + <u_i u_j> G_ij)); gmodel 1 gives G_ij = -(1/2 + 3/4 C0) <omega>
+ *   delta_ij and C0 eps. pressure_solve 1 solves the weak form of lap p = -d_i d_j (<U_i><U_j> +
+ *   <u_i u_j>) (natural boundary condition, zero mean) and adds (dpdx0, dpdy0) to its
+ *   recovered gradient. All arithmetic is FP64; the output is rounded to FP32.
+ * The first call on a mesh builds and uploads its finite-element tables (kept until
+ * lpdf_mesh_free). Calls on the same mesh share its scratch: serialise them.
+ * Errors: LPDF_ERR_ARG, LPDF_ERR_UNSUPPORTED (ns), LPDF_ERR_CG_NOCONV (iters still filled in),
+ * LPDF_ERR_CUDA.
+ * ------------------------------------------------------------------------------------- */
+int lpdf_elliptic_relax_solve(const lpdf_mesh* mesh, const lpdf_params* params, const double* stats,
+                              float* fields, double tol, int32_t maxit, int32_t* iters, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * lpdf_pdf_step_static -- the same particle step as lpdf_pdf_step for callers that cannot

@@ -269,6 +269,9 @@ int lpdf_mesh_load(const double* node_xy, int32_t n_nodes, const int32_t* tri, i
     for (int e = 0; e < n_tri; ++e)
         for (int k = 0; k < 3; ++k) m->nbr[3 * e + k] = en[4 * e + k];
     m->master = std::move(master);
+    m->node_xy.assign(node_xy, node_xy + 2 * (size_t)n_nodes);
+    m->tri.assign(tri, tri + 3 * (size_t)n_tri);
+    m->tag.assign(edge_tag, edge_tag + 3 * (size_t)n_tri);
     *out = m;
     return LPDF_OK;
 }
@@ -277,6 +280,7 @@ void lpdf_mesh_free(lpdf_mesh* mesh)
 {
     if (!mesh) return;
     free_mesh_device(mesh->d);
+    fem_free(mesh->fem);
     delete mesh;
 }
 
@@ -481,6 +485,43 @@ int lpdf_grid_statistics(lpdf_ctx* c, double* out, int raw, void* stream)
 {
     if (!c || !out) return fail(LPDF_ERR_ARG, "grid_statistics: NULL argument");
     CUDA_TRY(launch_grid_statistics(c->mesh->d, c->ns, c->node_acc, out, raw ? 1 : 0, (cudaStream_t)stream));
+    return LPDF_OK;
+}
+
+
+int lpdf_elliptic_relax_solve(const lpdf_mesh* mesh, const lpdf_params* params, const double* stats,
+                              float* fields, double tol, int32_t maxit, int32_t* iters, void* stream)
+{
+    if (!mesh || !params || !stats || !fields) return fail(LPDF_ERR_ARG, "elliptic_relax_solve: NULL argument");
+    if (params->ns < 1 || params->ns > LPDF_MAX_SCALARS)
+        return fail(LPDF_ERR_UNSUPPORTED, "elliptic_relax_solve: ns = %d outside 1..%d", params->ns,
+                    LPDF_MAX_SCALARS);
+    if (params->gmodel < 0 || params->gmodel > 1 || params->pressure_solve < 0 || params->pressure_solve > 1)
+        return fail(LPDF_ERR_ARG, "elliptic_relax_solve: gmodel = %d, pressure_solve = %d", params->gmodel,
+                    params->pressure_solve);
+    if (!(tol > 0.0) || maxit < 1)
+        return fail(LPDF_ERR_ARG, "elliptic_relax_solve: tol = %g, maxit = %d", tol, maxit);
+    {
+        std::lock_guard<std::mutex> lock(mesh->fem_mutex);
+        if (!mesh->fem) {
+            Fem* F = nullptr;
+            cudaError_t e = fem_build(mesh->node_xy.data(), mesh->d.n_nodes, mesh->tri.data(), mesh->d.n_tri,
+                                      mesh->tag.data(), mesh->master, &F);
+            if (e != cudaSuccess)
+                return fail(LPDF_ERR_CUDA, "elliptic_relax_solve: table upload: %s", cudaGetErrorString(e));
+            mesh->fem = F;
+        }
+    }
+    int it[2] = {0, 0};
+    const cudaError_t e = node_fields_solve(*mesh->fem, stats, *params, fields, tol, maxit, it, (cudaStream_t)stream);
+    if (iters) {
+        iters[0] = it[0];
+        iters[1] = it[1];
+    }
+    if (e == cudaErrorNotReady)
+        return fail(LPDF_ERR_CG_NOCONV, "elliptic_relax_solve: no convergence to %g in %d iterations (%d, %d)", tol,
+                    maxit, it[0], it[1]);
+    if (e != cudaSuccess) return fail(LPDF_ERR_CUDA, "elliptic_relax_solve: %s", cudaGetErrorString(e));
     return LPDF_OK;
 }
 

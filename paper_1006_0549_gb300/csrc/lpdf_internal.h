@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <vector>
 
 #include "lpdf.h"
@@ -73,6 +74,42 @@ struct SortScratch {
 cudaError_t launch_sort(const DevMesh& m, const DevState& s, int ns, const DevState& dst, SortScratch& w,
                         unsigned long long* status, cudaStream_t st);
 
+// P1 finite-element tables of the gridpoint solve (lpdf_solve.cu), built once per mesh.
+// DOFs are the geometric nodes with periodic partners merged (numbered in node order).
+struct Fem {
+    static constexpr int kWorkPerDof = 56;     // FP64 scratch per DOF
+    static constexpr int kDotBlocks = 1024;    // partial sums of one dot product
+    int ndof = 0, nnz = 0, E = 0, N = 0;
+    int* dof = nullptr;          // geometric node -> DOF
+    int* dof_node = nullptr;     // DOF -> its master node (statistics row)
+    int* edof = nullptr;         // 3 DOFs per element
+    double* area = nullptr;      // per element
+    double* grad = nullptr;      // 6 per element: grad of the 3 shape functions
+    int* de_ptr = nullptr;       // DOF -> incident (element, corner) pairs e*3 + a (CSR)
+    int* de_el = nullptr;
+    double* darea = nullptr;     // sum of the areas of the incident pairs
+    int* row = nullptr;          // DOF x DOF matrix pattern (CSR)
+    int* col = nullptr;
+    int* cptr = nullptr;         // CSR entry -> element-matrix contributions e*9 + a*3 + b
+    int* cel = nullptr;
+    double* Mval = nullptr;      // consistent mass matrix
+    double* Kval = nullptr;      // stiffness matrix (unit coefficient)
+    double* Aval = nullptr;      // M + L^2 K of the current solve
+    unsigned char* wall = nullptr;
+    double* normal = nullptr;    // inward unit normal per wall DOF
+    double* work = nullptr;      // kWorkPerDof * ndof + 16 * E doubles
+    double* part = nullptr;      // 4 * kDotBlocks
+    double* scal = nullptr;      // CG scalars (device)
+    double* scal_host = nullptr; // pinned copy
+};
+cudaError_t fem_build(const double* node_xy, int n_nodes, const int32_t* tri, int n_tri, const int32_t* tag,
+                      const std::vector<int32_t>& master, Fem** out);
+void fem_free(Fem* F);
+// statistics (n_nodes x (11 + 2 ns), lpdf_grid_statistics raw = 0) -> node fields; iters[2];
+// cudaErrorNotReady when a CG did not converge within maxit
+cudaError_t node_fields_solve(const Fem& F, const double* stats, const lpdf_params& P, float* out, double tol,
+                              int maxit, int* iters, cudaStream_t st);
+
 StepParams make_step_params(const lpdf_params& p, const struct ::lpdf_mesh* m, uint64_t step);
 // records the calling thread's error message (lpdf_last_error) and returns `code`
 int lpdf_set_error(int code, const char* fmt, ...);
@@ -85,8 +122,12 @@ struct lpdf_mesh {
     lpdf::DevMesh d;
     std::vector<int32_t> nbr;      // host copy, 3 per element
     std::vector<int32_t> master;   // host copy
+    std::vector<double> node_xy;   // host copies of the input (for the gridpoint solve)
+    std::vector<int32_t> tri, tag;
     double box[4];
     int device;
+    mutable std::mutex fem_mutex;
+    mutable lpdf::Fem* fem = nullptr;   // built by the first lpdf_elliptic_relax_solve call
 };
 
 struct lpdf_ctx {

@@ -34,7 +34,8 @@ MAX_SCALARS = 4
 EXPORTS = ("lpdf_params_default", "lpdf_last_error", "lpdf_version", "lpdf_mesh_load", "lpdf_mesh_free",
            "lpdf_mesh_info", "lpdf_mesh_neighbors", "lpdf_mesh_masters", "lpdf_ctx_create", "lpdf_ctx_free",
            "lpdf_ctx_set_params", "lpdf_ctx_size", "lpdf_particles_init", "lpdf_set_state", "lpdf_get_state",
-           "lpdf_pdf_step", "lpdf_status", "lpdf_grid_statistics", "lpdf_pdf_step_static", "lpdf_sort")
+           "lpdf_pdf_step", "lpdf_status", "lpdf_grid_statistics", "lpdf_pdf_step_static", "lpdf_sort",
+           "lpdf_elliptic_relax_solve")
 
 
 class LpdfError(RuntimeError):
@@ -50,7 +51,9 @@ class Params(ctypes.Structure):
                 ("lid_u", ctypes.c_double), ("seed", ctypes.c_uint64), ("ns", ctypes.c_int32),
                 ("n_sources", ctypes.c_int32), ("src_x", ctypes.c_float * MAX_SOURCES),
                 ("src_y", ctypes.c_float * MAX_SOURCES), ("src_r", ctypes.c_float * MAX_SOURCES),
-                ("src_alpha", ctypes.c_int32 * MAX_SOURCES), ("sort_every", ctypes.c_int32)]
+                ("src_alpha", ctypes.c_int32 * MAX_SOURCES), ("sort_every", ctypes.c_int32),
+                ("gmodel", ctypes.c_int32), ("pressure_solve", ctypes.c_int32), ("reserved_", ctypes.c_int32),
+                ("dpdx0", ctypes.c_double), ("dpdy0", ctypes.c_double)]
 
 
 _lib = None
@@ -90,6 +93,7 @@ def lib():
     L.lpdf_status.argtypes = [vp, vp, vp]
     L.lpdf_grid_statistics.argtypes = [vp, vp, ctypes.c_int, vp]
     L.lpdf_pdf_step_static.argtypes = [vp, vp, i64] + [vp] * 9 + [vp, u64, vp, vp, vp]
+    L.lpdf_elliptic_relax_solve.argtypes = [vp, vp, vp, vp, ctypes.c_double, i32, vp, vp]
     for name in EXPORTS:
         f = getattr(L, name)
         if f.restype is ctypes.c_int or (name not in ("lpdf_params_default", "lpdf_mesh_free", "lpdf_ctx_free",
@@ -168,6 +172,14 @@ class Mesh:
         box = np.empty(4)
         _check(lib().lpdf_mesh_info(self.h, ctypes.byref(n), ctypes.byref(e), _ptr(box)))
         return n.value, e.value, tuple(box)
+
+    def elliptic_relax_solve(self, params: Params, stats, out, tol: float = 1e-10, maxit: int = 20000, stream=None):
+        """lpdf_elliptic_relax_solve: node fields (out, n_nodes x nfp float32, CUDA) from gridpoint
+        statistics (stats, n_nodes x (11 + 2 ns) float64, CUDA). Returns the CG iteration counts."""
+        it = np.zeros(2, dtype=np.int32)
+        _check(lib().lpdf_elliptic_relax_solve(self.h, ctypes.byref(params), _ptr(stats), _ptr(out), float(tol),
+                                               int(maxit), _ptr(it), _stream(stream)))
+        return int(it[0]), int(it[1])
 
     def __del__(self):
         try:

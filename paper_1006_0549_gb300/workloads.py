@@ -252,6 +252,59 @@ def synthetic_node_fields(mesh: Mesh, ns: int, seed: int, noise: float = 0.05) -
     return F.astype(np.float32)
 
 
+def synthetic_statistics(mesh: Mesh, ns: int, seed: int, noise: float = 0.02) -> np.ndarray:
+    """(N, 11 + 2 ns) float64 gridpoint statistics in the layout of the statistics call (raw = 0):
+    S0, <U>, <V>, <W>, <uu>, <uv>, <uw>, <vv>, <vw>, <ww>, <omega>, <phi_a> (ns), <phi_a'^2> (ns).
+
+    Smooth wall-bounded profiles (channel: log-law mean, near-wall peak of the normal stresses,
+    antisymmetric shear stress; cavity: a lid-driven vortex shape) with a little seeded noise,
+    positive-definite stress tensors and positive frequency; periodic duplicates equal."""
+    rng = np.random.default_rng(seed)
+    N = mesh.n_nodes
+    x, y = mesh.node_xy[:, 0], mesh.node_xy[:, 1]
+    st = np.zeros((N, 11 + 2 * ns))
+    st[:, 0] = 50.0 * (1.0 + 0.1 * rng.random(N))
+    if mesh.kind == "channel":
+        yw = np.minimum(y, 2.0 - y)
+        sgn = np.where(y < 1.0, 1.0, -1.0)
+        st[:, 1] = _loglaw(yw) / 20.0
+        st[:, 2] = 0.05 * np.sin(x) * np.sin(np.pi * y / 2.0)
+        bump = np.exp(-((180.0 * yw - 15.0) / 30.0) ** 2)
+        uu = 0.5 + 3.0 * bump
+        vv = 0.3 + 0.5 * bump
+        ww = 0.4 + 1.0 * bump
+        uv = -0.4 * sgn * np.sqrt(uu * vv) * np.tanh(10.0 * yw)
+        om = 1.0 / (0.3 * 0.41 * np.maximum(yw, 10.0 / 180.0)) / 20.0 + 1.0
+    else:
+        st[:, 1] = (y ** 3) * (1.0 - 0.5 * np.cos(2 * np.pi * x))
+        st[:, 2] = -0.2 * np.sin(np.pi * x) * np.sin(np.pi * y)
+        uu = 0.02 * (1.0 + y)
+        vv = 0.015 * (1.0 + x * y)
+        ww = 0.01 * (1.5 - 0.5 * x)
+        uv = -0.3 * np.sqrt(uu * vv) * np.sin(np.pi * x) * y
+        om = 1.0 + 2.0 * np.exp(-10 * np.minimum.reduce([x, 1 - x, y, 1 - y]))
+    st[:, 3] = 0.01 * rng.standard_normal(N)
+    st[:, 1] += noise * rng.standard_normal(N) * np.abs(st[:, 1]).max()
+    st[:, 2] += noise * 0.1 * rng.standard_normal(N)
+    st[:, 4] = uu * (1.0 + noise * rng.standard_normal(N))
+    st[:, 5] = uv
+    st[:, 6] = 0.05 * np.sqrt(uu * ww) * rng.standard_normal(N) * noise
+    st[:, 7] = vv * (1.0 + noise * rng.standard_normal(N))
+    st[:, 8] = 0.05 * np.sqrt(vv * ww) * rng.standard_normal(N) * noise
+    st[:, 9] = ww * (1.0 + noise * rng.standard_normal(N))
+    st[:, 10] = om * (1.0 + noise * rng.standard_normal(N))
+    for a in range(ns):
+        st[:, 11 + a] = np.clip(0.1 + 0.05 * rng.standard_normal(N), 0.0, 1.0)
+        st[:, 11 + ns + a] = 0.01 * rng.random(N)
+    if mesh.period_x > 0.0:
+        right = np.nonzero(x == mesh.period_x)[0]
+        left = np.nonzero(x == 0.0)[0]
+        ly = {float(y[i]): i for i in left}
+        for i in right:
+            st[i] = st[ly[float(y[i])]]
+    return st
+
+
 def node_init_fields(mesh: Mesh, sigma: float = 1.0, re_tau: float = 180.0) -> np.ndarray:
     """(N, 8) float32 initial-condition fields per node: <U>, <V>, <W>, sigma_u, <omega>, pad.
 
