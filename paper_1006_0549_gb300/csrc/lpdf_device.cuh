@@ -1,0 +1,337 @@
+// Device helpers shared by the kernels of liblpdf (sm_103a): counter-based normals, exact
+// orientation and point location on the triangle mesh, interpolation, the CTA node table of
+// 64-bit fixed-point moment sums, and bulk-copy (TMA) / mbarrier wrappers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include "lpdf_internal.h"
+
+namespace lpdf {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): 10 rounds of two 32x32->64 products
+// with the round multipliers, the high words xored with the other counter words and the round
+// key, the key advanced by the Weyl increments between rounds.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// (w + 1/2) 2^-32, rounded to FP32
+__device__ __forceinline__ float u01(uint32_t w) { return fmaf((float)w, 0x1p-32f, 0x1p-33f); }
+
+// Box-Muller (1958) on the special-function unit: r^2 = -2 ln u0 (lg2.approx: absolute error
+// ~2^-22 in log2), r = r^2 * rsqrt(r^2), angle theta = 2 pi u1 - pi in [-pi, pi), where the SFU
+// sine and cosine are accurate to ~2^-21.4 absolute; cos(theta + pi) = -cos(theta) and
+// sin(theta + pi) = -sin(theta), so z0 = r cos(2 pi u1), z1 = r sin(2 pi u1) as in the oracle.
+__device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float& z0, float& z1)
+{
+    const float r2 = -2.0f * __logf(u01(w0));
+    const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
+    const float th = fmaf(6.28318530717958648f, u01(w1), -3.14159265358979324f);
+    float sn, cs;
+    __sincosf(th, &sn, &cs);
+    z0 = -r * cs;
+    z1 = -r * sn;
+}
+
+// accurate variant for the initialisation kernel (not on the hot path)
+__device__ __forceinline__ void box_muller_accurate(uint32_t w0, uint32_t w1, float& z0, float& z1)
+{
+    const float r = sqrtf(-2.0f * logf(u01(w0)));
+    float sn, cs;
+    sincospif(2.0f * u01(w1), &sn, &cs);
+    z0 = r * cs;
+    z1 = r * sn;
+}
+
+// ------------------------------------------------------------------------------------------
+// Exact orientation (rare fallback): sign of (ax-cx)(by-cy) - (ay-cy)(bx-cx) by exact FP64
+// expansion arithmetic (Shewchuk 1997: two-sum, FMA two-product, grow-expansion).
+// ------------------------------------------------------------------------------------------
+static __device__ __noinline__ int orient_exact(double ax, double ay, double bx, double by, double cx, double cy)
+{
+    double t[16];
+    int nt = 0;
+    auto tsum = [](double a, double b, double& s, double& e) {
+        s = a + b;
+        const double bv = s - a, av = s - bv;
+        e = (a - av) + (b - bv);
+    };
+    double d[8];
+    tsum(ax, -cx, d[0], d[1]);
+    tsum(by, -cy, d[2], d[3]);
+    tsum(ay, -cy, d[4], d[5]);
+    tsum(bx, -cx, d[6], d[7]);
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            double p = d[i] * d[2 + j];
+            t[nt++] = p;
+            t[nt++] = fma(d[i], d[2 + j], -p);
+            double q = d[4 + i] * d[6 + j];
+            t[nt++] = -q;
+            t[nt++] = -fma(d[4 + i], d[6 + j], -q);
+        }
+    double h[17];
+    int nh = 0;
+    for (int i = 0; i < nt; ++i) {
+        double q = t[i];
+        int m = 0;
+        for (int k = 0; k < nh; ++k) {
+            double s, e;
+            tsum(q, h[k], s, e);
+            if (e != 0.0) h[m++] = e;
+            q = s;
+        }
+        if (q != 0.0) h[m++] = q;
+        nh = m;
+    }
+    if (nh == 0) return 0;
+    return h[nh - 1] > 0.0 ? 1 : -1;
+}
+
+// orientation of p relative to directed edge a->b, (bx-ax)(py-ay) - (by-ay)(px-ax): the FP32
+// value (Kahan's FMA determinant: at most 1.5 ulp of the result beyond the rounding of the four
+// differences) and its exact sign. Filter: every rounding above is bounded by 3.5 eps32 (|t1| +
+// |t2|) (eps32 = 2^-24); 4e-7 (~6.7 eps32) also covers the rounding of the bound. Undecided
+// cases go to the exact FP64 expansion.
+__device__ __forceinline__ float orient_sign(float ax, float ay, float bx, float by, float px, float py, int& sgn)
+{
+    const float dx1 = __fsub_rn(bx, ax), dy1 = __fsub_rn(by, ay);
+    const float dx2 = __fsub_rn(px, ax), dy2 = __fsub_rn(py, ay);
+    const float w = dy1 * dx2;
+    const float e = fmaf(-dy1, dx2, w);
+    const float f = fmaf(dx1, dy2, -w);
+    const float val = f + e;
+    const float detsum = fmaf(fabsf(dx1), fabsf(dy2), fabsf(w));
+    const float bound = 4.0e-7f * detsum;
+    if (detsum > 1e-25f && val > bound) { sgn = 1; return val; }
+    if (detsum > 1e-25f && -val > bound) { sgn = -1; return val; }
+    sgn = orient_exact((double)bx, (double)by, (double)px, (double)py, (double)ax, (double)ay);
+    return val;
+}
+
+// an edge a->b of a CCW triangle owns the points on it iff it is a "top-left" edge
+__device__ __forceinline__ bool edge_owns(float ax, float ay, float bx, float by)
+{
+    return (by < ay) || (by == ay && bx > ax);
+}
+
+// One test of the barycentric neighbour walk at element e: true if e is the unique owner of
+// (px, py) (exact inside tests in the element's own frame; lam = its barycentrics, from the
+// orientation values); otherwise `next` = the neighbour across the exit edge (the edge with the
+// most negative orientation value, the lowest local index on ties), -1 for a wall. In a
+// periodic image frame the test only navigates.
+__device__ __forceinline__ bool walk_test(const DevMesh& M, int e, float px, float py, float lam[3], int& next)
+{
+    const float4 X = __ldg(&M.ex[e]);
+    const float4 Y = __ldg(&M.ey[e]);
+    const int4 N = __ldg(&M.en[e]);
+    const float xs[3] = {X.x, X.y, X.z}, ys[3] = {Y.x, Y.y, Y.z};
+    const int nb[3] = {N.x, N.y, N.z};
+    // nearest periodic image of the point relative to this element (elements are much
+    // smaller than the period, so |centroid - x| > period/2 means the other image)
+    float sh = 0.0f;
+    if (M.periodic) {
+        const float d = X.w - px;
+        if (fabsf(d) > 0.5f * M.period) sh = copysignf(M.period, d);
+    }
+    int best = -1;
+    float bestv = 0.0f;
+    if (sh == 0.0f) {
+        bool all_in = true;
+        float vv[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int a = k, b = (k + 1) % 3;
+            int s;
+            vv[k] = orient_sign(xs[a], ys[a], xs[b], ys[b], px, py, s);
+            const bool in = s > 0 || (s == 0 && edge_owns(xs[a], ys[a], xs[b], ys[b]));
+            if (!in) {
+                all_in = false;
+                if (best < 0 || vv[k] < bestv) { best = k; bestv = vv[k]; }
+            }
+        }
+        if (all_in) {
+            // edge k = (v_k, v_k+1) is opposite vertex k+2: lambda_{k+2} = orient_k / (2 area)
+            lam[2] = vv[0] * Y.w;
+            lam[0] = vv[1] * Y.w;
+            lam[1] = vv[2] * Y.w;
+            return true;
+        }
+    } else {
+        const float qx = px + sh;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int a = k, b = (k + 1) % 3;
+            const float val = (xs[b] - xs[a]) * (py - ys[a]) - (ys[b] - ys[a]) * (qx - xs[a]);
+            const bool in = (val > 0.0f) || nb[k] < 0;
+            if (!in && (best < 0 || val < bestv)) { best = k; bestv = val; }
+        }
+        if (best < 0) best = (N.w & 1) ? 0 : (N.w & 2) ? 1 : (N.w & 4) ? 2 : 0;
+    }
+    next = best == 0 ? N.x : (best == 1 ? N.y : N.z);
+    return false;
+}
+
+// The whole walk from element e: the owner of (px, py) (and its barycentrics), -1 on a wall
+// exit, -2 at the hop cap.
+__device__ __forceinline__ int locate_walk(const DevMesh& M, int e, float px, float py, int& hops, float lam[3])
+{
+#pragma unroll 1
+    for (int h = 0; h <= kHopCap; ++h) {
+        int next;
+        if (walk_test(M, e, px, py, lam, next)) { hops = h; return e; }
+        if (next < 0) { hops = h; return -1; }
+        e = next;
+    }
+    hops = kHopCap + 1;
+    return -2;
+}
+
+// a*d - b*c with one rounding error bound of 1.5 ulp (Kahan's FMA determinant)
+__device__ __forceinline__ float det2(float a, float b, float c, float d)
+{
+    const float w = b * c;
+    const float e = fmaf(-b, c, w);
+    const float f = fmaf(a, d, -w);
+    return f + e;
+}
+
+__device__ __forceinline__ void barycentric(const float4& X, const float4& Y, float px, float py, float& l0,
+                                            float& l1, float& l2)
+{
+    l0 = det2(X.y - px, Y.y - py, X.z - px, Y.z - py) * Y.w;
+    l1 = det2(X.z - px, Y.z - py, X.x - px, Y.x - py) * Y.w;
+    l2 = det2(X.x - px, Y.x - py, X.y - px, Y.y - py) * Y.w;
+}
+
+__device__ __forceinline__ bool in_source(float px, float py, float sx, float sy, float r)
+{
+    const float dx = __fsub_rn(px, sx), dy = __fsub_rn(py, sy);
+    return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) < __fmul_rn(r, r);
+}
+
+// ------------------------------------------------------------------------------------------
+// CTA node table: 64-bit fixed-point moment sums keyed by statistics node. A lookup probes at
+// most kProbe slots; a node that finds no slot goes straight to the global accumulators.
+// ------------------------------------------------------------------------------------------
+constexpr int kProbe = 16;
+
+template <int NQ, int NT>
+struct NodeTable {
+    int key[NT];
+    unsigned long long acc[NT][NQ];
+};
+
+template <int NQ, int NT>
+__device__ __forceinline__ int table_slot(NodeTable<NQ, NT>& T, int node)
+{
+    const unsigned h = ((unsigned)node * 2654435761u) >> 9;
+#pragma unroll 1
+    for (int p = 0; p < kProbe; ++p) {
+        const int s = (h + p) & (NT - 1);
+        const int k = T.key[s];
+        if (k == node) return s;
+        if (k == -1) {
+            const int old = atomicCAS(&T.key[s], -1, node);
+            if (old == -1 || old == node) return s;
+        }
+    }
+    return -1;
+}
+
+__device__ __forceinline__ long long to_fixed(float v, unsigned& err)
+{
+    if (!(fabsf(v) < kFixLimit)) err |= kErrOverflow;
+    return __float2ll_rn(v * 4294967296.0f);
+}
+
+template <int NQ, int NT>
+__device__ __forceinline__ void table_add(NodeTable<NQ, NT>& T, int slot, int node, int q, long long v,
+                                          unsigned long long* __restrict__ node_acc)
+{
+    if (v == 0) return;
+    if (slot >= 0) atomicAdd(&T.acc[slot][q], (unsigned long long)v);
+    else atomicAdd(&node_acc[(size_t)node * NQ + q], (unsigned long long)v);
+}
+
+// ------------------------------------------------------------------------------------------
+// Bulk-copy (TMA) and mbarrier helpers (inline PTX, sm_90+ forms valid on sm_103a).
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: gives up after ~2^22 polls (each poll may suspend the thread briefly)
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity)
+{
+#pragma unroll 1
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, unsigned long long* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Internal consistency check: a failed check records kErrCheck in the status word and the
+// caller skips the access, so a logic error can never become a wild address.
+__device__ __forceinline__ bool consistent(bool ok, unsigned& err)
+{
+    if (!ok) err |= kErrCheck;
+    return ok;
+}
+
+}  // namespace lpdf
