@@ -6,8 +6,8 @@ particles, three velocity components, frequency and one scalar released from a l
 y = 0.67; Re_tau = 180, dt = 1e-3), initialised on the device by lpdf_particles_init, with
 synthetic node fields of the channel's structure held fixed (the gridpoint solves are not part
 of the timed step). One step = lpdf_pdf_step: Eq. 4/5/9/2 for every particle, wrap and wall
-reflection, exact point location, scalar sources and the moment sums at gridpoints; every
-`sort_every` steps also the element re-bucketing.
+reflection, exact point location, scalar sources, the re-bucketing of the ensemble by element
+(a stable counting sort) and the moment sums at gridpoints.
 
 Prints one JSON line. `--impl reference` times the FP64 CPU oracle instead (a bounded sample of
 the same workload on the host cores).
@@ -34,10 +34,9 @@ UNIT = "particle-updates/s"
 # algorithmic bytes of one particle update (ns = 1): read x, y, u, v, w, omega, psi, elem, pid
 # (36 B) and write x, y, u, v, w, omega, psi, elem (32 B)
 BYTES_PER_UPDATE = 68
-# the element re-bucketing runs inside lpdf_pdf_step before every SORT_EVERY-th step (timed)
-SORT_EVERY = 16
-# kernels of one re-bucketing: count, scan, scatter, segment sort, 9 state-row gathers (ns = 1)
-SORT_LAUNCHES = 13
+# kernels of one lpdf_pdf_step: advance, 3 scan kernels, record scatter, record offsets, particle
+# scatter, moments
+LAUNCHES_PER_STEP = 8
 
 
 def _env_int(k, d):
@@ -151,7 +150,6 @@ def build_workload(rank: int, ppe: int):
     wk.n_per_elem = ppe
     mesh = lpdf.Mesh(wk.mesh)
     params = lpdf.params_for(wk)
-    params.sort_every = SORT_EVERY
     ctx = lpdf.Context(mesh, params, wk.n_particles)
     init = torch.from_numpy(wl.node_init_fields(wk.mesh)).cuda()
     ctx.particles_init(wk.n_per_elem, init, m_erlang=4)
@@ -324,7 +322,6 @@ def main():
                    "particles_per_element": r["wk"].n_per_elem, "scalars": r["wk"].ns,
                    "l2": "inputs larger than L2 (state 0.9 GB per step)", "node_fields": "synthetic, held fixed",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "sort_every": SORT_EVERY,
                    "mean_walk_hops": r["hops"]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth",
@@ -336,7 +333,7 @@ def main():
         "e2e": {"value": P_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"],
                 "note": "per step: node fields host->device, pdf_step, grid_statistics, statistics device->host; "
                         "the particle state stays resident in HBM"},
-        "gpu_launches": K + SORT_LAUNCHES * sum(1 for s in range(args.warmup, args.warmup + K) if s % SORT_EVERY == 0),
+        "gpu_launches": K * LAUNCHES_PER_STEP,
     }
     print(json.dumps(line))
     if dist is not None:

@@ -77,8 +77,6 @@ typedef struct {
     int32_t n_sources;
     float src_x[LPDF_MAX_SOURCES], src_y[LPDF_MAX_SOURCES], src_r[LPDF_MAX_SOURCES];
     int32_t src_alpha[LPDF_MAX_SOURCES]; /* scalar index set to 1 inside source disc s */
-    int32_t sort_every; /* > 0: lpdf_pdf_step re-buckets the particles by element (lpdf_sort)
-                           before every sort_every-th step; 0: only on explicit lpdf_sort calls */
     int32_t gmodel;         /* lpdf_elliptic_relax_solve: 0 elliptic relaxation, 1 simplified Langevin model */
     int32_t pressure_solve; /* lpdf_elliptic_relax_solve: 1 solve for the mean pressure,
                                0 gradient = (dpdx0, dpdy0) only */
@@ -91,7 +89,7 @@ typedef struct lpdf_ctx lpdf_ctx;
 
 /* Fills *p with C3 = 5, C4 = 0.25, Cphi = 2, C0 = 2.1, Comega1 = 0.5, Comega2 = 0.73,
  * CL = 0.134, Ceta = 72, nu = 1/180, dt = 1e-3, ns = 1, no sources, seed = 1, lid_u = 0,
- * sort_every = 0, gmodel = 0, pressure_solve = 0, dpdx0 = dpdy0 = 0. */
+ * gmodel = 0, pressure_solve = 0, dpdx0 = dpdy0 = 0. */
 void lpdf_params_default(lpdf_params* p);
 
 /* Message of the calling thread's last error ("" if none). Owned by the library. */

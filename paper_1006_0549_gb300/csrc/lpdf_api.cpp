@@ -46,6 +46,19 @@ cudaError_t dalloc(T** p, size_t n)
 
 bool is_f32(double v) { return (double)(float)v == v; }
 
+cudaError_t alloc_pipe(PipeScratch& w, int64_t cap, size_t E)
+{
+    const size_t nrec = (size_t)((cap + 255) / 256) * 256;
+    cudaError_t e = cudaSuccess;
+    if ((e = dalloc(&w.perm, cap)) || (e = dalloc(&w.perm_new, cap)) || (e = dalloc(&w.rrank, cap)) ||
+        (e = dalloc(&w.rec_key, nrec)) || (e = dalloc(&w.rec_cnt, nrec)) || (e = dalloc(&w.rec_off, nrec)) ||
+        (e = dalloc(&w.nrec, nrec / 256)) || (e = dalloc(&w.kwork, 3 * (E + 1))) || (e = dalloc(&w.kstart, E + 1)) ||
+        (e = dalloc(&w.krstart, E + 1)) || (e = dalloc(&w.klist, nrec)) || (e = dalloc(&w.klist2, nrec)) ||
+        (e = dalloc(&w.scan_part, 2 * 4096)))
+        return e;
+    return cudaSuccess;
+}
+
 void free_mesh_device(DevMesh& d)
 {
     cudaFree(d.ex); cudaFree(d.ey); cudaFree(d.en); cudaFree(d.ev); cudaFree(d.em); cudaFree(d.master);
@@ -104,7 +117,6 @@ int check_params(const lpdf_params* p)
         if (p->src_alpha[i] < 0 || p->src_alpha[i] >= p->ns)
             return fail(LPDF_ERR_ARG, "source %d sets scalar %d, but ns = %d", i, p->src_alpha[i], p->ns);
     if (!(p->dt > 0.0) || !(p->nu >= 0.0)) return fail(LPDF_ERR_ARG, "need dt > 0 and nu >= 0");
-    if (p->sort_every < 0) return fail(LPDF_ERR_ARG, "sort_every = %d", p->sort_every);
     return LPDF_OK;
 }
 
@@ -336,7 +348,8 @@ int lpdf_ctx_create(const lpdf_mesh* mesh, const lpdf_params* params, int64_t ca
         (ce = dalloc(&s2.elem, cap)) || (ce = dalloc(&s2.pid, cap)) ||
         (ce = dalloc(&c->sort.cnt, E + 1)) || (ce = dalloc(&c->sort.cursor, E + 1)) ||
         (ce = dalloc(&c->sort.start, E + 2)) || (ce = dalloc(&c->sort.perm, cap)) ||
-        (ce = dalloc(&c->node_acc, (size_t)mesh->d.n_nodes * nq)) || (ce = dalloc(&c->status, 4))) {
+        (ce = dalloc(&c->node_acc, (size_t)mesh->d.n_nodes * nq)) || (ce = dalloc(&c->status, 4)) ||
+        (ce = alloc_pipe(c->pipe, cap, E))) {
         lpdf_ctx_free(c);
         return fail(LPDF_ERR_CUDA, "ctx_create: %s", cudaGetErrorString(ce));
     }
@@ -358,6 +371,10 @@ void lpdf_ctx_free(lpdf_ctx* c)
         cudaFree(s->psi); cudaFree(s->elem); cudaFree(s->pid);
     }
     cudaFree(c->sort.cnt); cudaFree(c->sort.cursor); cudaFree(c->sort.start); cudaFree(c->sort.perm);
+    PipeScratch& w = c->pipe;
+    void* pp[] = {w.perm, w.perm_new, w.rrank, w.rec_key, w.rec_cnt, w.rec_off, w.nrec, w.kwork, w.kstart,
+                  w.krstart, w.klist, w.klist2, w.scan_part};
+    for (void* q : pp) cudaFree(q);
     cudaFree(c->node_acc); cudaFree(c->status);
     delete c;
 }
@@ -385,6 +402,8 @@ int lpdf_particles_init(lpdf_ctx* c, int32_t n_per_elem, const float* node_init,
     c->s.n = P;
     CUDA_TRY(launch_particles_init(c->mesh->d, c->s, c->ns, n_per_elem, node_init, m_erlang, c->params.seed,
                                    c->status, (cudaStream_t)stream));
+    // generated element by element: the buffer is already in element order
+    CUDA_TRY(launch_iota(c->pipe.perm, P, (cudaStream_t)stream));
     return LPDF_OK;
 }
 
@@ -420,8 +439,12 @@ int lpdf_set_state(lpdf_ctx* c, int64_t n, const float* x, const float* y, const
     if (n > 0 && (!x || !y || !u || !v || !w || !om || !psi || !elem || !pid))
         return fail(LPDF_ERR_ARG, "set_state needs every array");
     c->s.n = n;
-    return copy_state(c, n, true, (float*)x, (float*)y, (float*)u, (float*)v, (float*)w, (float*)om, (float*)psi,
-                      (int32_t*)elem, (uint32_t*)pid, on_device, (cudaStream_t)stream);
+    const int rc = copy_state(c, n, true, (float*)x, (float*)y, (float*)u, (float*)v, (float*)w, (float*)om,
+                              (float*)psi, (int32_t*)elem, (uint32_t*)pid, on_device, (cudaStream_t)stream);
+    if (rc) return rc;
+    // any order is valid input; the first step brings the ensemble into element order
+    CUDA_TRY(launch_iota(c->pipe.perm, n, (cudaStream_t)stream));
+    return LPDF_OK;
 }
 
 int lpdf_get_state(const lpdf_ctx* c, float* x, float* y, float* u, float* v, float* w, float* om, float* psi,
@@ -438,6 +461,7 @@ int lpdf_sort(lpdf_ctx* c, void* stream)
     c->s2.n = c->s.n;
     CUDA_TRY(launch_sort(c->mesh->d, c->s, c->ns, c->s2, c->sort, c->status, (cudaStream_t)stream));
     std::swap(c->s, c->s2);
+    CUDA_TRY(launch_iota(c->pipe.perm, c->s.n, (cudaStream_t)stream));
     return LPDF_OK;
 }
 
@@ -445,15 +469,16 @@ int lpdf_pdf_step(lpdf_ctx* c, const float* node_fields, uint64_t step, void* st
 {
     if (!c || !node_fields) return fail(LPDF_ERR_ARG, "pdf_step: NULL argument");
     const cudaStream_t st = (cudaStream_t)stream;
-    if (c->params.sort_every > 0 && c->nsteps % c->params.sort_every == 0) {
-        const int rc = lpdf_sort(c, stream);
-        if (rc) return rc;
-    }
     ++c->nsteps;
     const int nq = nquant(c->ns);
     CUDA_TRY(cudaMemsetAsync(c->node_acc, 0, sizeof(unsigned long long) * (size_t)c->mesh->d.n_nodes * nq, st));
     const StepParams p = make_step_params(c->params, c->mesh, step);
-    CUDA_TRY(launch_pdf_step(c->mesh->d, c->s, c->ns, node_fields, p, c->node_acc, c->status, st));
+    c->s2.n = c->s.n;
+    CUDA_TRY(launch_pdf_step_pipeline(c->mesh->d, c->s, c->s2, c->ns, node_fields, p, c->pipe, c->node_acc,
+                                      c->status, st));
+    // the new state is in the second buffer, listed in element order by perm_new
+    std::swap(c->s, c->s2);
+    std::swap(c->pipe.perm, c->pipe.perm_new);
     return LPDF_OK;
 }
 

@@ -34,13 +34,25 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 // (w + 1/2) 2^-32, rounded to FP32
 __device__ __forceinline__ float u01(uint32_t w) { return fmaf((float)w, 0x1p-32f, 0x1p-33f); }
 
+// -2 ln u for u = (w + 1/2) 2^-32. Near u = 1 both the FP32 rounding of u and a logarithm with a
+// bounded absolute error would leave a large relative error in the (small) result; there
+// v = 1 - u = (~w + 1/2) 2^-32 is formed exactly from the integer and -ln(1 - v) summed as its
+// series v + v^2/2 + ... + v^6/6 (v < 1/16: the remainder is below 1e-8 relative).
+__device__ __forceinline__ float neg2log_tail(uint32_t w)
+{
+    const float v = fmaf((float)(~w), 0x1p-32f, 0x1p-33f);
+    const float s = fmaf(v, fmaf(v, fmaf(v, fmaf(v, fmaf(v, 1.0f / 6.0f, 0.2f), 0.25f), 1.0f / 3.0f), 0.5f), 1.0f);
+    return 2.0f * v * s;
+}
+
 // Box-Muller (1958) on the special-function unit: r^2 = -2 ln u0 (lg2.approx: absolute error
-// ~2^-22 in log2), r = r^2 * rsqrt(r^2), angle theta = 2 pi u1 - pi in [-pi, pi), where the SFU
-// sine and cosine are accurate to ~2^-21.4 absolute; cos(theta + pi) = -cos(theta) and
-// sin(theta + pi) = -sin(theta), so z0 = r cos(2 pi u1), z1 = r sin(2 pi u1) as in the oracle.
+// ~2^-22 in log2, used for u0 <= 15/16 where -ln u0 >= 0.064), r = r^2 * rsqrt(r^2), angle
+// theta = 2 pi u1 - pi in [-pi, pi), where the SFU sine and cosine are accurate to ~2^-21.4
+// absolute; cos(theta + pi) = -cos(theta) and sin(theta + pi) = -sin(theta), so
+// z0 = r cos(2 pi u1), z1 = r sin(2 pi u1) as in the oracle.
 __device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float& z0, float& z1)
 {
-    const float r2 = -2.0f * __logf(u01(w0));
+    const float r2 = w0 >= 0xF0000000u ? neg2log_tail(w0) : -2.0f * __logf(u01(w0));
     const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
     const float th = fmaf(6.28318530717958648f, u01(w1), -3.14159265358979324f);
     float sn, cs;
@@ -52,7 +64,7 @@ __device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float& z0, 
 // accurate variant for the initialisation kernel (not on the hot path)
 __device__ __forceinline__ void box_muller_accurate(uint32_t w0, uint32_t w1, float& z0, float& z1)
 {
-    const float r = sqrtf(-2.0f * logf(u01(w0)));
+    const float r = sqrtf(w0 >= 0xF0000000u ? neg2log_tail(w0) : -2.0f * logf(u01(w0)));
     float sn, cs;
     sincospif(2.0f * u01(w1), &sn, &cs);
     z0 = r * cs;
@@ -220,11 +232,6 @@ __device__ __forceinline__ void barycentric(const float4& X, const float4& Y, fl
     l2 = det2(X.x - px, Y.x - py, X.y - px, Y.y - py) * Y.w;
 }
 
-__device__ __forceinline__ bool in_source(float px, float py, float sx, float sy, float r)
-{
-    const float dx = __fsub_rn(px, sx), dy = __fsub_rn(py, sy);
-    return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) < __fmul_rn(r, r);
-}
 
 // ------------------------------------------------------------------------------------------
 // CTA node table: 64-bit fixed-point moment sums keyed by statistics node. A lookup probes at
@@ -325,6 +332,118 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// ------------------------------------------------------------------------------------------
+// One particle's state in registers, and its forward-Euler step (Section "Governing
+// equations"): Eq. 4 for U, Eq. 5 for omega, Eq. 9 in IEM form for psi, Eq. 2 for X with the
+// same dW_1, dW_2; periodic wrap, wall reflection, the half-open domain and the scalar sources.
+// ------------------------------------------------------------------------------------------
+template <int NS>
+struct ParticleState {
+    float x, y, u, v, w, om, psi[NS];
+    int elem;
+    uint32_t pid;
+};
+
+__device__ __forceinline__ bool in_source(float px, float py, float sx, float sy, float r)
+{
+    const float dx = __fsub_rn(px, sx), dy = __fsub_rn(py, sy);
+    return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) < __fmul_rn(r, r);
+}
+
+// On return p holds the new state except the element, which is the walk's start: the old
+// element, or 0 when the old one is outside the mesh (`bad`).
+template <int NS>
+__device__ __forceinline__ void advance_particle(const DevMesh& M, const float* __restrict__ F, const StepParams& P,
+                                                 ParticleState<NS>& p, unsigned& err, bool& bad)
+{
+    constexpr int NFP = (22 + NS + 3) / 4 * 4;
+    const float x = p.x, y = p.y, u = p.u, v = p.v, w = p.w, om = p.om;
+    bad = (unsigned)p.elem >= (unsigned)M.n_tri;
+    const int e = bad ? 0 : p.elem;
+    const float4 X = __ldg(&M.ex[e]);
+    const float4 Y = __ldg(&M.ey[e]);
+    const int4 V = __ldg(&M.ev[e]);
+    float l0, l1, l2;
+    barycentric(X, Y, x, y, l0, l1, l2);
+    // linear shape-function interpolation of the node fields
+    float Fi[NFP];
+    {
+        const float4* R0 = reinterpret_cast<const float4*>(F) + (size_t)V.x * (NFP / 4);
+        const float4* R1 = reinterpret_cast<const float4*>(F) + (size_t)V.y * (NFP / 4);
+        const float4* R2 = reinterpret_cast<const float4*>(F) + (size_t)V.z * (NFP / 4);
+#pragma unroll
+        for (int q = 0; q < NFP / 4; ++q) {
+            const float4 a = __ldg(R0 + q), b = __ldg(R1 + q), c = __ldg(R2 + q);
+            Fi[4 * q + 0] = fmaf(l0, a.x, fmaf(l1, b.x, l2 * c.x));
+            Fi[4 * q + 1] = fmaf(l0, a.y, fmaf(l1, b.y, l2 * c.y));
+            Fi[4 * q + 2] = fmaf(l0, a.z, fmaf(l1, b.z, l2 * c.z));
+            Fi[4 * q + 3] = fmaf(l0, a.w, fmaf(l1, b.w, l2 * c.w));
+        }
+    }
+    // Wiener increments: Philox blocks 0 and 1 of counter (pid, step, 0<<16 | block)
+    const uint4 r0 = philox4x32_10(make_uint4(p.pid, P.step_lo, P.step_hi, 0u), P.key0, P.key1);
+    const uint4 r1 = philox4x32_10(make_uint4(p.pid, P.step_lo, P.step_hi, 1u), P.key0, P.key1);
+    float z0, z1, z2, z3, z4, z5;
+    box_muller(r0.x, r0.y, z0, z1);
+    box_muller(r0.z, r0.w, z2, z3);
+    box_muller(r1.x, r1.y, z4, z5);
+    const float dW1 = P.sdt * z0, dW2 = P.sdt * z1;
+    const float c0e = sqrtf(fmaxf(Fi[LPDF_F_C0EPS], 0.0f));
+    const float Ur = u - Fi[LPDF_F_U + 0], Vr = v - Fi[LPDF_F_U + 1], Wr = w - Fi[LPDF_F_U + 2];
+    // Eq. 4
+    float un = u + (-Fi[LPDF_F_DPDX] + P.nu2 * Fi[LPDF_F_LAPU] + Fi[LPDF_F_G11] * Ur + Fi[LPDF_F_G11 + 1] * Vr) * P.dt
+             + P.s2nu * (Fi[LPDF_F_DUDX] * dW1 + Fi[LPDF_F_DUDX + 1] * dW2) + c0e * (P.sdt * z2);
+    float vn = v + (-Fi[LPDF_F_DPDX + 1] + P.nu2 * Fi[LPDF_F_LAPU + 1] + Fi[LPDF_F_G11 + 2] * Ur
+                    + Fi[LPDF_F_G11 + 3] * Vr) * P.dt
+             + P.s2nu * (Fi[LPDF_F_DUDX + 2] * dW1 + Fi[LPDF_F_DUDX + 3] * dW2) + c0e * (P.sdt * z3);
+    float wn = w + (P.nu2 * Fi[LPDF_F_LAPU + 2] + Fi[LPDF_F_G11 + 4] * Wr) * P.dt
+             + P.s2nu * (Fi[LPDF_F_DUDX + 4] * dW1 + Fi[LPDF_F_DUDX + 5] * dW2) + c0e * (P.sdt * z4);
+    // Eq. 5 (S_omega of Eq. 6 is a node field)
+    const float Om = Fi[LPDF_F_OMEGA];
+    float omn = om - P.C3 * Om * (om - Om) * P.dt - Fi[LPDF_F_SOMEGA] * Om * om * P.dt
+              + sqrtf(2.0f * P.C3 * P.C4 * Om * Om * fmaxf(om, 0.0f)) * (P.sdt * z5);
+    omn = fabsf(omn);
+    // Eq. 9, IEM form: 1/t_m = C_phi <omega> / 2
+    const float mix = P.half_cphi * Om * P.dt;
+#pragma unroll
+    for (int a = 0; a < NS; ++a) p.psi[a] = p.psi[a] - (p.psi[a] - Fi[LPDF_F_PHI0 + a]) * mix;
+    // Eq. 2 with the velocity at t_n and the same dW_1, dW_2
+    float qx = x + u * P.dt + P.s2nu * dW1;
+    float qy = y + v * P.dt + P.s2nu * dW2;
+    if (M.periodic) {
+        if (qx < M.x0) qx += M.period;
+        else if (qx >= M.x1) qx -= M.period;
+        if (qx < M.x0 || qx >= M.x1) qx -= floorf((qx - M.x0) / M.period) * M.period;   // moves > one period
+    }
+#pragma unroll 1
+    for (int it = 0; it < 8; ++it) {
+        if (qy < M.y0) { qy = 2.0f * M.y0 - qy; un = -un; vn = -vn; wn = -wn; }
+        else if (qy > M.y1) { qy = 2.0f * M.y1 - qy; un = 2.0f * P.lid_u - un; vn = -vn; wn = -wn; }
+        else if (!M.periodic && qx < M.x0) { qx = 2.0f * M.x0 - qx; un = -un; vn = -vn; wn = -wn; }
+        else if (!M.periodic && qx > M.x1) { qx = 2.0f * M.x1 - qx; un = -un; vn = -vn; wn = -wn; }
+        else break;
+    }
+    // half-open domain [x0, x1) x [y0, y1)
+    if (qx >= M.x1) qx = M.periodic ? M.x0 : nextafterf(M.x1, -CUDART_INF_F);
+    if (qy >= M.y1) qy = nextafterf(M.y1, -CUDART_INF_F);
+    // concentrated scalar sources
+    for (int q = 0; q < P.n_src; ++q)
+        if (in_source(qx, qy, P.src_x[q], P.src_y[q], P.src_r[q])) {
+#pragma unroll
+            for (int a = 0; a < NS; ++a)
+                if (a == P.src_alpha[q]) p.psi[a] = 1.0f;
+        }
+    if (!(isfinite(un) && isfinite(vn) && isfinite(wn) && isfinite(omn) && isfinite(qx) && isfinite(qy)))
+        err |= kErrNonFinite;
+    p.x = qx;
+    p.y = qy;
+    p.u = un;
+    p.v = vn;
+    p.w = wn;
+    p.om = omn;
+    p.elem = e;
+}
 
 // Internal consistency check: a failed check records kErrCheck in the status word and the
 // caller skips the access, so a logic error can never become a wild address.

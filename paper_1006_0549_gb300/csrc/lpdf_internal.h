@@ -74,6 +74,27 @@ struct SortScratch {
 cudaError_t launch_sort(const DevMesh& m, const DevState& s, int ns, const DevState& dst, SortScratch& w,
                         unsigned long long* status, cudaStream_t st);
 
+// scratch of the step pipeline (lpdf_pipeline.cu)
+struct PipeScratch {
+    int* perm = nullptr;         // the current buffer in element order (the next step's gather order)
+    int* perm_new = nullptr;     // written by the step: the next buffer in element order
+    uint16_t* rrank = nullptr;   // per particle: (record slot << 8) | rank within its block's record
+    int* rec_key = nullptr;      // per block record (block * 256 + slot): element, count, offset
+    int* rec_cnt = nullptr;
+    int* rec_off = nullptr;
+    int* nrec = nullptr;         // records per block
+    int* kwork = nullptr;        // 3 (E + 1): particles, records and cursors per element
+    int* kstart = nullptr;       // E + 1: bucket starts
+    int* krstart = nullptr;      // E + 1: record-list starts
+    int* klist = nullptr;        // records grouped by element, then in block order
+    int* klist2 = nullptr;
+    int* scan_part = nullptr;    // 2 x 4096 scan tile totals
+};
+cudaError_t launch_pdf_step_pipeline(const DevMesh& m, const DevState& cur, const DevState& nxt, int ns,
+                                     const float* fields, const StepParams& p, PipeScratch& w,
+                                     unsigned long long* node_acc, unsigned long long* status, cudaStream_t st);
+cudaError_t launch_iota(int* p, int64_t n, cudaStream_t st);
+
 // P1 finite-element tables of the gridpoint solve (lpdf_solve.cu), built once per mesh.
 // DOFs are the geometric nodes with periodic partners merged (numbered in node order).
 struct Fem {
@@ -134,8 +155,9 @@ struct lpdf_ctx {
     const lpdf_mesh* mesh;
     lpdf_params params;
     lpdf::DevState s;                         // current particle state
-    lpdf::DevState s2;                        // second buffer (target of the re-bucketing)
+    lpdf::DevState s2;                        // second buffer (written by the step and the re-bucketing)
     lpdf::SortScratch sort;
+    lpdf::PipeScratch pipe;
     unsigned long long* node_acc = nullptr;   // n_nodes x nq fixed-point sums
     unsigned long long* status = nullptr;     // 4 words
     int ns;

@@ -1,0 +1,509 @@
+// The particle time step as a pipeline that keeps the ensemble in element order (sm_103a).
+//
+// Per step (Section "Governing equations": Eq. 2, 4, 5, 6, 9 in IEM form, forward Euler,
+// statistics at the gridpoints, tracking through the unstructured grid):
+//   K1  advance_kernel: thread i takes the particle perm[i] of the current buffer (perm lists the
+//       buffer in element order), advances it (Eq. 4, 5, 9, 2, wrap, reflection, sources),
+//       locates it with the barycentric neighbour walk and writes it to position i of the next
+//       buffer. Each 256-particle block also counts its particles per new element (a sparse
+//       histogram: one record per distinct element) and gives every particle its rank among the
+//       block's particles of the same element, in position order.
+//   S1  exclusive scans: particles per element -> bucket starts; records per element -> list starts.
+//   S2  record_scatter_kernel: every record joins its element's record list.
+//   S3  key_offsets_kernel (a warp per element): the element's records in block order, and each
+//       record's offset = bucket start + the counts of the element's records in earlier blocks.
+//   S4  particle_scatter_kernel: perm_new[offset(record) + rank] = i. perm_new lists the next
+//       buffer in (new element, position) order: a stable counting sort, fully deterministic.
+//   K2  moments_kernel (a warp per element): the element's particles, gathered through perm_new
+//       in canonical order; lambda_a' q_k accumulated in FP32 per lane over at most kLaneChunk
+//       particles, a fixed butterfly across the lanes, one 64-bit fixed-point atomic add per
+//       node and quantity.
+// Every step leaves perm_new as the next step's perm, so the ensemble is re-bucketed by element
+// every step without a separate sort, and the reduction never needs a hash or a binning pass.
+#include <algorithm>
+
+#include "lpdf_device.cuh"
+
+namespace lpdf {
+
+namespace {
+
+constexpr int kBlk = 256;          // K1 block: particles (= threads) per histogram block
+constexpr int kRecHash = 512;      // hash slots for the distinct elements of a block
+constexpr int kLaneChunk = 16;     // K2: particles a lane sums in FP32 before the warp reduction
+constexpr int kScanItems = 4;      // scan: items per thread
+constexpr int kScanThreads = 1024;
+constexpr int kScanTile = kScanItems * kScanThreads;
+
+__device__ __forceinline__ unsigned rec_hash(int key) { return ((unsigned)key * 2654435761u) >> 23; }   // 9 bits
+static_assert(kRecHash == 512, "rec_hash gives 9 bits");
+
+// exclusive scan over the kBlk threads of a block; `total` gets the sum (two barriers)
+__device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int& total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    int off = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kBlk / 32; ++w) {
+        const int s = wsum[w];
+        off += w < wid ? s : 0;
+        tot += s;
+    }
+    __syncthreads();
+    total = tot;
+    return off + incl - v;
+}
+
+// ------------------------------------------------------------------------------------------
+// K1
+// ------------------------------------------------------------------------------------------
+template <int NS>
+__global__ void __launch_bounds__(kBlk, 3)
+advance_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevState cur,
+               const __grid_constant__ DevState nxt, const int* __restrict__ perm, const float* __restrict__ F,
+               const __grid_constant__ StepParams P, uint16_t* __restrict__ rrank, int* __restrict__ rec_key,
+               int* __restrict__ rec_cnt, int* __restrict__ nrec, int* __restrict__ kcnt, int* __restrict__ krc,
+               unsigned long long* __restrict__ status)
+{
+    __shared__ int hkey[kRecHash];
+    __shared__ __align__(16) unsigned short hcnt[kRecHash][kBlk / 32];
+    __shared__ int hrec[kRecHash];
+    __shared__ int wsum[kBlk / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int s = tid; s < kRecHash; s += kBlk) hkey[s] = -1;
+    {
+        uint4* z = reinterpret_cast<uint4*>(&hcnt[0][0]);
+        constexpr int n16 = (int)(sizeof(hcnt) / sizeof(uint4));
+        for (int k = tid; k < n16; k += kBlk) z[k] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    const int64_t i = (int64_t)blockIdx.x * kBlk + tid;
+    unsigned err = 0;
+    int hops = 0;
+    int key = -1;
+    if (i < cur.n) {
+        const int src = perm[i];
+        ParticleState<NS> p;
+        p.x = cur.x[src];
+        p.y = cur.y[src];
+        p.u = cur.u[src];
+        p.v = cur.v[src];
+        p.w = cur.w[src];
+        p.om = cur.om[src];
+#pragma unroll
+        for (int a = 0; a < NS; ++a) p.psi[a] = cur.psi[(size_t)a * cur.cap + src];
+        p.elem = cur.elem[src];
+        p.pid = cur.pid[src];
+        bool bad;
+        advance_particle<NS>(M, F, P, p, err, bad);
+        // barycentric neighbour walk from the old element
+        const int e0 = p.elem;
+        int e = e0, h = 0, ne = e0;
+        bool lost = false;
+#pragma unroll 1
+        for (;;) {
+            float lam[3];
+            int next = -1;
+            if (walk_test(M, e, p.x, p.y, lam, next)) {
+                ne = e;
+                hops += h;
+                break;
+            }
+            if (next < 0 || h >= kHopCap) {
+                lost = true;
+                hops += next < 0 ? h : kHopCap + 1;
+                break;
+            }
+            e = next;
+            ++h;
+        }
+        if (lost) ne = e0;
+        if (lost || bad) {
+            err |= kErrLost;
+            atomicAdd(&status[1], 1ull);
+            atomicCAS(&status[2], ~0ull, (unsigned long long)p.pid);
+        }
+        nxt.x[i] = p.x;
+        nxt.y[i] = p.y;
+        nxt.u[i] = p.u;
+        nxt.v[i] = p.v;
+        nxt.w[i] = p.w;
+        nxt.om[i] = p.om;
+#pragma unroll
+        for (int a = 0; a < NS; ++a) nxt.psi[(size_t)a * nxt.cap + i] = p.psi[a];
+        nxt.elem[i] = ne;
+        nxt.pid[i] = p.pid;
+        key = ne;
+    }
+    __syncthreads();
+    // ---- sparse histogram of the new elements: one insert per distinct element of a warp
+    const unsigned m = __match_any_sync(kFull, key);
+    const int leader = __ffs(m) - 1;
+    int slot = -1;
+    if (key >= 0 && lane == leader) {
+        const unsigned h0 = rec_hash(key);
+#pragma unroll 1
+        for (int q = 0; q < kRecHash; ++q) {
+            const int s = (h0 + q) & (kRecHash - 1);
+            const int c = hkey[s];
+            if (c == key) { slot = s; break; }
+            if (c == -1) {
+                const int old = atomicCAS(&hkey[s], -1, key);
+                if (old == -1 || old == key) { slot = s; break; }
+            }
+        }
+        if (slot >= 0) hcnt[slot][wid] = (unsigned short)__popc(m);
+    }
+    slot = __shfl_sync(kFull, slot, leader);
+    const int rank_w = __popc(m & lt);
+    __syncthreads();
+    // ---- records in slot order; per-(element, warp) prefixes -----------------------------------
+    {
+        const int s0 = 2 * tid, s1 = 2 * tid + 1;
+        const int k0 = hkey[s0], k1 = hkey[s1];
+        const int o0 = k0 >= 0, o1 = k1 >= 0;
+        int total;
+        const int r0 = block_exclusive_scan(o0 + o1, wsum, total);
+        const int ss[2] = {s0, s1}, kk[2] = {k0, k1}, oo[2] = {o0, o1}, rr[2] = {r0, r0 + o0};
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            if (!oo[q]) continue;
+            const int s = ss[q];
+            int run = 0;
+#pragma unroll
+            for (int w = 0; w < kBlk / 32; ++w) {
+                const int c = hcnt[s][w];
+                hcnt[s][w] = (unsigned short)run;
+                run += c;
+            }
+            hrec[s] = rr[q];
+            const int64_t rid = (int64_t)blockIdx.x * kBlk + rr[q];
+            rec_key[rid] = kk[q];
+            rec_cnt[rid] = run;
+            atomicAdd(&kcnt[kk[q]], run);
+            atomicAdd(&krc[kk[q]], 1);
+        }
+        if (tid == 0) nrec[blockIdx.x] = total;
+    }
+    __syncthreads();
+    if (key >= 0) {
+        if (consistent(slot >= 0, err))
+            rrank[i] = (uint16_t)((hrec[slot] << 8) | (hcnt[slot][wid] + rank_w));
+    }
+    const unsigned e_or = __reduce_or_sync(kFull, err);
+    const int h_sum = __reduce_add_sync(kFull, hops);
+    if (lane == 0) {
+        if (e_or) atomicOr(&status[0], (unsigned long long)e_or);
+        if (h_sum) atomicAdd(&status[3], (unsigned long long)h_sum);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// S1: exclusive scan of two int arrays of length n (blockIdx.y picks the array)
+// ------------------------------------------------------------------------------------------
+struct ScanPair {
+    const int* in[2];
+    int* out[2];
+    int* part[2];
+    // select without dynamic indexing of the parameter arrays
+    __device__ __forceinline__ const int* src(int a) const { return a ? in[1] : in[0]; }
+    __device__ __forceinline__ int* dst(int a) const { return a ? out[1] : out[0]; }
+    __device__ __forceinline__ int* tot(int a) const { return a ? part[1] : part[0]; }
+};
+
+__device__ __forceinline__ int block_scan_1024(int v, int* wsum, int& total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int s = wsum[lane];
+        int x = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += t;
+        }
+        wsum[lane] = x - s;
+        if (lane == 31) wsum[32] = x;
+    }
+    __syncthreads();
+    total = wsum[32];
+    const int r = wsum[wid] + incl - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(ScanPair sp, int n)
+{
+    __shared__ int wsum[33];
+    const int a = blockIdx.y;
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < n ? sp.src(a)[base + k] : 0;
+        sum += v[k];
+    }
+    int total;
+    int run = block_scan_1024(sum, wsum, total);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) sp.dst(a)[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0) sp.tot(a)[blockIdx.x] = total;
+}
+
+// the tile totals (at most kScanTile of them) scanned in place
+__global__ void __launch_bounds__(kScanThreads) scan_parts_kernel(ScanPair sp, int ntiles)
+{
+    __shared__ int wsum[33];
+    const int a = blockIdx.y;
+    const int base = threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < ntiles ? sp.tot(a)[base + k] : 0;
+        sum += v[k];
+    }
+    int total;
+    int run = block_scan_1024(sum, wsum, total);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < ntiles) sp.tot(a)[base + k] = run;
+        run += v[k];
+    }
+}
+
+__global__ void scan_add_kernel(ScanPair sp, int n)
+{
+    const int a = blockIdx.y;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) sp.dst(a)[j] += sp.tot(a)[j / kScanTile];
+}
+
+// ------------------------------------------------------------------------------------------
+// S2, S3, S4
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlk) record_scatter_kernel(const int* __restrict__ nrec, const int* __restrict__ rec_key,
+                                                              const int* __restrict__ krstart, int* __restrict__ kcur,
+                                                              int* __restrict__ klist)
+{
+    const int t = threadIdx.x;
+    if (t >= nrec[blockIdx.x]) return;
+    const int rid = blockIdx.x * kBlk + t;
+    const int key = rec_key[rid];
+    klist[krstart[key] + atomicAdd(&kcur[key], 1)] = rid;
+}
+
+// a warp per element: its records in block order (a record id is block * kBlk + slot, and an
+// element has at most one record per block), then the running offsets
+__global__ void __launch_bounds__(256) key_offsets_kernel(int n_keys, const int* __restrict__ kstart,
+                                                          const int* __restrict__ krstart,
+                                                          const int* __restrict__ klist, int* __restrict__ klist2,
+                                                          const int* __restrict__ rec_cnt, int* __restrict__ rec_off)
+{
+    const int e = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (e >= n_keys) return;
+    const int r0 = krstart[e], r1 = krstart[e + 1], nr = r1 - r0;
+    if (nr == 0) return;
+    if (nr == 1) {
+        if (lane == 0) rec_off[klist[r0]] = kstart[e];
+        return;
+    }
+    // rank of every record id among the element's (ids are distinct)
+    for (int j = lane; j < nr; j += 32) {
+        const int id = klist[r0 + j];
+        int rank = 0;
+        for (int q = 0; q < nr; ++q) rank += klist[r0 + q] < id;
+        klist2[r0 + rank] = id;
+    }
+    __syncwarp();
+    int carry = kstart[e];
+    for (int j0 = 0; j0 < nr; j0 += 32) {
+        const int j = j0 + lane;
+        const int id = j < nr ? klist2[r0 + j] : -1;
+        const int c = id >= 0 ? rec_cnt[id] : 0;
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (id >= 0) rec_off[id] = carry + incl - c;
+        carry += __shfl_sync(kFull, incl, 31);
+    }
+}
+
+__global__ void particle_scatter_kernel(int64_t n, const uint16_t* __restrict__ rrank, const int* __restrict__ rec_off,
+                                        int* __restrict__ perm_new)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned pk = rrank[i];
+    const int64_t rid = (i / kBlk) * kBlk + (pk >> 8);
+    perm_new[rec_off[rid] + (pk & 255u)] = (int)i;
+}
+
+// ------------------------------------------------------------------------------------------
+// K2
+// ------------------------------------------------------------------------------------------
+template <int NS>
+__global__ void __launch_bounds__(256, 2) moments_kernel(const __grid_constant__ DevMesh M,
+                                                      const __grid_constant__ DevState S,
+                                                      const int* __restrict__ perm, const int* __restrict__ kstart,
+                                                      unsigned long long* __restrict__ node_acc,
+                                                      unsigned long long* __restrict__ status)
+{
+    constexpr int NQ = 11 + 2 * NS, NK = 3 * NQ;
+    const int e = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (e >= M.n_tri) return;
+    const int p0 = kstart[e], p1 = kstart[e + 1];
+    if (p0 >= p1) return;
+    const float4 X = __ldg(&M.ex[e]);
+    const float4 Y = __ldg(&M.ey[e]);
+    const int4 mv = __ldg(&M.em[e]);
+    unsigned err = 0;
+#pragma unroll 1
+    for (int base = p0; base < p1; base += 32 * kLaneChunk) {
+        float acc[NK];
+#pragma unroll
+        for (int k = 0; k < NK; ++k) acc[k] = 0.0f;
+        const int end = min(p1, base + 32 * kLaneChunk);
+#pragma unroll 2
+        for (int pos = base + lane; pos < end; pos += 32) {
+            const int idx = perm[pos];
+            const float x = S.x[idx], y = S.y[idx];
+            float q[NQ];
+            const float u = S.u[idx], v = S.v[idx], w = S.w[idx];
+            q[0] = 1.0f; q[1] = u; q[2] = v; q[3] = w;
+            q[4] = u * u; q[5] = u * v; q[6] = u * w; q[7] = v * v; q[8] = v * w; q[9] = w * w;
+            q[10] = S.om[idx];
+#pragma unroll
+            for (int a = 0; a < NS; ++a) {
+                const float ps = S.psi[(size_t)a * S.cap + idx];
+                q[11 + a] = ps;
+                q[11 + NS + a] = ps * ps;
+            }
+            float l0, l1, l2;
+            barycentric(X, Y, x, y, l0, l1, l2);
+#pragma unroll
+            for (int k = 0; k < NQ; ++k) {
+                acc[k] = fmaf(l0, q[k], acc[k]);
+                acc[NQ + k] = fmaf(l1, q[k], acc[NQ + k]);
+                acc[2 * NQ + k] = fmaf(l2, q[k], acc[2 * NQ + k]);
+            }
+        }
+        // the same butterfly in every lane: every lane ends with every column's sum
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(kFull, acc[k], o);
+        }
+        // lane j adds columns j and j + 32
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+            const int col = lane + 32 * kk;
+            float mine = 0.0f;
+#pragma unroll
+            for (int k = 0; k < NK; ++k)
+                if (k == col) mine = acc[k];
+            if (col < NK) {
+                const int c = col / NQ, qq = col - c * NQ;
+                const int node = c == 0 ? mv.x : (c == 1 ? mv.y : mv.z);
+                const long long v = to_fixed(mine, err);
+                if (v != 0) atomicAdd(&node_acc[(size_t)node * NQ + qq], (unsigned long long)v);
+            }
+        }
+    }
+    const unsigned e_or = __reduce_or_sync(kFull, err);
+    if (lane == 0 && e_or) atomicOr(&status[0], (unsigned long long)e_or);
+}
+
+__global__ void iota_kernel(int* __restrict__ p, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = (int)i;
+}
+
+inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+cudaError_t scan_pair(const int* in0, int* out0, const int* in1, int* out1, int n, int* part, cudaStream_t st)
+{
+    const int ntiles = (n + kScanTile - 1) / kScanTile;
+    if (ntiles > kScanTile) return cudaErrorInvalidValue;
+    ScanPair sp{{in0, in1}, {out0, out1}, {part, part + kScanTile}};
+    scan_tiles_kernel<<<dim3(ntiles, 2), kScanThreads, 0, st>>>(sp, n);
+    scan_parts_kernel<<<dim3(1, 2), kScanThreads, 0, st>>>(sp, ntiles);
+    scan_add_kernel<<<dim3(nblocks(n, 256), 2), 256, 0, st>>>(sp, n);
+    return cudaGetLastError();
+}
+
+template <int NS>
+cudaError_t run_pipeline(const DevMesh& m, const DevState& cur, const DevState& nxt, const float* fields,
+                         const StepParams& p, PipeScratch& w, unsigned long long* node_acc, unsigned long long* status,
+                         cudaStream_t st)
+{
+    const int64_t n = cur.n;
+    if (n == 0) return cudaSuccess;
+    const int E = m.n_tri;
+    const int64_t nblk = (n + kBlk - 1) / kBlk;
+    cudaError_t e = cudaMemsetAsync(w.kwork, 0, sizeof(int) * 3 * (size_t)(E + 1), st);
+    if (e != cudaSuccess) return e;
+    int* kcnt = w.kwork;
+    int* krc = w.kwork + (E + 1);
+    int* kcur = w.kwork + 2 * (E + 1);
+    advance_kernel<NS><<<(unsigned)nblk, kBlk, 0, st>>>(m, cur, nxt, w.perm, fields, p, w.rrank, w.rec_key, w.rec_cnt,
+                                                        w.nrec, kcnt, krc, status);
+    e = scan_pair(kcnt, w.kstart, krc, w.krstart, E + 1, w.scan_part, st);
+    if (e != cudaSuccess) return e;
+    record_scatter_kernel<<<(unsigned)nblk, kBlk, 0, st>>>(w.nrec, w.rec_key, w.krstart, kcur, w.klist);
+    key_offsets_kernel<<<nblocks((int64_t)E * 32, 256), 256, 0, st>>>(E, w.kstart, w.krstart, w.klist, w.klist2,
+                                                                       w.rec_cnt, w.rec_off);
+    particle_scatter_kernel<<<nblocks(n, 256), 256, 0, st>>>(n, w.rrank, w.rec_off, w.perm_new);
+    moments_kernel<NS><<<nblocks((int64_t)E * 32, 256), 256, 0, st>>>(m, nxt, w.perm_new, w.kstart, node_acc, status);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_pdf_step_pipeline(const DevMesh& m, const DevState& cur, const DevState& nxt, int ns,
+                                     const float* fields, const StepParams& p, PipeScratch& w,
+                                     unsigned long long* node_acc, unsigned long long* status, cudaStream_t st)
+{
+    switch (ns) {
+        case 1: return run_pipeline<1>(m, cur, nxt, fields, p, w, node_acc, status, st);
+        case 2: return run_pipeline<2>(m, cur, nxt, fields, p, w, node_acc, status, st);
+        case 3: return run_pipeline<3>(m, cur, nxt, fields, p, w, node_acc, status, st);
+        case 4: return run_pipeline<4>(m, cur, nxt, fields, p, w, node_acc, status, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_iota(int* p, int64_t n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    iota_kernel<<<nblocks(n, 256), 256, 0, st>>>(p, n);
+    return cudaGetLastError();
+}
+
+}  // namespace lpdf

@@ -3,7 +3,7 @@
 // 4, 5, 6, 9 in IEM form; statistics at particle positions; tracking through the unstructured
 // grid), fused with the reduction of the new state's moments to the gridpoints.
 //
-// A persistent CTA (256 threads, two per SM) walks a contiguous range of 1024-particle
+// A persistent CTA (128 threads, four per SM) walks a contiguous range of 512-particle
 // sub-tiles. Per sub-tile:
 //   1. bulk copy (TMA) of the state rows into shared memory;
 //   2. every thread advances its 4 particles (Eq. 4, 5, 9, 2, wrap, reflection, sources) in
@@ -15,14 +15,15 @@
 //      match_any on each 32-particle row; one block scan gives every bin its range of sorted
 //      positions and its accumulation units (runs of at most kUnit particles, aligned to the
 //      bin start);
-//   4. each thread accumulates whole units in FP32 registers (lambda_a' q_k for the 3 corners
-//      and the 11 + 2 ns quantities); the warp then hands its units' partials through a small
-//      shared scratch, kGroup lanes at a time, to column owners: lane k sums column k over each
-//      run of equal bins, converts the sum once to 64-bit fixed point and adds it to the CTA
-//      node table (no two lanes of a warp add to the same word).
+//   4. each thread accumulates one unit in FP32 registers (lambda_a' q_k for the 3 corners and
+//      the 11 + 2 ns quantities); after a barrier the tile is dead and becomes a column-major
+//      scratch of all units' partials; thread i then takes (bin, column) tasks: it sums the
+//      column over the bin's units, converts the sum once to 64-bit fixed point and adds it to
+//      the CTA node table (one add per bin and column, no two threads on the same word).
 // The bins, units and lanes are a function of the sub-tile's contents only, and integer
 // addition is associative: the gridpoint sums are bit-reproducible.
 #include <algorithm>
+#include <cstddef>
 
 #include "lpdf_device.cuh"
 
@@ -30,22 +31,22 @@ namespace lpdf {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 128;
 constexpr int kWarps = kThreads / 32;
 constexpr int kPPT = 4;                       // particles per thread per sub-tile
-constexpr int kT = kThreads * kPPT;           // sub-tile: 1024 particles
-constexpr int kUnit = 8;                      // particles per accumulation unit
-constexpr int kMaxBins = 256;                 // distinct new elements per sub-tile (more: direct path)
-constexpr int kHash = 512;                    // bin hash slots
+constexpr int kT = kThreads * kPPT;           // sub-tile: 512 particles
+constexpr int kUnit = 6;                      // particles per accumulation unit
+constexpr int kMaxBins = kThreads;            // distinct new elements per sub-tile (more: direct path)
+constexpr int kHash = 2 * kThreads;           // bin hash slots
 constexpr int kMaxUnits = kT / kUnit + kMaxBins;
 constexpr unsigned short kNoBin = 0xFFFF;
-constexpr int kGroup = 8;                     // lanes per hand-over of unit partials
+constexpr int kScrPitch = kThreads + 1;       // hand-over scratch: [column][unit], padded
 
 template <int NS>
 struct Smem {
     static constexpr int NF = 8 + NS;         // x, y, u, v, w, omega, psi[NS], elem, pid
     static constexpr int NQ = 11 + 2 * NS;
-    static constexpr int NT = NS <= 2 ? 256 : 128;   // node-table slots
+    static constexpr int NT = 128;            // node-table slots
     static constexpr int F_X = 0, F_Y = 1, F_U = 2, F_V = 3, F_W = 4, F_OM = 5, F_PSI = 6, F_ELEM = 6 + NS,
                          F_PID = 7 + NS;
     alignas(128) float tile[NF][kT];          // bulk-copy rows (16-byte aligned)
@@ -59,17 +60,25 @@ struct Smem {
     unsigned short bstart[kMaxBins + 1];
     unsigned short ustart[kMaxBins + 1];
     short cslot[kMaxBins][3];                 // node-table slot of each bin's corners (-1: global)
-    float scr[kWarps][kGroup][3 * NQ];        // unit partials on their way to the column owners
-    int sbin[kWarps][kGroup];
     int wsum[kWarps];
     int nbins, nunits, tfill, abort;
     NodeTable<NQ, NT> table;
     unsigned long long bar;
 };
 
-static_assert(sizeof(Smem<1>) <= 112 * 1024 && sizeof(Smem<2>) <= 112 * 1024 && sizeof(Smem<3>) <= 112 * 1024 &&
-                  sizeof(Smem<4>) <= 112 * 1024,
-              "two CTAs per SM");
+// the hand-over scratch (3 NQ columns x kScrPitch) lives in the tile and lam rows
+template <int NS>
+constexpr bool scratch_fits()
+{
+    return offsetof(Smem<NS>, lam) == sizeof(((Smem<NS>*)nullptr)->tile) &&
+           (size_t)3 * Smem<NS>::NQ * kScrPitch * sizeof(float) <=
+               sizeof(((Smem<NS>*)nullptr)->tile) + sizeof(((Smem<NS>*)nullptr)->lam);
+}
+static_assert(scratch_fits<1>() && scratch_fits<2>() && scratch_fits<3>() && scratch_fits<4>(), "scratch");
+// four CTAs per SM: 228 KB of shared memory per SM, 1 KB of it reserved per CTA
+static_assert(sizeof(Smem<1>) <= 56 * 1024 && sizeof(Smem<2>) <= 56 * 1024 && sizeof(Smem<3>) <= 56 * 1024 &&
+                  sizeof(Smem<4>) <= 56 * 1024,
+              "four CTAs per SM");
 
 // exclusive block scan over kThreads threads; `total` gets the sum. Contains two barriers.
 __device__ __forceinline__ int block_scan(int v, int* wsum, int& total)
@@ -95,7 +104,8 @@ __device__ __forceinline__ int block_scan(int v, int* wsum, int& total)
     return off + incl - v;
 }
 
-__device__ __forceinline__ unsigned hash_slot(int key) { return ((unsigned)key * 2654435761u) >> 23; }   // 9 bits
+__device__ __forceinline__ unsigned hash_slot(int key) { return ((unsigned)key * 2654435761u) >> 24; }   // 8 bits
+static_assert(kHash == 256, "hash_slot gives 8 bits");
 
 // node-table slot of `node`, counting new insertions in `fill`
 template <int NQ, int NT>
@@ -120,111 +130,34 @@ __device__ __forceinline__ int table_slot_counted(NodeTable<NQ, NT>& T, int node
 }
 
 // ------------------------------------------------------------------------------------------
-// Eq. 4, 5, 9 (IEM), 2; wrap and reflection; sources, for the particle in tile column t.
-// The new state replaces the old one in the tile; the element row keeps the walk's start
-// (the old element, or 0 when it is outside the mesh: `bad`).
+// The particle in tile column t: advanced in place (the element row keeps the walk's start).
 // ------------------------------------------------------------------------------------------
 template <int NS>
 __device__ __forceinline__ void advance_state(const DevMesh& M, const float* __restrict__ F, const StepParams& P,
                                               Smem<NS>& sm, int t, unsigned& err, bool& bad)
 {
     using SM = Smem<NS>;
-    constexpr int NFP = (22 + NS + 3) / 4 * 4;
-    const float x = sm.tile[SM::F_X][t], y = sm.tile[SM::F_Y][t];
-    const float u = sm.tile[SM::F_U][t], v = sm.tile[SM::F_V][t], w = sm.tile[SM::F_W][t];
-    const float om = sm.tile[SM::F_OM][t];
-    const int elem = __float_as_int(sm.tile[SM::F_ELEM][t]);
-    const uint32_t pid = __float_as_uint(sm.tile[SM::F_PID][t]);
-    bad = (unsigned)elem >= (unsigned)M.n_tri;
-    const int e = bad ? 0 : elem;
-    const float4 X = __ldg(&M.ex[e]);
-    const float4 Y = __ldg(&M.ey[e]);
-    const int4 V = __ldg(&M.ev[e]);
-    float l0, l1, l2;
-    barycentric(X, Y, x, y, l0, l1, l2);
-    // linear shape-function interpolation of the node fields
-    float Fi[NFP];
-    {
-        const float4* R0 = reinterpret_cast<const float4*>(F) + (size_t)V.x * (NFP / 4);
-        const float4* R1 = reinterpret_cast<const float4*>(F) + (size_t)V.y * (NFP / 4);
-        const float4* R2 = reinterpret_cast<const float4*>(F) + (size_t)V.z * (NFP / 4);
+    ParticleState<NS> q;
+    q.x = sm.tile[SM::F_X][t];
+    q.y = sm.tile[SM::F_Y][t];
+    q.u = sm.tile[SM::F_U][t];
+    q.v = sm.tile[SM::F_V][t];
+    q.w = sm.tile[SM::F_W][t];
+    q.om = sm.tile[SM::F_OM][t];
 #pragma unroll
-        for (int q = 0; q < NFP / 4; ++q) {
-            const float4 a = __ldg(R0 + q), b = __ldg(R1 + q), c = __ldg(R2 + q);
-            Fi[4 * q + 0] = fmaf(l0, a.x, fmaf(l1, b.x, l2 * c.x));
-            Fi[4 * q + 1] = fmaf(l0, a.y, fmaf(l1, b.y, l2 * c.y));
-            Fi[4 * q + 2] = fmaf(l0, a.z, fmaf(l1, b.z, l2 * c.z));
-            Fi[4 * q + 3] = fmaf(l0, a.w, fmaf(l1, b.w, l2 * c.w));
-        }
-    }
-    // Wiener increments: Philox blocks 0 and 1 of counter (pid, step, 0<<16 | block)
-    const uint4 r0 = philox4x32_10(make_uint4(pid, P.step_lo, P.step_hi, 0u), P.key0, P.key1);
-    const uint4 r1 = philox4x32_10(make_uint4(pid, P.step_lo, P.step_hi, 1u), P.key0, P.key1);
-    float z0, z1, z2, z3, z4, z5;
-    box_muller(r0.x, r0.y, z0, z1);
-    box_muller(r0.z, r0.w, z2, z3);
-    box_muller(r1.x, r1.y, z4, z5);
-    const float dW1 = P.sdt * z0, dW2 = P.sdt * z1;
-    const float c0e = sqrtf(fmaxf(Fi[LPDF_F_C0EPS], 0.0f));
-    const float Ur = u - Fi[LPDF_F_U + 0], Vr = v - Fi[LPDF_F_U + 1], Wr = w - Fi[LPDF_F_U + 2];
-    // Eq. 4
-    float un = u + (-Fi[LPDF_F_DPDX] + P.nu2 * Fi[LPDF_F_LAPU] + Fi[LPDF_F_G11] * Ur + Fi[LPDF_F_G11 + 1] * Vr) * P.dt
-             + P.s2nu * (Fi[LPDF_F_DUDX] * dW1 + Fi[LPDF_F_DUDX + 1] * dW2) + c0e * (P.sdt * z2);
-    float vn = v + (-Fi[LPDF_F_DPDX + 1] + P.nu2 * Fi[LPDF_F_LAPU + 1] + Fi[LPDF_F_G11 + 2] * Ur
-                    + Fi[LPDF_F_G11 + 3] * Vr) * P.dt
-             + P.s2nu * (Fi[LPDF_F_DUDX + 2] * dW1 + Fi[LPDF_F_DUDX + 3] * dW2) + c0e * (P.sdt * z3);
-    float wn = w + (P.nu2 * Fi[LPDF_F_LAPU + 2] + Fi[LPDF_F_G11 + 4] * Wr) * P.dt
-             + P.s2nu * (Fi[LPDF_F_DUDX + 4] * dW1 + Fi[LPDF_F_DUDX + 5] * dW2) + c0e * (P.sdt * z4);
-    // Eq. 5 (S_omega of Eq. 6 is a node field)
-    const float Om = Fi[LPDF_F_OMEGA];
-    float omn = om - P.C3 * Om * (om - Om) * P.dt - Fi[LPDF_F_SOMEGA] * Om * om * P.dt
-              + sqrtf(2.0f * P.C3 * P.C4 * Om * Om * fmaxf(om, 0.0f)) * (P.sdt * z5);
-    omn = fabsf(omn);
-    // Eq. 9, IEM form: 1/t_m = C_phi <omega> / 2
-    const float mix = P.half_cphi * Om * P.dt;
-    float psi[NS];
+    for (int a = 0; a < NS; ++a) q.psi[a] = sm.tile[SM::F_PSI + a][t];
+    q.elem = __float_as_int(sm.tile[SM::F_ELEM][t]);
+    q.pid = __float_as_uint(sm.tile[SM::F_PID][t]);
+    advance_particle<NS>(M, F, P, q, err, bad);
+    sm.tile[SM::F_X][t] = q.x;
+    sm.tile[SM::F_Y][t] = q.y;
+    sm.tile[SM::F_U][t] = q.u;
+    sm.tile[SM::F_V][t] = q.v;
+    sm.tile[SM::F_W][t] = q.w;
+    sm.tile[SM::F_OM][t] = q.om;
 #pragma unroll
-    for (int a = 0; a < NS; ++a) {
-        const float ps = sm.tile[SM::F_PSI + a][t];
-        psi[a] = ps - (ps - Fi[LPDF_F_PHI0 + a]) * mix;
-    }
-    // Eq. 2 with the velocity at t_n and the same dW_1, dW_2
-    float qx = x + u * P.dt + P.s2nu * dW1;
-    float qy = y + v * P.dt + P.s2nu * dW2;
-    if (M.periodic) {
-        if (qx < M.x0) qx += M.period;
-        else if (qx >= M.x1) qx -= M.period;
-        if (qx < M.x0 || qx >= M.x1) qx -= floorf((qx - M.x0) / M.period) * M.period;   // moves > one period
-    }
-#pragma unroll 1
-    for (int it = 0; it < 8; ++it) {
-        if (qy < M.y0) { qy = 2.0f * M.y0 - qy; un = -un; vn = -vn; wn = -wn; }
-        else if (qy > M.y1) { qy = 2.0f * M.y1 - qy; un = 2.0f * P.lid_u - un; vn = -vn; wn = -wn; }
-        else if (!M.periodic && qx < M.x0) { qx = 2.0f * M.x0 - qx; un = -un; vn = -vn; wn = -wn; }
-        else if (!M.periodic && qx > M.x1) { qx = 2.0f * M.x1 - qx; un = -un; vn = -vn; wn = -wn; }
-        else break;
-    }
-    // half-open domain [x0, x1) x [y0, y1)
-    if (qx >= M.x1) qx = M.periodic ? M.x0 : nextafterf(M.x1, -CUDART_INF_F);
-    if (qy >= M.y1) qy = nextafterf(M.y1, -CUDART_INF_F);
-    // concentrated scalar sources
-    for (int q = 0; q < P.n_src; ++q)
-        if (in_source(qx, qy, P.src_x[q], P.src_y[q], P.src_r[q])) {
-#pragma unroll
-            for (int a = 0; a < NS; ++a)
-                if (a == P.src_alpha[q]) psi[a] = 1.0f;
-        }
-    if (!(isfinite(un) && isfinite(vn) && isfinite(wn) && isfinite(omn) && isfinite(qx) && isfinite(qy)))
-        err |= kErrNonFinite;
-    sm.tile[SM::F_X][t] = qx;
-    sm.tile[SM::F_Y][t] = qy;
-    sm.tile[SM::F_U][t] = un;
-    sm.tile[SM::F_V][t] = vn;
-    sm.tile[SM::F_W][t] = wn;
-    sm.tile[SM::F_OM][t] = omn;
-#pragma unroll
-    for (int a = 0; a < NS; ++a) sm.tile[SM::F_PSI + a][t] = psi[a];
-    sm.tile[SM::F_ELEM][t] = __int_as_float(e);
+    for (int a = 0; a < NS; ++a) sm.tile[SM::F_PSI + a][t] = q.psi[a];
+    sm.tile[SM::F_ELEM][t] = __int_as_float(q.elem);
 }
 
 // moment quantities of the particle in tile column t: 1, u, v, w, uu, uv, uw, vv, vw, ww, omega,
@@ -243,6 +176,16 @@ __device__ __forceinline__ void quantities(const Smem<NS>& sm, int t, float* q)
         q[11 + a] = ps;
         q[11 + NS + a] = ps * ps;
     }
+}
+
+// statistics node of corner c of bin b: the node-table key of its slot, else from the mesh
+template <int NS>
+__device__ __forceinline__ int bin_node(const Smem<NS>& sm, const DevMesh& M, int b, int c)
+{
+    const int slot = sm.cslot[b][c];
+    if (slot >= 0) return sm.table.key[slot];
+    const int4 mv = __ldg(&M.em[sm.binel[b]]);
+    return c == 0 ? mv.x : (c == 1 ? mv.y : mv.z);
 }
 
 template <int NS>
@@ -264,7 +207,7 @@ __device__ __forceinline__ void flush_table(Smem<NS>& sm, unsigned long long* __
 }
 
 template <int NS>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 4)
 pdf_step_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevState S, const float* __restrict__ F,
                 const __grid_constant__ StepParams P, unsigned long long* __restrict__ node_acc,
                 unsigned long long* __restrict__ status, int64_t tiles_per_cta, int use_bulk)
@@ -346,40 +289,45 @@ pdf_step_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevSt
                 badmask |= (unsigned)bad << j;
             }
         }
-        // ---- 2b. pooled neighbour walk over the thread's particles ----------------------------
+        // ---- 2b. pooled neighbour walk: two walks in flight per thread ---------------------------
         int mykey[kPPT];                       // new element per particle, -1 for none
 #pragma unroll
         for (int j = 0; j < kPPT; ++j) mykey[j] = -1;
         {
-            int j = 0, h = 0, e = -1, e0 = -1;
-            float px = 0.0f, py = 0.0f;
-            if (tid < nvalid) {
-                e = e0 = __float_as_int(sm.tile[SM::F_ELEM][tid]);
-                px = sm.tile[SM::F_X][tid];
-                py = sm.tile[SM::F_Y][tid];
-            } else {
-                j = kPPT;
-            }
-#pragma unroll 1
-            while (j < kPPT) {
-                float lam[3];
-                int next = -1;
-                const bool found = walk_test(M, e, px, py, lam, next);
-                const bool stop = found || next < 0 || h >= kHopCap;
-                if (!stop) {
-                    e = next;
-                    ++h;
-                    continue;
+            struct Walk {
+                int j, e, e0, h;
+                float px, py;
+            };
+            int jn = 0;                            // next particle of this thread to start
+            auto start = [&](Walk& w) {
+                const int t = jn * kThreads + tid;
+                if (jn < kPPT && t < nvalid) {
+                    w.j = jn++;
+                    w.e = w.e0 = __float_as_int(sm.tile[SM::F_ELEM][t]);
+                    w.px = sm.tile[SM::F_X][t];
+                    w.py = sm.tile[SM::F_Y][t];
+                    w.h = 0;
+                } else {
+                    w.j = -1;
+                    w.e = 0;
                 }
-                const int t = j * kThreads + tid;
-                int ne = e;
+            };
+            // one test of walk w; on a stop, record the particle and start the next one
+            auto step = [&](Walk& w, bool found, int next, float* lam) {
+                if (!(found || next < 0 || w.h >= kHopCap)) {
+                    w.e = next;
+                    ++w.h;
+                    return;
+                }
+                const int t = w.j * kThreads + tid;
+                int ne = w.e;
                 bool lost = !found;
-                hops += found ? h : (next < 0 ? h : kHopCap + 1);
+                hops += found ? w.h : (next < 0 ? w.h : kHopCap + 1);
                 if (lost) {
-                    ne = e0;
-                    barycentric(__ldg(&M.ex[ne]), __ldg(&M.ey[ne]), px, py, lam[0], lam[1], lam[2]);
+                    ne = w.e0;
+                    barycentric(__ldg(&M.ex[ne]), __ldg(&M.ey[ne]), w.px, w.py, lam[0], lam[1], lam[2]);
                 }
-                if ((badmask >> j) & 1u) lost = true;
+                if ((badmask >> w.j) & 1u) lost = true;
                 if (lost) {
                     err |= kErrLost;
                     atomicAdd(&status[1], 1ull);
@@ -389,20 +337,24 @@ pdf_step_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevSt
                 sm.lam[0][t] = lam[0];
                 sm.lam[1][t] = lam[1];
                 sm.lam[2][t] = lam[2];
-                // j is thread-divergent: select the register without dynamic indexing
+                // w.j is thread-divergent: select the register without dynamic indexing
 #pragma unroll
                 for (int jj = 0; jj < kPPT; ++jj)
-                    if (jj == j) mykey[jj] = ne;
-                ++j;
-                const int t2 = j * kThreads + tid;
-                if (j < kPPT && t2 < nvalid) {
-                    e = e0 = __float_as_int(sm.tile[SM::F_ELEM][t2]);
-                    px = sm.tile[SM::F_X][t2];
-                    py = sm.tile[SM::F_Y][t2];
-                    h = 0;
-                } else {
-                    j = kPPT;
-                }
+                    if (jj == w.j) mykey[jj] = ne;
+                start(w);
+            };
+            Walk A, B;
+            start(A);
+            start(B);
+#pragma unroll 1
+            while (A.j >= 0 || B.j >= 0) {
+                float la[3], lb[3];
+                int na = -1, nb = -1;
+                bool fa = false, fb = false;
+                if (A.j >= 0) fa = walk_test(M, A.e, A.px, A.py, la, na);
+                if (B.j >= 0) fb = walk_test(M, B.e, B.px, B.py, lb, nb);
+                if (A.j >= 0) step(A, fa, na, la);
+                if (B.j >= 0) step(B, fb, nb, lb);
             }
         }
         // ---- 3a. insert the new elements into the bin hash (one insert per distinct key of a row)
@@ -551,7 +503,8 @@ pdf_step_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevSt
                 const int ek = sm.binel[b];
                 if (!consistent(ek >= 0 && ek < M.n_tri, err)) { sm.cslot[b][c] = -1; continue; }
                 const int4 mv = __ldg(&M.em[ek]);
-                sm.cslot[b][c] = (short)table_slot_counted(sm.table, c == 0 ? mv.x : (c == 1 ? mv.y : mv.z), &sm.tfill);
+                const int node = c == 0 ? mv.x : (c == 1 ? mv.y : mv.z);
+                sm.cslot[b][c] = (short)table_slot_counted(sm.table, node, &sm.tfill);
             }
         }
         __syncthreads();
@@ -559,69 +512,57 @@ pdf_step_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevSt
         {
             const int nu = min(sm.nunits, kMaxUnits);
             const int nb = sm.nbins;
-            // warp-uniform rounds: lane `lane` of warp `wid` takes unit r * kThreads + wid * 32 + lane
-#pragma unroll 1
-            for (int ub = wid * 32; ub < nu; ub += kThreads) {
-                const int u = ub + lane;
-                int b = -1;
-                float acc[NK];
+            float acc[NK];
+            // accumulate unit u into acc (sorted positions of its bin, two particles per pass)
+            auto accumulate = [&](int u, int b) {
 #pragma unroll
                 for (int k = 0; k < NK; ++k) acc[k] = 0.0f;
-                if (u < nu) {
-                    b = sm.ubin[u];
-                    if (!consistent(b < nb, err)) b = -1;
-                }
-                if (b >= 0) {
-                    const int p0 = sm.bstart[b] + (u - sm.ustart[b]) * kUnit;
-                    const int p1 = min(p0 + kUnit, (int)sm.bstart[b + 1]);
+                const int p0 = sm.bstart[b] + (u - sm.ustart[b]) * kUnit;
+                const int p1 = min(p0 + kUnit, (int)sm.bstart[b + 1]);
+                int p = p0;
 #pragma unroll 1
-                    for (int p = p0; p < p1; ++p) {
-                        const int t = sm.perm[p];
-                        if (!consistent(t < kT, err)) break;
-                        const float l0 = sm.lam[0][t], l1 = sm.lam[1][t], l2 = sm.lam[2][t];
-                        float q[NQ];
-                        quantities<NS>(sm, t, q);
+                for (; p + 1 < p1; p += 2) {
+                    const int t0 = sm.perm[p], t1 = sm.perm[p + 1];
+                    if (!consistent(t0 < kT && t1 < kT, err)) return;
+                    const float a0 = sm.lam[0][t0], a1 = sm.lam[1][t0], a2 = sm.lam[2][t0];
+                    const float c0 = sm.lam[0][t1], c1 = sm.lam[1][t1], c2 = sm.lam[2][t1];
+                    float q0[NQ], q1[NQ];
+                    quantities<NS>(sm, t0, q0);
+                    quantities<NS>(sm, t1, q1);
 #pragma unroll
-                        for (int k = 0; k < NQ; ++k) {
-                            acc[k] = fmaf(l0, q[k], acc[k]);
-                            acc[NQ + k] = fmaf(l1, q[k], acc[NQ + k]);
-                            acc[2 * NQ + k] = fmaf(l2, q[k], acc[2 * NQ + k]);
-                        }
+                    for (int k = 0; k < NQ; ++k) {
+                        acc[k] = fmaf(c0, q1[k], fmaf(a0, q0[k], acc[k]));
+                        acc[NQ + k] = fmaf(c1, q1[k], fmaf(a1, q0[k], acc[NQ + k]));
+                        acc[2 * NQ + k] = fmaf(c2, q1[k], fmaf(a2, q0[k], acc[2 * NQ + k]));
                     }
                 }
-                // hand-over, kGroup lanes at a time: lane k owns columns k and k + 32
+                if (p < p1) {
+                    const int t0 = sm.perm[p];
+                    if (!consistent(t0 < kT, err)) return;
+                    const float a0 = sm.lam[0][t0], a1 = sm.lam[1][t0], a2 = sm.lam[2][t0];
+                    float q0[NQ];
+                    quantities<NS>(sm, t0, q0);
+#pragma unroll
+                    for (int k = 0; k < NQ; ++k) {
+                        acc[k] = fmaf(a0, q0[k], acc[k]);
+                        acc[NQ + k] = fmaf(a1, q0[k], acc[NQ + k]);
+                        acc[2 * NQ + k] = fmaf(a2, q0[k], acc[2 * NQ + k]);
+                    }
+                }
+            };
+            // units beyond the first kThreads (sub-tiles spread over many elements): added
+            // straight to the node table, one unit at a time
 #pragma unroll 1
-                for (int g = 0; g < 32; g += kGroup) {
-                    if (lane >= g && lane < g + kGroup) {
+            for (int u = tid + kThreads; u < nu; u += kThreads) {
+                const int b = sm.ubin[u];
+                if (!consistent(b < nb, err)) continue;
+                accumulate(u, b);
 #pragma unroll
-                        for (int k = 0; k < NK; ++k) sm.scr[wid][lane - g][k] = acc[k];
-                        sm.sbin[wid][lane - g] = b;
-                    }
-                    __syncwarp();
+                for (int c = 0; c < 3; ++c)
 #pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-                        const int k = lane + 32 * kk;
-                        if (k >= NK) break;
-                        const int c = k / NQ, q = k - c * NQ;
-                        int cur = -1;
-                        float sum = 0.0f;
-#pragma unroll
-                        for (int l = 0; l <= kGroup; ++l) {
-                            const int bl = l < kGroup ? sm.sbin[wid][l] : -2;
-                            if (bl != cur) {
-                                if (cur >= 0) {
-                                    const int4 mv = __ldg(&M.em[sm.binel[cur]]);
-                                    table_add(sm.table, (int)sm.cslot[cur][c], c == 0 ? mv.x : (c == 1 ? mv.y : mv.z),
-                                              q, to_fixed(sum, err), node_acc);
-                                }
-                                cur = bl;
-                                sum = 0.0f;
-                            }
-                            if (l < kGroup) sum += sm.scr[wid][l][k];
-                        }
-                    }
-                    __syncwarp();
-                }
+                    for (int k = 0; k < NQ; ++k)
+                        table_add(sm.table, (int)sm.cslot[b][c], bin_node(sm, M, b, c), k,
+                                  to_fixed(acc[c * NQ + k], err), node_acc);
             }
             // particles without a bin (more than kMaxBins distinct elements in the sub-tile)
 #pragma unroll 1
@@ -639,6 +580,37 @@ pdf_step_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevSt
                         if (v != 0) atomicAdd(&node_acc[(size_t)nd[c] * NQ + k], (unsigned long long)v);
                     }
                 }
+            }
+            // the first kThreads units: one per thread
+            int b = -1;
+            if (tid < nu) {
+                b = sm.ubin[tid];
+                if (consistent(b < nb, err)) accumulate(tid, b);
+                else b = -1;
+            }
+            if (b < 0) {
+#pragma unroll
+                for (int k = 0; k < NK; ++k) acc[k] = 0.0f;
+            }
+            // every read of the tile (and the bulk store's) is over: the tile becomes the scratch
+            if (tid == 0) bulk_wait_read_all();
+            __syncthreads();
+            float* const scr = &sm.tile[0][0];
+#pragma unroll
+            for (int k = 0; k < NK; ++k) scr[k * kScrPitch + tid] = acc[k];
+            __syncthreads();
+            // (bin, column) tasks: the column summed over the bin's units (those of the first kThreads)
+            const int ntask = nb * NK;
+#pragma unroll 1
+            for (int i = tid; i < ntask; i += kThreads) {
+                const int bb = i / NK, k = i - (i / NK) * NK;
+                const int c = k / NQ, q = k - c * NQ;
+                const int u0 = sm.ustart[bb], u1 = min((int)sm.ustart[bb + 1], kThreads);
+                const float* col = scr + k * kScrPitch;
+                float sum = 0.0f;
+                for (int u = u0; u < u1; ++u) sum += col[u];
+                if (u1 > u0)
+                    table_add(sm.table, (int)sm.cslot[bb][c], bin_node(sm, M, bb, c), q, to_fixed(sum, err), node_acc);
             }
         }
         // generic reads of the tile are done before the next bulk load overwrites it
@@ -675,8 +647,8 @@ cudaError_t launch_step_ns(const DevMesh& m, const DevState& s, const float* fie
     }
     const int64_t ntiles = (s.n + kT - 1) / kT;
     if (ntiles == 0) return cudaSuccess;
-    // persistent CTAs, two per SM, each on a contiguous range of sub-tiles
-    const int64_t grid = std::min<int64_t>(ntiles, 2 * (int64_t)n_sm);
+    // persistent CTAs, four per SM, each on a contiguous range of sub-tiles
+    const int64_t grid = std::min<int64_t>(ntiles, 4 * (int64_t)n_sm);
     const int64_t per = (ntiles + grid - 1) / grid;
     const int64_t used = (ntiles + per - 1) / per;
     // bulk copies need 16-byte aligned rows: every base pointer and the psi row stride

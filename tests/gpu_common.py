@@ -46,6 +46,21 @@ def gpu_step(ctx: lpdf.Context, fields_dev, st: wl.State, step: int):
     return out, S.cpu().numpy(), rc, status
 
 
+def match_pids(want, have):
+    """Indices into `have` that list the same pids as `want` (both permutations of one set)."""
+    want = np.asarray(want).astype(np.int64)
+    have = np.asarray(have).astype(np.int64)
+    ih = np.argsort(have, kind="stable")
+    pos = np.searchsorted(have[ih], want)
+    assert np.all(pos < have.size) and np.array_equal(have[ih][pos], want), "the step lost or invented particles"
+    return ih[pos]
+
+
+def reorder(st: wl.State, idx) -> wl.State:
+    return wl.State(*(np.ascontiguousarray(getattr(st, k)[idx]) for k in FIELDS), np.ascontiguousarray(st.psi[:, idx]),
+                    np.ascontiguousarray(st.elem[idx]), np.ascontiguousarray(st.pid[idx]))
+
+
 def compare_step(mesh: wl.Mesh, om: oracle.OracleMesh, params: lpdf.Params, F, st_in: wl.State, step: int,
                  g: wl.State, check_locate: bool = True):
     """Per-stage parity of one step from the same input state.
@@ -57,6 +72,9 @@ def compare_step(mesh: wl.Mesh, om: oracle.OracleMesh, params: lpdf.Params, F, s
        position (bit-exact).
     Returns a dict of diagnostics."""
     ns = params.ns
+    # the step may list its output in another order (it keeps the ensemble in element order):
+    # match the particles by pid
+    g = reorder(g, match_pids(st_in.pid, g.pid))
     op = oracle_params(params)
     res, oelem, aux, lost = oracle.pdf_step(om, op, F, st_in, step)
     assert lost == 0

@@ -44,7 +44,7 @@ def test_params_struct_layout_matches_header():
     p = lpdf.Params()
     lpdf.lib().lpdf_params_default(ctypes.byref(p))
     assert (p.C3, p.C4, p.Cphi, p.C0, p.Comega1, p.Comega2) == (5.0, 0.25, 2.0, 2.1, 0.5, 0.73)
-    assert p.ns == 1 and p.n_sources == 0 and p.sort_every == 0 and p.seed == 1
+    assert p.ns == 1 and p.n_sources == 0 and p.seed == 1
 
 
 def test_params_struct_size_matches_header():

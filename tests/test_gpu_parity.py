@@ -206,18 +206,17 @@ def test_sort_rebuckets_deterministically(torch_cuda):
     assert np.array_equal(g.psi, sp.psi[:, idx])
 
 
-def test_step_with_periodic_rebucketing_matches_step_without(torch_cuda):
-    """sort_every only changes the order: per-pid state after 3 steps is bit-identical."""
+def test_explicit_rebucketing_changes_only_the_order(torch_cuda):
+    """lpdf_sort between steps changes only the order: per-pid state after 3 steps is bit-identical."""
     wk = wl.channel_small()
     mesh, gm, om, params, F, Fd, ctx, npe = _setup(wk, n_per_elem=10)
     st = wl.synthetic_state(mesh, npe, wk.ns, seed=42)
-    p2 = lpdf.params_for(wk)
-    p2.sort_every = 2
-    ctx2 = lpdf.Context(gm, p2, st.n)
+    ctx2 = lpdf.Context(gm, lpdf.params_for(wk), st.n)
     ctx.set_state(gc.torch_state(st))
     ctx2.set_state(gc.torch_state(st))
     for step in range(3):
         ctx.pdf_step(Fd, step)
+        ctx2.sort()
         ctx2.pdf_step(Fd, step)
     a = gc.host_state(ctx.get_state(), wk.ns)
     b = gc.host_state(ctx2.get_state(), wk.ns)
@@ -225,3 +224,26 @@ def test_step_with_periodic_rebucketing_matches_step_without(torch_cuda):
     for k in gc.FIELDS:
         assert np.array_equal(getattr(a, k)[ia], getattr(b, k)[ib])
     assert np.array_equal(a.elem[ia], b.elem[ib])
+
+
+@pytest.mark.parametrize("workload", ["channel", "cavity"])
+def test_consecutive_steps_through_the_element_order(torch_cuda, workload):
+    """Steps without set_state in between: each step gathers its input through the element order
+    the previous step left behind. Every step matches the oracle run from that step's input
+    (matched by pid), and the moments match the oracle's reduction of each new state."""
+    import torch
+    wk = wl.channel_small() if workload == "channel" else wl.cavity_small()
+    mesh, gm, om, params, F, Fd, ctx, npe = _setup(wk, n_per_elem=25)
+    st = wl.synthetic_state(mesh, npe, wk.ns, seed=43)
+    ctx.set_state(gc.torch_state(st))
+    for step in range(4):
+        before = gc.host_state(ctx.get_state(), wk.ns)
+        ctx.pdf_step(Fd, step)
+        rc, status = ctx.status(raise_on_error=False)
+        assert rc == lpdf.LPDF_OK, status
+        after = gc.host_state(ctx.get_state(), wk.ns)
+        S = torch.empty((mesh.n_nodes, 11 + 2 * wk.ns), dtype=torch.float64, device="cuda")
+        ctx.grid_statistics(S, raw=True)
+        torch.cuda.synchronize()
+        gc.compare_step(mesh, om, params, F, before, step, after, check_locate=(step == 3))
+        gc.compare_moments(om, after, S.cpu().numpy(), wk.ns)
