@@ -34,9 +34,9 @@ UNIT = "particle-updates/s"
 # algorithmic bytes of one particle update (ns = 1): read x, y, u, v, w, omega, psi, elem, pid
 # (36 B) and write x, y, u, v, w, omega, psi, elem (32 B)
 BYTES_PER_UPDATE = 68
-# kernels of one lpdf_pdf_step: advance, 3 scan kernels, record scatter, record offsets, particle
-# scatter, moments
-LAUNCHES_PER_STEP = 8
+# kernels of one lpdf_pdf_step: advance, histogram, 3 scan kernels, record scatter, record offsets,
+# particle scatter, moments
+LAUNCHES_PER_STEP = 9
 
 
 def _env_int(k, d):

@@ -5,9 +5,10 @@
 //   K1  advance_kernel: thread i takes the particle perm[i] of the current buffer (perm lists the
 //       buffer in element order), advances it (Eq. 4, 5, 9, 2, wrap, reflection, sources),
 //       locates it with the barycentric neighbour walk and writes it to position i of the next
-//       buffer. Each 256-particle block also counts its particles per new element (a sparse
-//       histogram: one record per distinct element) and gives every particle its rank among the
-//       block's particles of the same element, in position order.
+//       buffer. No barriers: a thread's walk never waits for another's.
+//   H   histogram_kernel: each 256-particle block of the next buffer counts its particles per new
+//       element (a sparse histogram: one record per distinct element) and gives every particle
+//       its rank among the block's particles of the same element, in position order.
 //   S1  exclusive scans: particles per element -> bucket starts; records per element -> list starts.
 //   S2  record_scatter_kernel: every record joins its element's record list.
 //   S3  key_offsets_kernel (a warp per element): the element's records in block order, and each
@@ -66,29 +67,15 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int& total
 // K1
 // ------------------------------------------------------------------------------------------
 template <int NS>
-__global__ void __launch_bounds__(kBlk, 3)
+__global__ void __launch_bounds__(kBlk, 4)
 advance_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevState cur,
                const __grid_constant__ DevState nxt, const int* __restrict__ perm, const float* __restrict__ F,
-               const __grid_constant__ StepParams P, uint16_t* __restrict__ rrank, int* __restrict__ rec_key,
-               int* __restrict__ rec_cnt, int* __restrict__ nrec, int* __restrict__ kcnt, int* __restrict__ krc,
-               unsigned long long* __restrict__ status)
+               const __grid_constant__ StepParams P, unsigned long long* __restrict__ status)
 {
-    __shared__ int hkey[kRecHash];
-    __shared__ __align__(16) unsigned short hcnt[kRecHash][kBlk / 32];
-    __shared__ int hrec[kRecHash];
-    __shared__ int wsum[kBlk / 32];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const unsigned lt = (1u << lane) - 1u;
-    for (int s = tid; s < kRecHash; s += kBlk) hkey[s] = -1;
-    {
-        uint4* z = reinterpret_cast<uint4*>(&hcnt[0][0]);
-        constexpr int n16 = (int)(sizeof(hcnt) / sizeof(uint4));
-        for (int k = tid; k < n16; k += kBlk) z[k] = make_uint4(0u, 0u, 0u, 0u);
-    }
-    const int64_t i = (int64_t)blockIdx.x * kBlk + tid;
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x;
     unsigned err = 0;
     int hops = 0;
-    int key = -1;
     if (i < cur.n) {
         const int src = perm[i];
         ParticleState<NS> p;
@@ -141,10 +128,41 @@ advance_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevSta
         for (int a = 0; a < NS; ++a) nxt.psi[(size_t)a * nxt.cap + i] = p.psi[a];
         nxt.elem[i] = ne;
         nxt.pid[i] = p.pid;
-        key = ne;
     }
+    const unsigned e_or = __reduce_or_sync(kFull, err);
+    const int h_sum = __reduce_add_sync(kFull, hops);
+    if (lane == 0) {
+        if (e_or) atomicOr(&status[0], (unsigned long long)e_or);
+        if (h_sum) atomicAdd(&status[3], (unsigned long long)h_sum);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// H
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlk) histogram_kernel(const int* __restrict__ elem, int64_t n,
+                                                         uint16_t* __restrict__ rrank, int* __restrict__ rec_key,
+                                                         int* __restrict__ rec_cnt, int* __restrict__ nrec,
+                                                         int* __restrict__ kcnt, int* __restrict__ krc,
+                                                         unsigned long long* __restrict__ status)
+{
+    __shared__ int hkey[kRecHash];
+    __shared__ __align__(16) unsigned short hcnt[kRecHash][kBlk / 32];
+    __shared__ int hrec[kRecHash];
+    __shared__ int wsum[kBlk / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int s = tid; s < kRecHash; s += kBlk) hkey[s] = -1;
+    {
+        uint4* z = reinterpret_cast<uint4*>(&hcnt[0][0]);
+        constexpr int n16 = (int)(sizeof(hcnt) / sizeof(uint4));
+        for (int k = tid; k < n16; k += kBlk) z[k] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    const int64_t i = (int64_t)blockIdx.x * kBlk + tid;
+    const int key = i < n ? elem[i] : -1;
+    unsigned err = 0;
     __syncthreads();
-    // ---- sparse histogram of the new elements: one insert per distinct element of a warp
+    // one insert per distinct element of a warp
     const unsigned m = __match_any_sync(kFull, key);
     const int leader = __ffs(m) - 1;
     int slot = -1;
@@ -199,11 +217,7 @@ advance_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevSta
             rrank[i] = (uint16_t)((hrec[slot] << 8) | (hcnt[slot][wid] + rank_w));
     }
     const unsigned e_or = __reduce_or_sync(kFull, err);
-    const int h_sum = __reduce_add_sync(kFull, hops);
-    if (lane == 0) {
-        if (e_or) atomicOr(&status[0], (unsigned long long)e_or);
-        if (h_sum) atomicAdd(&status[3], (unsigned long long)h_sum);
-    }
+    if (lane == 0 && e_or) atomicOr(&status[0], (unsigned long long)e_or);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -472,8 +486,9 @@ cudaError_t run_pipeline(const DevMesh& m, const DevState& cur, const DevState& 
     int* kcnt = w.kwork;
     int* krc = w.kwork + (E + 1);
     int* kcur = w.kwork + 2 * (E + 1);
-    advance_kernel<NS><<<(unsigned)nblk, kBlk, 0, st>>>(m, cur, nxt, w.perm, fields, p, w.rrank, w.rec_key, w.rec_cnt,
-                                                        w.nrec, kcnt, krc, status);
+    advance_kernel<NS><<<(unsigned)nblk, kBlk, 0, st>>>(m, cur, nxt, w.perm, fields, p, status);
+    histogram_kernel<<<(unsigned)nblk, kBlk, 0, st>>>(nxt.elem, n, w.rrank, w.rec_key, w.rec_cnt, w.nrec, kcnt, krc,
+                                                      status);
     e = scan_pair(kcnt, w.kstart, krc, w.krstart, E + 1, w.scan_part, st);
     if (e != cudaSuccess) return e;
     record_scatter_kernel<<<(unsigned)nblk, kBlk, 0, st>>>(w.nrec, w.rec_key, w.krstart, kcur, w.klist);
