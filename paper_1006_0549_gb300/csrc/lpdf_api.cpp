@@ -62,6 +62,7 @@ cudaError_t alloc_pipe(PipeScratch& w, int64_t cap, size_t E)
 void free_mesh_device(DevMesh& d)
 {
     cudaFree(d.ex); cudaFree(d.ey); cudaFree(d.en); cudaFree(d.ev); cudaFree(d.em); cudaFree(d.master);
+    cudaFree(d.ea); cudaFree(d.eb);
     d = DevMesh();
 }
 
@@ -162,7 +163,7 @@ int lpdf_mesh_load(const double* node_xy, int32_t n_nodes, const int32_t* tri, i
     const bool periodic = period_x > 0.0;
     if (periodic && (float)(x1 - x0) != (float)period_x)
         return fail(LPDF_ERR_MESH, "period %.9g differs from the x extent %.9g", period_x, x1 - x0);
-    std::vector<float> ex(4 * (size_t)n_tri), ey(4 * (size_t)n_tri);
+    std::vector<float> ex(4 * (size_t)n_tri), ey(4 * (size_t)n_tri), ea(4 * (size_t)n_tri), eb(4 * (size_t)n_tri);
     std::vector<int32_t> en(4 * (size_t)n_tri, -1), ev(4 * (size_t)n_tri, 0), em(4 * (size_t)n_tri, 0);
     for (int e = 0; e < n_tri; ++e) {
         const int* t = tri + 3 * e;
@@ -177,6 +178,14 @@ int lpdf_mesh_load(const double* node_xy, int32_t n_nodes, const int32_t* tri, i
         ex[4 * e + 3] = (float)((ax + bx + cx) / 3.0);
         ey[4 * e + 0] = (float)ay; ey[4 * e + 1] = (float)by; ey[4 * e + 2] = (float)cy;
         ey[4 * e + 3] = (float)(1.0 / A);
+        ea[4 * e + 0] = (float)ax;
+        ea[4 * e + 1] = (float)ay;
+        ea[4 * e + 2] = (float)((cy - ay) / A);
+        ea[4 * e + 3] = (float)(-(cx - ax) / A);
+        eb[4 * e + 0] = (float)(-(by - ay) / A);
+        eb[4 * e + 1] = (float)((bx - ax) / A);
+        eb[4 * e + 2] = ex[4 * e + 3];
+        eb[4 * e + 3] = 0.0f;
         for (int k = 0; k < 3; ++k) ev[4 * e + k] = t[k];
         ev[4 * e + 3] = 0;
         en[4 * e + 3] = 0;   // bit k: edge k is periodic
@@ -267,6 +276,9 @@ int lpdf_mesh_load(const double* node_xy, int32_t n_nodes, const int32_t* tri, i
     if ((ce = dalloc(&d.ex, n_tri)) != cudaSuccess || (ce = dalloc(&d.ey, n_tri)) != cudaSuccess ||
         (ce = dalloc(&d.en, n_tri)) != cudaSuccess || (ce = dalloc(&d.ev, n_tri)) != cudaSuccess ||
         (ce = dalloc(&d.em, n_tri)) != cudaSuccess || (ce = dalloc(&d.master, n_nodes)) != cudaSuccess ||
+        (ce = dalloc(&d.ea, n_tri)) != cudaSuccess || (ce = dalloc(&d.eb, n_tri)) != cudaSuccess ||
+        (ce = cudaMemcpy(d.ea, ea.data(), sizeof(float) * ea.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (ce = cudaMemcpy(d.eb, eb.data(), sizeof(float) * eb.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (ce = cudaMemcpy(d.ex, ex.data(), sizeof(float) * ex.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (ce = cudaMemcpy(d.ey, ey.data(), sizeof(float) * ey.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (ce = cudaMemcpy(d.en, en.data(), sizeof(int32_t) * en.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||

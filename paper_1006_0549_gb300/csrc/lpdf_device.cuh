@@ -200,6 +200,40 @@ __device__ __forceinline__ bool walk_test(const DevMesh& M, int e, float px, flo
     return false;
 }
 
+// The walk test in the affine barycentric form relative to vertex 0, with a certified error
+// bound: 1 = (px, py) is strictly inside e; 0 = it is certainly outside, leave through `next`
+// (the edge opposite the most negative lambda; -1 for a wall); -1 = undecided (within the
+// rounding bound of an edge, or in a periodic image frame): the caller runs walk_test.
+// Bound: with u = 2^-24, dx = fl(px - x_v0) (x_v0 exact in FP32) and the coefficients rounded
+// from FP64, |lambda_a' - lambda_a| <= 4.01 u (|b_a dx| + |g_a dy|) for a = 1, 2, and for
+// lambda_0 = 1 - lambda_1 - lambda_2 that sum plus 2 u (1 + |lambda_1| + |lambda_2|); the
+// constants below carry a margin for the rounding of the bounds themselves.
+__device__ __forceinline__ int walk_test_fast(const DevMesh& M, int e, float px, float py, int& next)
+{
+    const float4 A = __ldg(&M.ea[e]);
+    const float4 B = __ldg(&M.eb[e]);
+    const int4 N = __ldg(&M.en[e]);
+    if (M.periodic && fabsf(B.z - px) > 0.5f * M.period) return -1;
+    const float dx = __fsub_rn(px, A.x), dy = __fsub_rn(py, A.y);
+    const float t1 = A.z * dx, s1 = A.w * dy, t2 = B.x * dx, s2 = B.y * dy;
+    const float l1 = t1 + s1, l2 = t2 + s2;
+    const float l0 = (1.0f - l1) - l2;
+    const float E1 = 3.0e-7f * (fabsf(t1) + fabsf(s1)) + 1e-30f;
+    const float E2 = 3.0e-7f * (fabsf(t2) + fabsf(s2)) + 1e-30f;
+    const float E0 = E1 + E2 + 1.5e-7f * (1.0f + fabsf(l1) + fabsf(l2));
+    if (l0 > E0 && l1 > E1 && l2 > E2) return 1;
+    // the most negative lambda, lowest index on ties
+    int a = 0;
+    float lm = l0;
+    if (l1 < lm) { a = 1; lm = l1; }
+    if (l2 < lm) { a = 2; lm = l2; }
+    const float Ea = a == 0 ? E0 : (a == 1 ? E1 : E2);
+    if (!(lm < -Ea)) return -1;
+    // vertex a is opposite edge (a + 1) % 3 (edge k runs from vertex k to vertex k + 1)
+    next = a == 0 ? N.y : (a == 1 ? N.z : N.x);
+    return 0;
+}
+
 // The whole walk from element e: the owner of (px, py) (and its barycentrics), -1 on a wall
 // exit, -2 at the hop cap.
 __device__ __forceinline__ int locate_walk(const DevMesh& M, int e, float px, float py, int& hops, float lam[3])

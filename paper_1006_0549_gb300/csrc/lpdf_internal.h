@@ -33,6 +33,10 @@ struct DevMesh {
     int4* ev = nullptr;       // (node0, node1, node2, 0): geometric node ids (node-field rows)
     int4* em = nullptr;       // (master0, master1, master2, 0): statistics node ids
     int* master = nullptr;    // n_nodes
+    // affine barycentrics relative to vertex 0: lambda_1 = b1 dx + g1 dy, lambda_2 = b2 dx + g2 dy,
+    // lambda_0 = 1 - lambda_1 - lambda_2, (dx, dy) = p - vertex 0
+    float4* ea = nullptr;     // (x_v0, y_v0, b1, g1)
+    float4* eb = nullptr;     // (b2, g2, centroid x, 0)
 };
 
 struct StepParams {

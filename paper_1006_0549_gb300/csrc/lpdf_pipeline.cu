@@ -97,9 +97,13 @@ advance_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevSta
         bool lost = false;
 #pragma unroll 1
         for (;;) {
-            float lam[3];
             int next = -1;
-            if (walk_test(M, e, p.x, p.y, lam, next)) {
+            int r = walk_test_fast(M, e, p.x, p.y, next);
+            if (r < 0) {
+                float lam[3];
+                r = walk_test(M, e, p.x, p.y, lam, next) ? 1 : 0;
+            }
+            if (r == 1) {
                 ne = e;
                 hops += h;
                 break;
