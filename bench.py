@@ -55,25 +55,34 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+# the sources of the advance kernel: a traffic figure taken on other sources is stale
+KERNEL_SOURCES = ("lpdf_pipeline.cu", "lpdf_device.cuh", "lpdf_internal.h")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "advance_kernel_channel5M_traffic.txt")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1006_0549_gb300", "csrc"))):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_1006_0549_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload: str, n_particles: int):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "pdf_step_traffic.json")
-    if not os.path.exists(p):
+def ncu_traffic(n_particles: int):
+    """DRAM bytes (read + write) of one advance-kernel launch, from the committed summary of an
+    ncu capture of a smaller case scaled by the particles a launch processes; None when the
+    summary was taken on other kernel sources."""
+    if not os.path.exists(TRAFFIC_FILE):
         return None
-    with open(p) as f:
-        d = json.load(f)
+    d = {}
+    with open(TRAFFIC_FILE) as f:
+        for line in f:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                d[k.strip()] = v.strip()
     if d.get("kernel_source_hash") != kernel_source_hash():
         return None
-    per_particle = float(d["dram_bytes_per_launch"]) / float(d["particles"])
+    per_particle = (float(d["dram__bytes_read.sum"]) + float(d["dram__bytes_write.sum"])) / float(d["particles"])
     return per_particle * n_particles
 
 
@@ -175,6 +184,8 @@ def run_gpu(args, rank, world, dist):
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
+    ctx.set_timing(True)
+    ctx.timings()
     with ClockSampler(torch.cuda.current_device()) as clk:
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
@@ -189,6 +200,9 @@ def run_gpu(args, rank, world, dist):
     if dist is not None:
         dist.barrier()
     total_ms = t0.elapsed_time(t1)
+    kms, ksteps = ctx.timings()
+    ctx.set_timing(False)
+    kernel_ms = {"advance": kms[0] / ksteps, "rebucket": kms[1] / ksteps, "moments": kms[2] / ksteps}
     per = [a.elapsed_time(b) for a, b in ev]
     print("per-step ms:", " ".join(f"{x:.3f}" for x in per), file=sys.stderr)
     rc, status = ctx.status(raise_on_error=False)
@@ -213,7 +227,7 @@ def run_gpu(args, rank, world, dist):
         torch.cuda.synchronize()
         step += 1
     e2e_s = (time.perf_counter() - te) / Ke
-    return dict(P=P, total_ms=total_ms, per=per, clocks=clk.summary(), hops=hops, e2e_s=e2e_s,
+    return dict(P=P, total_ms=total_ms, per=per, kernel_ms=kernel_ms, clocks=clk.summary(), hops=hops, e2e_s=e2e_s,
                 h2d=int(h_fields.numel() * 4), d2h=int(h_stats.numel() * 8), wk=wk)
 
 
@@ -308,11 +322,12 @@ def main():
     K = args.steps
     ms_step = total_ms / K
     value = P_all * K / (total_ms * 1e-3)
-    per = r["per"]
-    kernel_ms = statistics.mean(per)
+    kms = r["kernel_ms"]
     peak, peak_kind = measured_peaks()
-    achieved = BYTES_PER_UPDATE * P / (kernel_ms * 1e-3) / 1e9
-    traffic = ncu_traffic("channel-50k-25M", P)
+    # the advance kernel reads and writes the whole state: the step's algorithmic bytes
+    achieved = BYTES_PER_UPDATE * P / (kms["advance"] * 1e-3) / 1e9
+    step_gbs = BYTES_PER_UPDATE * P / (ms_step * 1e-3) / 1e9
+    traffic = ncu_traffic(P)
     cpu_n, cpu_dt = cpu_baseline_sample(r["wk"], args.cpu_sample)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -325,8 +340,9 @@ def main():
                    "mean_walk_hops": r["hops"]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth",
-                     "kernel": "pdf_step_kernel", "bytes_per_update": BYTES_PER_UPDATE,
-                     "kernel_ms": kernel_ms},
+                     "kernel": "advance_kernel", "bytes_per_update": BYTES_PER_UPDATE,
+                     "kernel_ms": kms["advance"], "kernels_ms_per_step": kms,
+                     "step_achieved_gbs": step_gbs, "step_frac": step_gbs / peak},
         "cpu_baseline": {"value": cpu_n / cpu_dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{cpu_n} particles of the same workload, one FP64 step + gridpoint moments"},
         "clocks": r["clocks"],

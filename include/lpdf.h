@@ -156,7 +156,9 @@ int lpdf_get_state(const lpdf_ctx* ctx, float* x, float* y, float* u, float* v, 
 
 /* ---------------------------------------------------------------------------------------
  * lpdf_pdf_step -- one forward-Euler step of every particle, then the gridpoint moment sums
- * of the new state. async.
+ * of the new state. async. The step also re-buckets the ensemble by element (a stable counting
+ * sort on the new elements, kept as the gather order of the next step), so the order in which
+ * lpdf_get_state lists the particles changes from step to step; pid identifies them.
  *   node_fields device, n_nodes x nfp FP32 (columns LPDF_F_*), evaluated at each particle by
  *               the linear shape functions of its element.
  *   step        the step index (part of the Philox counter: (pid, step, 0<<16 | block)).
@@ -171,11 +173,12 @@ int lpdf_get_state(const lpdf_ctx* ctx, float* x, float* y, float* u, float* v, 
 int lpdf_pdf_step(lpdf_ctx* ctx, const float* node_fields, uint64_t step, void* stream);
 
 /* ---------------------------------------------------------------------------------------
- * lpdf_sort -- re-buckets the ensemble by element: afterwards the particles of every element
- * are contiguous, ordered by element and then by their previous position (a deterministic
- * counting sort; pid travels with each particle). Particles are never lost or duplicated;
- * the pdf_step results do not depend on the order except through FP32 summation order of the
- * moment partials. async. Uses the context's second state buffer (allocated by ctx_create).
+ * lpdf_sort -- physically re-buckets the ensemble by element: afterwards the particles of every
+ * element are contiguous in the buffer lpdf_get_state reads, ordered by element and then by
+ * their previous position (a deterministic counting sort; pid travels with each particle).
+ * Particles are never lost or duplicated; the per-particle results of later steps do not depend
+ * on the order. lpdf_pdf_step keeps its own element order, so this is only needed to read the
+ * state in element order. async. Uses the context's second state buffer.
  * ------------------------------------------------------------------------------------- */
 int lpdf_sort(lpdf_ctx* ctx, void* stream);
 
@@ -189,6 +192,19 @@ int lpdf_sort(lpdf_ctx* ctx, void* stream);
  * corresponding bit was set (LPDF_ERR_CUDA for bits 8 and 16), else LPDF_OK.
  * ------------------------------------------------------------------------------------- */
 int lpdf_status(lpdf_ctx* ctx, int64_t* out, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * lpdf_ctx_set_timing / lpdf_ctx_timings -- device time of the kernels of lpdf_pdf_step, from
+ * CUDA events recorded on the step's stream (the paper has no counterpart: a measurement aid).
+ *   set_timing: enable = 1 records four events around the kernels of every following step,
+ *               0 stops recording.
+ *   timings:    sync; out_ms (host, 3 doubles) = summed milliseconds of the advance kernel, of
+ *               the re-bucketing kernels (histogram, scans, record and particle scatter) and of
+ *               the moments kernel over the steps recorded since the previous call; *steps (host,
+ *               may be NULL) = their number. The sums restart after each call.
+ * ------------------------------------------------------------------------------------- */
+int lpdf_ctx_set_timing(lpdf_ctx* ctx, int enable);
+int lpdf_ctx_timings(lpdf_ctx* ctx, double* out_ms, int64_t* steps);
 
 /* ---------------------------------------------------------------------------------------
  * lpdf_grid_statistics -- gridpoint statistics of the state left by the last pdf_step

@@ -383,6 +383,9 @@ void lpdf_ctx_free(lpdf_ctx* c)
         cudaFree(s->psi); cudaFree(s->elem); cudaFree(s->pid);
     }
     cudaFree(c->sort.cnt); cudaFree(c->sort.cursor); cudaFree(c->sort.start); cudaFree(c->sort.perm);
+    for (auto& q : c->ev_pending)
+        for (cudaEvent_t e : q) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
     PipeScratch& w = c->pipe;
     void* pp[] = {w.perm, w.perm_new, w.rrank, w.rec_key, w.rec_cnt, w.rec_off, w.nrec, w.kwork, w.kstart,
                   w.krstart, w.klist, w.klist2, w.scan_part};
@@ -486,11 +489,48 @@ int lpdf_pdf_step(lpdf_ctx* c, const float* node_fields, uint64_t step, void* st
     CUDA_TRY(cudaMemsetAsync(c->node_acc, 0, sizeof(unsigned long long) * (size_t)c->mesh->d.n_nodes * nq, st));
     const StepParams p = make_step_params(c->params, c->mesh, step);
     c->s2.n = c->s.n;
+    std::array<cudaEvent_t, 4> ev{};
+    if (c->timing) {
+        for (auto& e : ev) {
+            if (!c->ev_free.empty()) {
+                e = c->ev_free.back();
+                c->ev_free.pop_back();
+            } else {
+                CUDA_TRY(cudaEventCreate(&e));
+            }
+        }
+        c->ev_pending.push_back(ev);
+    }
     CUDA_TRY(launch_pdf_step_pipeline(c->mesh->d, c->s, c->s2, c->ns, node_fields, p, c->pipe, c->node_acc,
-                                      c->status, st));
+                                      c->status, st, c->timing ? ev.data() : nullptr));
     // the new state is in the second buffer, listed in element order by perm_new
     std::swap(c->s, c->s2);
     std::swap(c->pipe.perm, c->pipe.perm_new);
+    return LPDF_OK;
+}
+
+int lpdf_ctx_set_timing(lpdf_ctx* c, int enable)
+{
+    if (!c) return fail(LPDF_ERR_ARG, "ctx is NULL");
+    c->timing = enable != 0;
+    return LPDF_OK;
+}
+
+int lpdf_ctx_timings(lpdf_ctx* c, double* out_ms, int64_t* steps)
+{
+    if (!c || !out_ms) return fail(LPDF_ERR_ARG, "ctx_timings: NULL argument");
+    out_ms[0] = out_ms[1] = out_ms[2] = 0.0;
+    for (auto& q : c->ev_pending) {
+        CUDA_TRY(cudaEventSynchronize(q[3]));
+        for (int k = 0; k < 3; ++k) {
+            float ms = 0.0f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, q[k], q[k + 1]));
+            out_ms[k] += ms;
+        }
+        for (cudaEvent_t e : q) c->ev_free.push_back(e);
+    }
+    if (steps) *steps = (int64_t)c->ev_pending.size();
+    c->ev_pending.clear();
     return LPDF_OK;
 }
 

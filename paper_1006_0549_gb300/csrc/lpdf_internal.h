@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
 #include <mutex>
 #include <vector>
 
@@ -94,9 +95,12 @@ struct PipeScratch {
     int* klist2 = nullptr;
     int* scan_part = nullptr;    // 2 x 4096 scan tile totals
 };
+// ev (may be NULL): 4 events recorded before the advance kernel, after it, after the re-bucketing
+// kernels and after the moments kernel
 cudaError_t launch_pdf_step_pipeline(const DevMesh& m, const DevState& cur, const DevState& nxt, int ns,
                                      const float* fields, const StepParams& p, PipeScratch& w,
-                                     unsigned long long* node_acc, unsigned long long* status, cudaStream_t st);
+                                     unsigned long long* node_acc, unsigned long long* status, cudaStream_t st,
+                                     const cudaEvent_t* ev);
 cudaError_t launch_iota(int* p, int64_t n, cudaStream_t st);
 
 // P1 finite-element tables of the gridpoint solve (lpdf_solve.cu), built once per mesh.
@@ -166,4 +170,8 @@ struct lpdf_ctx {
     unsigned long long* status = nullptr;     // 4 words
     int ns;
     int64_t nsteps = 0;                       // pdf_step calls so far
+    // per-kernel timing (lpdf_ctx_set_timing): event quadruples of the recorded steps
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<std::array<cudaEvent_t, 4>> ev_pending;
 };

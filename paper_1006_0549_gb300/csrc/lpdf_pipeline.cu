@@ -479,7 +479,7 @@ cudaError_t scan_pair(const int* in0, int* out0, const int* in1, int* out1, int 
 template <int NS>
 cudaError_t run_pipeline(const DevMesh& m, const DevState& cur, const DevState& nxt, const float* fields,
                          const StepParams& p, PipeScratch& w, unsigned long long* node_acc, unsigned long long* status,
-                         cudaStream_t st)
+                         cudaStream_t st, const cudaEvent_t* ev)
 {
     const int64_t n = cur.n;
     if (n == 0) return cudaSuccess;
@@ -490,7 +490,9 @@ cudaError_t run_pipeline(const DevMesh& m, const DevState& cur, const DevState& 
     int* kcnt = w.kwork;
     int* krc = w.kwork + (E + 1);
     int* kcur = w.kwork + 2 * (E + 1);
+    if (ev) cudaEventRecord(ev[0], st);
     advance_kernel<NS><<<(unsigned)nblk, kBlk, 0, st>>>(m, cur, nxt, w.perm, fields, p, status);
+    if (ev) cudaEventRecord(ev[1], st);
     histogram_kernel<<<(unsigned)nblk, kBlk, 0, st>>>(nxt.elem, n, w.rrank, w.rec_key, w.rec_cnt, w.nrec, kcnt, krc,
                                                       status);
     e = scan_pair(kcnt, w.kstart, krc, w.krstart, E + 1, w.scan_part, st);
@@ -499,7 +501,9 @@ cudaError_t run_pipeline(const DevMesh& m, const DevState& cur, const DevState& 
     key_offsets_kernel<<<nblocks((int64_t)E * 32, 256), 256, 0, st>>>(E, w.kstart, w.krstart, w.klist, w.klist2,
                                                                        w.rec_cnt, w.rec_off);
     particle_scatter_kernel<<<nblocks(n, 256), 256, 0, st>>>(n, w.rrank, w.rec_off, w.perm_new);
+    if (ev) cudaEventRecord(ev[2], st);
     moments_kernel<NS><<<nblocks((int64_t)E * 32, 256), 256, 0, st>>>(m, nxt, w.perm_new, w.kstart, node_acc, status);
+    if (ev) cudaEventRecord(ev[3], st);
     return cudaGetLastError();
 }
 
@@ -507,13 +511,14 @@ cudaError_t run_pipeline(const DevMesh& m, const DevState& cur, const DevState& 
 
 cudaError_t launch_pdf_step_pipeline(const DevMesh& m, const DevState& cur, const DevState& nxt, int ns,
                                      const float* fields, const StepParams& p, PipeScratch& w,
-                                     unsigned long long* node_acc, unsigned long long* status, cudaStream_t st)
+                                     unsigned long long* node_acc, unsigned long long* status, cudaStream_t st,
+                                     const cudaEvent_t* ev)
 {
     switch (ns) {
-        case 1: return run_pipeline<1>(m, cur, nxt, fields, p, w, node_acc, status, st);
-        case 2: return run_pipeline<2>(m, cur, nxt, fields, p, w, node_acc, status, st);
-        case 3: return run_pipeline<3>(m, cur, nxt, fields, p, w, node_acc, status, st);
-        case 4: return run_pipeline<4>(m, cur, nxt, fields, p, w, node_acc, status, st);
+        case 1: return run_pipeline<1>(m, cur, nxt, fields, p, w, node_acc, status, st, ev);
+        case 2: return run_pipeline<2>(m, cur, nxt, fields, p, w, node_acc, status, st, ev);
+        case 3: return run_pipeline<3>(m, cur, nxt, fields, p, w, node_acc, status, st, ev);
+        case 4: return run_pipeline<4>(m, cur, nxt, fields, p, w, node_acc, status, st, ev);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -35,7 +35,7 @@ EXPORTS = ("lpdf_params_default", "lpdf_last_error", "lpdf_version", "lpdf_mesh_
            "lpdf_mesh_info", "lpdf_mesh_neighbors", "lpdf_mesh_masters", "lpdf_ctx_create", "lpdf_ctx_free",
            "lpdf_ctx_set_params", "lpdf_ctx_size", "lpdf_particles_init", "lpdf_set_state", "lpdf_get_state",
            "lpdf_pdf_step", "lpdf_status", "lpdf_grid_statistics", "lpdf_pdf_step_static", "lpdf_sort",
-           "lpdf_elliptic_relax_solve")
+           "lpdf_elliptic_relax_solve", "lpdf_ctx_set_timing", "lpdf_ctx_timings")
 
 
 class LpdfError(RuntimeError):
@@ -93,6 +93,8 @@ def lib():
     L.lpdf_status.argtypes = [vp, vp, vp]
     L.lpdf_grid_statistics.argtypes = [vp, vp, ctypes.c_int, vp]
     L.lpdf_pdf_step_static.argtypes = [vp, vp, i64] + [vp] * 9 + [vp, u64, vp, vp, vp]
+    L.lpdf_ctx_set_timing.argtypes = [vp, ctypes.c_int]
+    L.lpdf_ctx_timings.argtypes = [vp, vp, vp]
     L.lpdf_elliptic_relax_solve.argtypes = [vp, vp, vp, vp, ctypes.c_double, i32, vp, vp]
     for name in EXPORTS:
         f = getattr(L, name)
@@ -267,6 +269,18 @@ class Context:
         if raise_on_error:
             _check(rc)
         return rc, out
+
+    def set_timing(self, enable: bool = True):
+        """lpdf_ctx_set_timing: record the device time of the step's kernels."""
+        _check(lib().lpdf_ctx_set_timing(self.h, 1 if enable else 0))
+
+    def timings(self):
+        """lpdf_ctx_timings: (ms of the advance kernel, of the re-bucketing kernels, of the moments
+        kernel) summed over the steps recorded since the previous call, and their number."""
+        out = np.zeros(3)
+        n = ctypes.c_int64()
+        _check(lib().lpdf_ctx_timings(self.h, _ptr(out), ctypes.byref(n)))
+        return out, n.value
 
     def grid_statistics(self, out, raw: bool = False, stream=None):
         _check(lib().lpdf_grid_statistics(self.h, _ptr(out), 1 if raw else 0, _stream(stream)))
