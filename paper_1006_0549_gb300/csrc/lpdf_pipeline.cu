@@ -142,83 +142,100 @@ advance_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevSta
 }
 
 // ------------------------------------------------------------------------------------------
-// H
+// H: one warp per record block of kBlk positions, warp-synchronous (no block barriers)
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlk) histogram_kernel(const int* __restrict__ elem, int64_t n,
-                                                         uint16_t* __restrict__ rrank, int* __restrict__ rec_key,
-                                                         int* __restrict__ rec_cnt, int* __restrict__ nrec,
-                                                         int* __restrict__ kcnt, int* __restrict__ krc,
-                                                         unsigned long long* __restrict__ status)
+constexpr int kHWarps = 8;             // warps (record blocks) per CTA
+constexpr int kRows = kBlk / 32;       // rows of 32 positions in a record block
+constexpr int kWHash = 512;            // per-warp hash slots (a block has at most kBlk elements)
+
+__global__ void __launch_bounds__(32 * kHWarps) histogram_kernel(const int* __restrict__ elem, int64_t n,
+                                                               uint16_t* __restrict__ rrank,
+                                                               int* __restrict__ rec_key, int* __restrict__ rec_cnt,
+                                                               int* __restrict__ nrec, int* __restrict__ kcnt,
+                                                               int* __restrict__ krc, unsigned long long* __restrict__ status)
 {
-    __shared__ int hkey[kRecHash];
-    __shared__ __align__(16) unsigned short hcnt[kRecHash][kBlk / 32];
-    __shared__ int hrec[kRecHash];
-    __shared__ int wsum[kBlk / 32];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    __shared__ int hkey_s[kHWarps][kWHash];
+    __shared__ unsigned short hcnt_s[kHWarps][kWHash];
+    __shared__ unsigned char hrec_s[kHWarps][kWHash];
+    __shared__ short used_s[kHWarps][kBlk];   // slot of each record, in insertion order
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    for (int s = tid; s < kRecHash; s += kBlk) hkey[s] = -1;
-    {
-        uint4* z = reinterpret_cast<uint4*>(&hcnt[0][0]);
-        constexpr int n16 = (int)(sizeof(hcnt) / sizeof(uint4));
-        for (int k = tid; k < n16; k += kBlk) z[k] = make_uint4(0u, 0u, 0u, 0u);
+    const int64_t blk = (int64_t)blockIdx.x * kHWarps + wid;     // the record block of this warp
+    const int64_t nblk = (n + kBlk - 1) / kBlk;
+    if (blk >= nblk) return;
+    int* const hkey = hkey_s[wid];
+    unsigned short* const hcnt = hcnt_s[wid];
+    unsigned char* const hrec = hrec_s[wid];
+    short* const used = used_s[wid];
+    for (int s = lane; s < kWHash; s += 32) hkey[s] = -1;
+    const int64_t base = blk * kBlk;
+    int key[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        key[r] = i < n ? elem[i] : -1;
     }
-    const int64_t i = (int64_t)blockIdx.x * kBlk + tid;
-    const int key = i < n ? elem[i] : -1;
+    __syncwarp();
     unsigned err = 0;
-    __syncthreads();
-    // one insert per distinct element of a warp
-    const unsigned m = __match_any_sync(kFull, key);
-    const int leader = __ffs(m) - 1;
-    int slot = -1;
-    if (key >= 0 && lane == leader) {
-        const unsigned h0 = rec_hash(key);
+    int nr = 0;                       // records so far (warp-uniform)
+    int slot[kRows], rank[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        const int k = key[r];
+        const unsigned m = __match_any_sync(kFull, k);
+        const int leader = __ffs(m) - 1;
+        int s = -1, prefix = 0, fresh = 0;
+        if (k >= 0 && lane == leader) {
+            const unsigned h0 = rec_hash(k);
 #pragma unroll 1
-        for (int q = 0; q < kRecHash; ++q) {
-            const int s = (h0 + q) & (kRecHash - 1);
-            const int c = hkey[s];
-            if (c == key) { slot = s; break; }
-            if (c == -1) {
-                const int old = atomicCAS(&hkey[s], -1, key);
-                if (old == -1 || old == key) { slot = s; break; }
+            for (int q = 0; q < kWHash; ++q) {
+                const int t = (h0 + q) & (kWHash - 1);
+                const int c = hkey[t];
+                if (c == k) { s = t; break; }
+                if (c == -1) {
+                    // leaders of different elements of one row may probe the same empty slot
+                    const int old = atomicCAS(&hkey[t], -1, k);
+                    if (old == -1) { s = t; fresh = 1; break; }
+                    if (old == k) { s = t; break; }
+                }
             }
+            if (fresh) hcnt[s] = 0;
         }
-        if (slot >= 0) hcnt[slot][wid] = (unsigned short)__popc(m);
-    }
-    slot = __shfl_sync(kFull, slot, leader);
-    const int rank_w = __popc(m & lt);
-    __syncthreads();
-    // ---- records in slot order; per-(element, warp) prefixes -----------------------------------
-    {
-        const int s0 = 2 * tid, s1 = 2 * tid + 1;
-        const int k0 = hkey[s0], k1 = hkey[s1];
-        const int o0 = k0 >= 0, o1 = k1 >= 0;
-        int total;
-        const int r0 = block_exclusive_scan(o0 + o1, wsum, total);
-        const int ss[2] = {s0, s1}, kk[2] = {k0, k1}, oo[2] = {o0, o1}, rr[2] = {r0, r0 + o0};
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            if (!oo[q]) continue;
-            const int s = ss[q];
-            int run = 0;
-#pragma unroll
-            for (int w = 0; w < kBlk / 32; ++w) {
-                const int c = hcnt[s][w];
-                hcnt[s][w] = (unsigned short)run;
-                run += c;
-            }
-            hrec[s] = rr[q];
-            const int64_t rid = (int64_t)blockIdx.x * kBlk + rr[q];
-            rec_key[rid] = kk[q];
-            rec_cnt[rid] = run;
-            atomicAdd(&kcnt[kk[q]], run);
-            atomicAdd(&krc[kk[q]], 1);
+        // new records in lane order get consecutive record indices
+        const unsigned nb = __ballot_sync(kFull, fresh);
+        if (fresh) {
+            const int r_new = nr + __popc(nb & lt);
+            hrec[s] = (unsigned char)r_new;
+            used[r_new] = (short)s;
         }
-        if (tid == 0) nrec[blockIdx.x] = total;
+        nr += __popc(nb);
+        __syncwarp();
+        if (s >= 0) {
+            prefix = hcnt[s];
+            hcnt[s] = (unsigned short)(prefix + __popc(m));
+        }
+        s = __shfl_sync(kFull, s, leader);
+        prefix = __shfl_sync(kFull, prefix, leader);
+        slot[r] = s;
+        rank[r] = prefix + __popc(m & lt);
+        __syncwarp();
     }
-    __syncthreads();
-    if (key >= 0) {
-        if (consistent(slot >= 0, err))
-            rrank[i] = (uint16_t)((hrec[slot] << 8) | (hcnt[slot][wid] + rank_w));
+    // records of this block
+    for (int q = lane; q < nr; q += 32) {
+        const int s = used[q];
+        const int k = hkey[s], c = hcnt[s];
+        const int64_t rid = blk * kBlk + q;
+        rec_key[rid] = k;
+        rec_cnt[rid] = c;
+        atomicAdd(&kcnt[k], c);
+        atomicAdd(&krc[k], 1);
+    }
+    if (lane == 0) nrec[blk] = nr;
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        if (key[r] >= 0 && consistent(slot[r] >= 0 && rank[r] < kBlk, err))
+            rrank[i] = (uint16_t)(((unsigned)hrec[slot[r]] << 8) | (unsigned)rank[r]);
     }
     const unsigned e_or = __reduce_or_sync(kFull, err);
     if (lane == 0 && e_or) atomicOr(&status[0], (unsigned long long)e_or);
@@ -371,14 +388,29 @@ __global__ void __launch_bounds__(256) key_offsets_kernel(int n_keys, const int*
     }
 }
 
+constexpr int kScatterPer = 4;   // particles per thread of the particle scatter
+
 __global__ void particle_scatter_kernel(int64_t n, const uint16_t* __restrict__ rrank, const int* __restrict__ rec_off,
                                         int* __restrict__ perm_new)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const unsigned pk = rrank[i];
-    const int64_t rid = (i / kBlk) * kBlk + (pk >> 8);
-    perm_new[rec_off[rid] + (pk & 255u)] = (int)i;
+    const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x) * kScatterPer + threadIdx.x;
+    unsigned pk[kScatterPer];
+    int off[kScatterPer];
+#pragma unroll
+    for (int k = 0; k < kScatterPer; ++k) {
+        const int64_t i = i0 + (int64_t)k * blockDim.x;
+        pk[k] = i < n ? rrank[i] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < kScatterPer; ++k) {
+        const int64_t i = i0 + (int64_t)k * blockDim.x;
+        off[k] = i < n ? rec_off[(i / kBlk) * kBlk + (pk[k] >> 8)] : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < kScatterPer; ++k) {
+        const int64_t i = i0 + (int64_t)k * blockDim.x;
+        if (i < n) perm_new[off[k] + (pk[k] & 255u)] = (int)i;
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -407,28 +439,48 @@ __global__ void __launch_bounds__(256, 2) moments_kernel(const __grid_constant__
 #pragma unroll
         for (int k = 0; k < NK; ++k) acc[k] = 0.0f;
         const int end = min(p1, base + 32 * kLaneChunk);
-#pragma unroll 2
-        for (int pos = base + lane; pos < end; pos += 32) {
-            const int idx = perm[pos];
-            const float x = S.x[idx], y = S.y[idx];
-            float q[NQ];
-            const float u = S.u[idx], v = S.v[idx], w = S.w[idx];
-            q[0] = 1.0f; q[1] = u; q[2] = v; q[3] = w;
-            q[4] = u * u; q[5] = u * v; q[6] = u * w; q[7] = v * v; q[8] = v * w; q[9] = w * w;
-            q[10] = S.om[idx];
+        // MB particles per lane in flight: their index and state loads are issued before any of
+        // them is used; the accumulation order per lane stays position order
+        constexpr int MB = NS <= 2 ? 4 : 2;
+#pragma unroll 1
+        for (int pos0 = base + lane; pos0 < end; pos0 += 32 * MB) {
+            int idx[MB];
 #pragma unroll
-            for (int a = 0; a < NS; ++a) {
-                const float ps = S.psi[(size_t)a * S.cap + idx];
-                q[11 + a] = ps;
-                q[11 + NS + a] = ps * ps;
+            for (int k = 0; k < MB; ++k) idx[k] = pos0 + 32 * k < end ? perm[pos0 + 32 * k] : -1;
+            float sx[MB], sy[MB], su[MB], sv[MB], sw[MB], so[MB], sp[MB][NS];
+#pragma unroll
+            for (int k = 0; k < MB; ++k) {
+                const int j = idx[k] >= 0 ? idx[k] : 0;
+                sx[k] = S.x[j];
+                sy[k] = S.y[j];
+                su[k] = S.u[j];
+                sv[k] = S.v[j];
+                sw[k] = S.w[j];
+                so[k] = S.om[j];
+#pragma unroll
+                for (int a = 0; a < NS; ++a) sp[k][a] = S.psi[(size_t)a * S.cap + j];
             }
-            float l0, l1, l2;
-            barycentric(X, Y, x, y, l0, l1, l2);
 #pragma unroll
-            for (int k = 0; k < NQ; ++k) {
-                acc[k] = fmaf(l0, q[k], acc[k]);
-                acc[NQ + k] = fmaf(l1, q[k], acc[NQ + k]);
-                acc[2 * NQ + k] = fmaf(l2, q[k], acc[2 * NQ + k]);
+            for (int k = 0; k < MB; ++k) {
+                if (idx[k] < 0) break;
+                float q[NQ];
+                const float u = su[k], v = sv[k], w = sw[k];
+                q[0] = 1.0f; q[1] = u; q[2] = v; q[3] = w;
+                q[4] = u * u; q[5] = u * v; q[6] = u * w; q[7] = v * v; q[8] = v * w; q[9] = w * w;
+                q[10] = so[k];
+#pragma unroll
+                for (int a = 0; a < NS; ++a) {
+                    q[11 + a] = sp[k][a];
+                    q[11 + NS + a] = sp[k][a] * sp[k][a];
+                }
+                float l0, l1, l2;
+                barycentric(X, Y, sx[k], sy[k], l0, l1, l2);
+#pragma unroll
+                for (int kq = 0; kq < NQ; ++kq) {
+                    acc[kq] = fmaf(l0, q[kq], acc[kq]);
+                    acc[NQ + kq] = fmaf(l1, q[kq], acc[NQ + kq]);
+                    acc[2 * NQ + kq] = fmaf(l2, q[kq], acc[2 * NQ + kq]);
+                }
             }
         }
         // the same butterfly in every lane: every lane ends with every column's sum
@@ -493,14 +545,14 @@ cudaError_t run_pipeline(const DevMesh& m, const DevState& cur, const DevState& 
     if (ev) cudaEventRecord(ev[0], st);
     advance_kernel<NS><<<(unsigned)nblk, kBlk, 0, st>>>(m, cur, nxt, w.perm, fields, p, status);
     if (ev) cudaEventRecord(ev[1], st);
-    histogram_kernel<<<(unsigned)nblk, kBlk, 0, st>>>(nxt.elem, n, w.rrank, w.rec_key, w.rec_cnt, w.nrec, kcnt, krc,
-                                                      status);
+    histogram_kernel<<<(unsigned)((nblk + kHWarps - 1) / kHWarps), 32 * kHWarps, 0, st>>>(
+        nxt.elem, n, w.rrank, w.rec_key, w.rec_cnt, w.nrec, kcnt, krc, status);
     e = scan_pair(kcnt, w.kstart, krc, w.krstart, E + 1, w.scan_part, st);
     if (e != cudaSuccess) return e;
     record_scatter_kernel<<<(unsigned)nblk, kBlk, 0, st>>>(w.nrec, w.rec_key, w.krstart, kcur, w.klist);
     key_offsets_kernel<<<nblocks((int64_t)E * 32, 256), 256, 0, st>>>(E, w.kstart, w.krstart, w.klist, w.klist2,
                                                                        w.rec_cnt, w.rec_off);
-    particle_scatter_kernel<<<nblocks(n, 256), 256, 0, st>>>(n, w.rrank, w.rec_off, w.perm_new);
+    particle_scatter_kernel<<<nblocks(n, 256 * kScatterPer), 256, 0, st>>>(n, w.rrank, w.rec_off, w.perm_new);
     if (ev) cudaEventRecord(ev[2], st);
     moments_kernel<NS><<<nblocks((int64_t)E * 32, 256), 256, 0, st>>>(m, nxt, w.perm_new, w.kstart, node_acc, status);
     if (ev) cudaEventRecord(ev[3], st);
