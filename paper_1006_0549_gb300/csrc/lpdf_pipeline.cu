@@ -439,18 +439,23 @@ __global__ void __launch_bounds__(256, 2) moments_kernel(const __grid_constant__
 #pragma unroll
         for (int k = 0; k < NK; ++k) acc[k] = 0.0f;
         const int end = min(p1, base + 32 * kLaneChunk);
-        // MB particles per lane in flight: their index and state loads are issued before any of
-        // them is used; the accumulation order per lane stays position order
+        // the lane's gather indices for the whole chunk first, then MB particles per lane in
+        // flight: their state loads are issued before any of them is used; the accumulation order
+        // per lane stays position order
         constexpr int MB = NS <= 2 ? 4 : 2;
-#pragma unroll 1
-        for (int pos0 = base + lane; pos0 < end; pos0 += 32 * MB) {
-            int idx[MB];
+        int idx[kLaneChunk];
 #pragma unroll
-            for (int k = 0; k < MB; ++k) idx[k] = pos0 + 32 * k < end ? perm[pos0 + 32 * k] : -1;
+        for (int k = 0; k < kLaneChunk; ++k) {
+            const int pos = base + lane + 32 * k;
+            idx[k] = pos < end ? perm[pos] : -1;
+        }
+#pragma unroll
+        for (int k0 = 0; k0 < kLaneChunk; k0 += MB) {
+            if (base + 32 * k0 >= end) break;
             float sx[MB], sy[MB], su[MB], sv[MB], sw[MB], so[MB], sp[MB][NS];
 #pragma unroll
             for (int k = 0; k < MB; ++k) {
-                const int j = idx[k] >= 0 ? idx[k] : 0;
+                const int j = idx[k0 + k] >= 0 ? idx[k0 + k] : 0;
                 sx[k] = S.x[j];
                 sy[k] = S.y[j];
                 su[k] = S.u[j];
@@ -462,7 +467,7 @@ __global__ void __launch_bounds__(256, 2) moments_kernel(const __grid_constant__
             }
 #pragma unroll
             for (int k = 0; k < MB; ++k) {
-                if (idx[k] < 0) break;
+                if (idx[k0 + k] < 0) break;
                 float q[NQ];
                 const float u = su[k], v = sv[k], w = sw[k];
                 q[0] = 1.0f; q[1] = u; q[2] = v; q[3] = w;
