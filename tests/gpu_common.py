@@ -21,7 +21,8 @@ def torch_state(st: wl.State):
 
 
 def host_state(d, ns) -> wl.State:
-    g = {k: v.cpu().numpy() for k, v in d.items()}
+    """State from get_state's dict (torch tensors or numpy arrays)."""
+    g = {k: (v.cpu().numpy() if hasattr(v, "cpu") else np.asarray(v)) for k, v in d.items()}
     return wl.State(*(g[k].astype(np.float32) for k in FIELDS), g["psi"].reshape(ns, -1).astype(np.float32),
                     g["elem"].astype(np.int32), g["pid"].view(np.uint32))
 
