@@ -46,7 +46,7 @@ cudaError_t dalloc(T** p, size_t n)
 
 bool is_f32(double v) { return (double)(float)v == v; }
 
-cudaError_t alloc_pipe(PipeScratch& w, int64_t cap, size_t E)
+cudaError_t alloc_pipe(PipeScratch& w, int64_t cap, size_t E, int ns)
 {
     const size_t nrec = (size_t)((cap + 255) / 256) * 256;
     cudaError_t e = cudaSuccess;
@@ -54,7 +54,7 @@ cudaError_t alloc_pipe(PipeScratch& w, int64_t cap, size_t E)
         (e = dalloc(&w.rec_key, nrec)) || (e = dalloc(&w.rec_cnt, nrec)) || (e = dalloc(&w.rec_off, nrec)) ||
         (e = dalloc(&w.nrec, nrec / 256)) || (e = dalloc(&w.kwork, 3 * (E + 1))) || (e = dalloc(&w.kstart, E + 1)) ||
         (e = dalloc(&w.krstart, E + 1)) || (e = dalloc(&w.klist, nrec)) || (e = dalloc(&w.klist2, nrec)) ||
-        (e = dalloc(&w.scan_part, 2 * 4096)))
+        (e = dalloc(&w.scan_part, 2 * 4096)) || (e = dalloc(&w.efields, E * 3 * (size_t)nfields_padded(ns))))
         return e;
     return cudaSuccess;
 }
@@ -361,7 +361,7 @@ int lpdf_ctx_create(const lpdf_mesh* mesh, const lpdf_params* params, int64_t ca
         (ce = dalloc(&c->sort.cnt, E + 1)) || (ce = dalloc(&c->sort.cursor, E + 1)) ||
         (ce = dalloc(&c->sort.start, E + 2)) || (ce = dalloc(&c->sort.perm, cap)) ||
         (ce = dalloc(&c->node_acc, (size_t)mesh->d.n_nodes * nq)) || (ce = dalloc(&c->status, 4)) ||
-        (ce = alloc_pipe(c->pipe, cap, E))) {
+        (ce = alloc_pipe(c->pipe, cap, E, c->ns))) {
         lpdf_ctx_free(c);
         return fail(LPDF_ERR_CUDA, "ctx_create: %s", cudaGetErrorString(ce));
     }
@@ -388,7 +388,7 @@ void lpdf_ctx_free(lpdf_ctx* c)
     for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
     PipeScratch& w = c->pipe;
     void* pp[] = {w.perm, w.perm_new, w.rrank, w.rec_key, w.rec_cnt, w.rec_off, w.nrec, w.kwork, w.kstart,
-                  w.krstart, w.klist, w.klist2, w.scan_part};
+                  w.krstart, w.klist, w.klist2, w.scan_part, w.efields};
     for (void* q : pp) cudaFree(q);
     cudaFree(c->node_acc); cudaFree(c->status);
     delete c;

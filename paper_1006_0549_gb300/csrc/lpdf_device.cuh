@@ -385,24 +385,35 @@ __device__ __forceinline__ bool in_source(float px, float py, float sx, float sy
     return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) < __fmul_rn(r, r);
 }
 
-// On return p holds the new state except the element, which is the walk's start: the old
-// element, or 0 when the old one is outside the mesh (`bad`).
-template <int NS>
-__device__ __forceinline__ void advance_particle(const DevMesh& M, const float* __restrict__ F, const StepParams& P,
-                                                 ParticleState<NS>& p, unsigned& err, bool& bad)
+// Interpolated node fields at the particle, two sources:
+//   kElementTable = false: F is the node table (n_nodes x nfp); the P1 shape functions of the
+//                          element weight its three node rows;
+//   kElementTable = true:  F is the element table (n_tri x 3 x nfp: the fields at vertex 0 and
+//                          their x and y gradients on the element), so F(p) = F0 + Gx dx + Gy dy
+//                          with (dx, dy) = p - vertex 0; the same P1 interpolant.
+template <int NS, bool kElementTable>
+__device__ __forceinline__ void interpolate_fields(const DevMesh& M, const float* __restrict__ F, int e, float x,
+                                                   float y, float* Fi)
 {
     constexpr int NFP = (22 + NS + 3) / 4 * 4;
-    const float x = p.x, y = p.y, u = p.u, v = p.v, w = p.w, om = p.om;
-    bad = (unsigned)p.elem >= (unsigned)M.n_tri;
-    const int e = bad ? 0 : p.elem;
-    const float4 X = __ldg(&M.ex[e]);
-    const float4 Y = __ldg(&M.ey[e]);
-    const int4 V = __ldg(&M.ev[e]);
-    float l0, l1, l2;
-    barycentric(X, Y, x, y, l0, l1, l2);
-    // linear shape-function interpolation of the node fields
-    float Fi[NFP];
-    {
+    if (kElementTable) {
+        const float4 A = __ldg(&M.ea[e]);
+        const float dx = __fsub_rn(x, A.x), dy = __fsub_rn(y, A.y);
+        const float4* R = reinterpret_cast<const float4*>(F) + (size_t)e * (3 * NFP / 4);
+#pragma unroll
+        for (int q = 0; q < NFP / 4; ++q) {
+            const float4 a = __ldg(R + q), gx = __ldg(R + NFP / 4 + q), gy = __ldg(R + 2 * (NFP / 4) + q);
+            Fi[4 * q + 0] = fmaf(gx.x, dx, fmaf(gy.x, dy, a.x));
+            Fi[4 * q + 1] = fmaf(gx.y, dx, fmaf(gy.y, dy, a.y));
+            Fi[4 * q + 2] = fmaf(gx.z, dx, fmaf(gy.z, dy, a.z));
+            Fi[4 * q + 3] = fmaf(gx.w, dx, fmaf(gy.w, dy, a.w));
+        }
+    } else {
+        const float4 X = __ldg(&M.ex[e]);
+        const float4 Y = __ldg(&M.ey[e]);
+        const int4 V = __ldg(&M.ev[e]);
+        float l0, l1, l2;
+        barycentric(X, Y, x, y, l0, l1, l2);
         const float4* R0 = reinterpret_cast<const float4*>(F) + (size_t)V.x * (NFP / 4);
         const float4* R1 = reinterpret_cast<const float4*>(F) + (size_t)V.y * (NFP / 4);
         const float4* R2 = reinterpret_cast<const float4*>(F) + (size_t)V.z * (NFP / 4);
@@ -415,6 +426,21 @@ __device__ __forceinline__ void advance_particle(const DevMesh& M, const float* 
             Fi[4 * q + 3] = fmaf(l0, a.w, fmaf(l1, b.w, l2 * c.w));
         }
     }
+}
+
+// On return p holds the new state except the element, which is the walk's start: the old
+// element, or 0 when the old one is outside the mesh (`bad`).
+template <int NS, bool kElementTable = false>
+__device__ __forceinline__ void advance_particle(const DevMesh& M, const float* __restrict__ F, const StepParams& P,
+                                                 ParticleState<NS>& p, unsigned& err, bool& bad)
+{
+    constexpr int NFP = (22 + NS + 3) / 4 * 4;
+    const float x = p.x, y = p.y, u = p.u, v = p.v, w = p.w, om = p.om;
+    bad = (unsigned)p.elem >= (unsigned)M.n_tri;
+    const int e = bad ? 0 : p.elem;
+    // linear shape-function interpolation of the node fields
+    float Fi[NFP];
+    interpolate_fields<NS, kElementTable>(M, F, e, x, y, Fi);
     // Wiener increments: Philox blocks 0 and 1 of counter (pid, step, 0<<16 | block)
     const uint4 r0 = philox4x32_10(make_uint4(p.pid, P.step_lo, P.step_hi, 0u), P.key0, P.key1);
     const uint4 r1 = philox4x32_10(make_uint4(p.pid, P.step_lo, P.step_hi, 1u), P.key0, P.key1);

@@ -94,6 +94,7 @@ struct PipeScratch {
     int* klist = nullptr;        // records grouped by element, then in block order
     int* klist2 = nullptr;
     int* scan_part = nullptr;    // 2 x 4096 scan tile totals
+    float* efields = nullptr;    // n_tri x 3 x nfp: node fields in element form
 };
 // ev (may be NULL): 4 events recorded before the advance kernel, after it, after the re-bucketing
 // kernels and after the moments kernel

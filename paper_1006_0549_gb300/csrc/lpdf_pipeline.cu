@@ -2,6 +2,8 @@
 //
 // Per step (Section "Governing equations": Eq. 2, 4, 5, 6, 9 in IEM form, forward Euler,
 // statistics at the gridpoints, tracking through the unstructured grid):
+//   T   element_fields_kernel: the node fields in element form (per element: the fields at vertex
+//       0 and their x and y gradients), so a particle interpolates without the node indirection.
 //   K1  advance_kernel: thread i takes the particle perm[i] of the current buffer (perm lists the
 //       buffer in element order), advances it (Eq. 4, 5, 9, 2, wrap, reflection, sources),
 //       locates it with the barycentric neighbour walk and writes it to position i of the next
@@ -69,7 +71,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int& total
 template <int NS>
 __global__ void __launch_bounds__(kBlk, 4)
 advance_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevState cur,
-               const __grid_constant__ DevState nxt, const int* __restrict__ perm, const float* __restrict__ F,
+               const __grid_constant__ DevState nxt, const int* __restrict__ perm, const float* __restrict__ EF,
                const __grid_constant__ StepParams P, unsigned long long* __restrict__ status)
 {
     const int lane = threadIdx.x & 31;
@@ -90,7 +92,7 @@ advance_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevSta
         p.elem = cur.elem[src];
         p.pid = cur.pid[src];
         bool bad;
-        advance_particle<NS>(M, F, P, p, err, bad);
+        advance_particle<NS, true>(M, EF, P, p, err, bad);
         // barycentric neighbour walk from the old element
         const int e0 = p.elem;
         int e = e0, h = 0, ne = e0;
@@ -139,6 +141,32 @@ advance_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevSta
         if (e_or) atomicOr(&status[0], (unsigned long long)e_or);
         if (h_sum) atomicAdd(&status[3], (unsigned long long)h_sum);
     }
+}
+
+// ------------------------------------------------------------------------------------------
+// T: thread (e, q) writes float4 q of the three rows of element e
+// ------------------------------------------------------------------------------------------
+template <int NS>
+__global__ void element_fields_kernel(const __grid_constant__ DevMesh M, const float* __restrict__ F,
+                                      float* __restrict__ EF)
+{
+    constexpr int NFP = (22 + NS + 3) / 4 * 4, NQ4 = NFP / 4;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)M.n_tri * NQ4) return;
+    const int e = (int)(t / NQ4), q = (int)(t - (int64_t)e * NQ4);
+    const int4 V = __ldg(&M.ev[e]);
+    const float4 A = __ldg(&M.ea[e]);   // b1 = A.z, g1 = A.w
+    const float4 B = __ldg(&M.eb[e]);   // b2 = B.x, g2 = B.y
+    const float4 fa = __ldg(reinterpret_cast<const float4*>(F) + (size_t)V.x * NQ4 + q);
+    const float4 fb = __ldg(reinterpret_cast<const float4*>(F) + (size_t)V.y * NQ4 + q);
+    const float4 fc = __ldg(reinterpret_cast<const float4*>(F) + (size_t)V.z * NQ4 + q);
+    // F = fa + (fb - fa) lambda_1 + (fc - fa) lambda_2, lambda_1 = b1 dx + g1 dy, lambda_2 = b2 dx + g2 dy
+    auto gx = [&](float a, float b, float c) { return fmaf(b - a, A.z, (c - a) * B.x); };
+    auto gy = [&](float a, float b, float c) { return fmaf(b - a, A.w, (c - a) * B.y); };
+    float4* R = reinterpret_cast<float4*>(EF) + (size_t)e * 3 * NQ4;
+    R[q] = fa;
+    R[NQ4 + q] = make_float4(gx(fa.x, fb.x, fc.x), gx(fa.y, fb.y, fc.y), gx(fa.z, fb.z, fc.z), gx(fa.w, fb.w, fc.w));
+    R[2 * NQ4 + q] = make_float4(gy(fa.x, fb.x, fc.x), gy(fa.y, fb.y, fc.y), gy(fa.z, fb.z, fc.z), gy(fa.w, fb.w, fc.w));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -548,7 +576,9 @@ cudaError_t run_pipeline(const DevMesh& m, const DevState& cur, const DevState& 
     int* krc = w.kwork + (E + 1);
     int* kcur = w.kwork + 2 * (E + 1);
     if (ev) cudaEventRecord(ev[0], st);
-    advance_kernel<NS><<<(unsigned)nblk, kBlk, 0, st>>>(m, cur, nxt, w.perm, fields, p, status);
+    constexpr int NQ4 = (22 + NS + 3) / 4;
+    element_fields_kernel<NS><<<nblocks((int64_t)E * NQ4, 256), 256, 0, st>>>(m, fields, w.efields);
+    advance_kernel<NS><<<(unsigned)nblk, kBlk, 0, st>>>(m, cur, nxt, w.perm, w.efields, p, status);
     if (ev) cudaEventRecord(ev[1], st);
     histogram_kernel<<<(unsigned)((nblk + kHWarps - 1) / kHWarps), 32 * kHWarps, 0, st>>>(
         nxt.elem, n, w.rrank, w.rec_key, w.rec_cnt, w.nrec, kcnt, krc, status);
