@@ -228,15 +228,27 @@ def run_gpu(args, rank, world, dist):
         step += 1
     e2e_s = (time.perf_counter() - te) / Ke
     # the gridpoint side (not part of the metric): node fields from the last statistics, elliptic
-    # relaxation and mean-pressure CGs to a relative residual of 1e-10
+    # relaxation and mean-pressure CGs to a relative residual of 1e-6 (far below the statistical noise
+    # of the moments); cold (from zero), then warm
+    # (from the previous solution, on the statistics one step later, as in a time loop)
     gp = lpdf.params_for(wk, gmodel=0, pressure_solve=1, dpdx0=-1.0)
     out_fields = torch.empty_like(fields)
-    mesh.elliptic_relax_solve(gp, d_stats, out_fields, 1e-10, 20000)     # tables built, warm
+    mesh.elliptic_relax_solve(gp, d_stats, out_fields, 1e-6, 20000)     # tables built, warm caches
     torch.cuda.synchronize()
     tg = time.perf_counter()
-    its = mesh.elliptic_relax_solve(gp, d_stats, out_fields, 1e-10, 20000)
+    its_cold = mesh.elliptic_relax_solve(gp, d_stats, out_fields, 1e-6, 20000)
     torch.cuda.synchronize()
-    solve = {"ms": 1e3 * (time.perf_counter() - tg), "cg_iterations": list(its), "nodes": mesh.n_nodes,
+    cold_ms = 1e3 * (time.perf_counter() - tg)
+    ctx.pdf_step(fields, step)
+    ctx.grid_statistics(d_stats, raw=False)
+    gp.cg_warm_start = 1
+    torch.cuda.synchronize()
+    tg = time.perf_counter()
+    its_warm = mesh.elliptic_relax_solve(gp, d_stats, out_fields, 1e-6, 20000)
+    torch.cuda.synchronize()
+    warm_ms = 1e3 * (time.perf_counter() - tg)
+    solve = {"cold_ms": cold_ms, "cold_cg_iterations": list(its_cold), "warm_ms": warm_ms,
+             "warm_cg_iterations": list(its_warm), "nodes": mesh.n_nodes,
              "note": "lpdf_elliptic_relax_solve: recovery, FP64 elliptic-relaxation and pressure CGs, "
                      "host-timed (it synchronises); not included in the step"}
     return dict(P=P, total_ms=total_ms, per=per, kernel_ms=kernel_ms, clocks=clk.summary(), hops=hops, e2e_s=e2e_s,

@@ -80,7 +80,8 @@ typedef struct {
     int32_t gmodel;         /* lpdf_elliptic_relax_solve: 0 elliptic relaxation, 1 simplified Langevin model */
     int32_t pressure_solve; /* lpdf_elliptic_relax_solve: 1 solve for the mean pressure,
                                0 gradient = (dpdx0, dpdy0) only */
-    int32_t reserved_;
+    int32_t cg_warm_start;  /* lpdf_elliptic_relax_solve: 1 starts the CGs from the previous solution
+                               on this mesh (a time loop), 0 from zero */
     double dpdx0, dpdy0;    /* fixed mean pressure gradient added to the solved one (channel: -1, 0) */
 } lpdf_params;
 
@@ -89,7 +90,7 @@ typedef struct lpdf_ctx lpdf_ctx;
 
 /* Fills *p with C3 = 5, C4 = 0.25, Cphi = 2, C0 = 2.1, Comega1 = 0.5, Comega2 = 0.73,
  * CL = 0.134, Ceta = 72, nu = 1/180, dt = 1e-3, ns = 1, no sources, seed = 1, lid_u = 0,
- * gmodel = 0, pressure_solve = 0, dpdx0 = dpdy0 = 0. */
+ * gmodel = 0, pressure_solve = 0, cg_warm_start = 0, dpdx0 = dpdy0 = 0. */
 void lpdf_params_default(lpdf_params* p);
 
 /* Message of the calling thread's last error ("" if none). Owned by the library. */
@@ -224,7 +225,9 @@ int lpdf_grid_statistics(lpdf_ctx* ctx, double* out, int raw, void* stream);
  * conjugate-gradient convergence tests read residual norms back to the host).
  *   stats   device, n_nodes x (11 + 2 ns) FP64 as lpdf_grid_statistics(raw = 0) writes them
  *   fields  device out, n_nodes x nfp FP32 (columns LPDF_F_*)
- *   tol     relative residual of each conjugate gradient: |r| <= tol |r_0|
+ *   tol     relative residual of each conjugate gradient: |r| <= tol |r_ref|, r_ref the residual
+ *           of the start with a zero interior (with cg_warm_start the CG starts from the previous
+ *           solution on this mesh, so a slowly changing problem needs few iterations)
  *   maxit   iteration cap of each conjugate gradient
  *   iters   host out (may be NULL), 2 ints: iterations of the elliptic-relaxation solve (its
  *           four components at once) and of the pressure solve (0 when not run)

@@ -107,7 +107,7 @@ cudaError_t launch_iota(int* p, int64_t n, cudaStream_t st);
 // P1 finite-element tables of the gridpoint solve (lpdf_solve.cu), built once per mesh.
 // DOFs are the geometric nodes with periodic partners merged (numbered in node order).
 struct Fem {
-    static constexpr int kWorkPerDof = 56;     // FP64 scratch per DOF
+    static constexpr int kWorkPerDof = 65;     // FP64 scratch per DOF
     static constexpr int kDotBlocks = 1024;    // partial sums of one dot product
     int ndof = 0, nnz = 0, E = 0, N = 0;
     int* dof = nullptr;          // geometric node -> DOF
@@ -128,16 +128,18 @@ struct Fem {
     unsigned char* wall = nullptr;
     double* normal = nullptr;    // inward unit normal per wall DOF
     double* work = nullptr;      // kWorkPerDof * ndof + 16 * E doubles
-    double* part = nullptr;      // 4 * kDotBlocks
+    double* part = nullptr;      // 12 * kDotBlocks: partial sums of up to three 4-vector dot products
     double* scal = nullptr;      // CG scalars (device)
     double* scal_host = nullptr; // pinned copy
+    bool has_wp = false;         // the scratch holds a previous relaxation / pressure solution
+    bool has_p = false;
 };
 cudaError_t fem_build(const double* node_xy, int n_nodes, const int32_t* tri, int n_tri, const int32_t* tag,
                       const std::vector<int32_t>& master, Fem** out);
 void fem_free(Fem* F);
 // statistics (n_nodes x (11 + 2 ns), lpdf_grid_statistics raw = 0) -> node fields; iters[2];
 // cudaErrorNotReady when a CG did not converge within maxit
-cudaError_t node_fields_solve(const Fem& F, const double* stats, const lpdf_params& P, float* out, double tol,
+cudaError_t node_fields_solve(Fem& F, const double* stats, const lpdf_params& P, float* out, double tol,
                               int maxit, int* iters, cudaStream_t st);
 
 StepParams make_step_params(const lpdf_params& p, const struct ::lpdf_mesh* m, uint64_t step);

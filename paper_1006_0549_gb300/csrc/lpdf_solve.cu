@@ -30,7 +30,7 @@ namespace lpdf {
 namespace {
 
 constexpr int kDotThreads = 256;
-constexpr int kCheckEvery = 4;   // CG iterations between host-side convergence tests
+constexpr int kCheckEvery = 8;   // CG iterations between host-side convergence tests
 
 template <class T>
 cudaError_t upload(T** d, const std::vector<T>& h)
@@ -257,10 +257,95 @@ __global__ void cg_direction_kernel(int n, int nv, const double* __restrict__ sc
     }
 }
 
+// q_c = A p_c (0 on fixed rows) and block partials of p_c . q_c (fixed order)
+__global__ void spmv_dot_kernel(const Fem F, const double* __restrict__ A, const double* __restrict__ p,
+                                double* __restrict__ q, int mask, int nv, double* __restrict__ part)
+{
+    __shared__ double sh[4][kDotThreads];
+    const size_t n = F.ndof;
+    double acc[4] = {0, 0, 0, 0};
+    for (int i = blockIdx.x * kDotThreads + threadIdx.x; i < F.ndof; i += gridDim.x * kDotThreads) {
+        double s[4] = {0, 0, 0, 0};
+        if (!(mask && F.wall[i]))
+            for (int t = F.row[i]; t < F.row[i + 1]; ++t) {
+                const int j = F.col[t];
+                const double a = A[t];
+                for (int c = 0; c < nv; ++c) s[c] += a * p[c * n + j];
+            }
+        for (int c = 0; c < nv; ++c) {
+            q[c * n + i] = s[c];
+            acc[c] += p[c * n + i] * s[c];
+        }
+    }
+    for (int c = 0; c < 4; ++c) sh[c][threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int o = kDotThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int c = 0; c < 4; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 4; ++c) part[(size_t)c * gridDim.x + blockIdx.x] = sh[c][0];
+}
+
+// x += alpha p; r -= alpha q; z = r / diag; block partials of r . z and r . r
+__global__ void update_dot_kernel(int n, int nv, const double* __restrict__ sc, const double* __restrict__ diag,
+                                  const double* __restrict__ p, const double* __restrict__ q, double* __restrict__ x,
+                                  double* __restrict__ r, double* __restrict__ z, double* __restrict__ part_rz,
+                                  double* __restrict__ part_rr)
+{
+    __shared__ double sh[8][kDotThreads];
+    double a_rz[4] = {0, 0, 0, 0}, a_rr[4] = {0, 0, 0, 0};
+    for (int i = blockIdx.x * kDotThreads + threadIdx.x; i < n; i += gridDim.x * kDotThreads)
+        for (int c = 0; c < nv; ++c) {
+            const size_t o = (size_t)c * n + i;
+            const double al = sc[kAlpha + c];
+            x[o] += al * p[o];
+            const double rr = r[o] - al * q[o];
+            r[o] = rr;
+            const double zz = rr / diag[i];
+            z[o] = zz;
+            a_rz[c] += rr * zz;
+            a_rr[c] += rr * rr;
+        }
+    for (int c = 0; c < 4; ++c) {
+        sh[c][threadIdx.x] = a_rz[c];
+        sh[4 + c][threadIdx.x] = a_rr[c];
+    }
+    __syncthreads();
+    for (int o = kDotThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int c = 0; c < 8; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 4; ++c) {
+            part_rz[(size_t)c * gridDim.x + blockIdx.x] = sh[c][0];
+            part_rr[(size_t)c * gridDim.x + blockIdx.x] = sh[4 + c][0];
+        }
+}
+
+// beta = rz_new / rz, rz = rz_new, rr (for the convergence test)
+__global__ void scalar_beta_kernel(const double* __restrict__ part_rz, const double* __restrict__ part_rr, int nb,
+                                   int nv, double* __restrict__ sc)
+{
+    const int c = threadIdx.x;
+    if (c >= nv) return;
+    double rz = 0.0, rr = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        rz += part_rz[(size_t)c * nb + b];
+        rr += part_rr[(size_t)c * nb + b];
+    }
+    sc[kBeta + c] = sc[kRZ + c] != 0.0 ? rz / sc[kRZ + c] : 0.0;
+    sc[kRZ + c] = rz;
+    sc[kRR + c] = rr;
+}
+
 // ---------------------------------------------------------------- right-hand sides
-// elliptic relaxation: sources wp^h (11, 12, 22, 33) and wall values (in x, the CG's start)
+// elliptic relaxation: sources wp^h (11, 12, 22, 33); wall values in x (the CG's start, whose
+// interior is `prev`, or 0) and in xref (interior 0: the reference of the convergence test)
 __global__ void er_setup_kernel(const Fem F, const double* __restrict__ eps, double C0, double* __restrict__ src,
-                                double* __restrict__ x)
+                                double* __restrict__ x, const double* __restrict__ prev, double* __restrict__ xref)
 {
     const int d = blockIdx.x * blockDim.x + threadIdx.x;
     if (d >= F.ndof) return;
@@ -273,10 +358,11 @@ __global__ void er_setup_kernel(const Fem F, const double* __restrict__ eps, dou
     src[1 * n + d] = 0.0;
     src[2 * n + d] = s;
     src[3 * n + d] = s;
-    x[0 * n + d] = w ? -4.5 * e * n1 * n1 : 0.0;
-    x[1 * n + d] = w ? -4.5 * e * n1 * n2 : 0.0;
-    x[2 * n + d] = w ? -4.5 * e * n2 * n2 : 0.0;
-    x[3 * n + d] = 0.0;
+    const double wv[4] = {-4.5 * e * n1 * n1, -4.5 * e * n1 * n2, -4.5 * e * n2 * n2, 0.0};
+    for (int c = 0; c < 4; ++c) {
+        xref[c * n + d] = w ? wv[c] : 0.0;
+        x[c * n + d] = w ? wv[c] : (prev ? prev[c * n + d] : 0.0);
+    }
 }
 
 // T = <U><U> + <uu> in the plane: (T00, T01, T10, T11) per DOF
@@ -481,7 +567,7 @@ cudaError_t fem_build(const double* node_xy, int N, const int32_t* tri, int E, c
         (e = upload(&F->normal, normal)) ||
         (e = cudaMalloc((void**)&F->Aval, sizeof(double) * std::max(1, F->nnz))) ||
         (e = cudaMalloc((void**)&F->work, sizeof(double) * (Fem::kWorkPerDof * (size_t)ndof + 16 * (size_t)E))) ||
-        (e = cudaMalloc((void**)&F->part, sizeof(double) * 4 * Fem::kDotBlocks)) ||
+        (e = cudaMalloc((void**)&F->part, sizeof(double) * 12 * Fem::kDotBlocks)) ||
         (e = cudaMalloc((void**)&F->scal, sizeof(double) * kNScal)) ||
         (e = cudaMallocHost((void**)&F->scal_host, sizeof(double) * kNScal))) {
         fem_free(F);
@@ -506,16 +592,18 @@ namespace {
 void launch_dot(const Fem& F, const double* x, const double* y, int nv, int slot, int mode, cudaStream_t st)
 {
     const int nb = (int)std::min<unsigned>(Fem::kDotBlocks, blocks(F.ndof, kDotThreads));
-    dot_kernel<<<nb, kDotThreads, 0, st>>>(x, y, F.ndof, nv, F.part);
-    scalar_kernel<<<1, 32, 0, st>>>(F.part, nb, nv, slot, mode, F.scal);
+    dot_kernel<<<nb, kDotThreads, 0, st>>>(x, y, F.ndof, nv, F.part + 8 * Fem::kDotBlocks);
+    scalar_kernel<<<1, 32, 0, st>>>(F.part + 8 * Fem::kDotBlocks, nb, nv, slot, mode, F.scal);
 }
 
 // Jacobi-preconditioned CG on nv <= 4 systems with the same matrix A (diagonal `diag`).
 // x holds the start vector, with the fixed values in place on the wall rows when `mask` is set
-// (those rows are not solved for). Converged when ||r_c|| <= tol ||r_c(0)|| for every c
-// (tested on the host every kCheckEvery iterations). Returns cudaErrorNotReady if not converged.
-cudaError_t pcg(const Fem& F, const double* A, const double* diag, const double* b, double* x, int nv, int mask,
-                double tol, int maxit, int* iters, double* scratch, cudaStream_t st)
+// (those rows are not solved for). Converged when ||r_c|| <= tol ||r_c(xref)|| for every c, the
+// residual of the reference start xref (xref = NULL: x itself); tested on the host every
+// kCheckEvery iterations. Five launches per iteration: q = A p with p.q, alpha, the update with
+// r.z and r.r, beta, the new direction. Returns cudaErrorNotReady if not converged.
+cudaError_t pcg(const Fem& F, const double* A, const double* diag, const double* b, double* x, const double* xref,
+                int nv, int mask, double tol, int maxit, int* iters, double* scratch, cudaStream_t st)
 {
     const size_t n = F.ndof;
     double* r = scratch;
@@ -523,16 +611,24 @@ cudaError_t pcg(const Fem& F, const double* A, const double* diag, const double*
     double* p = z + 4 * n;
     double* q = p + 4 * n;
     const unsigned g = blocks((int64_t)n);
+    const int nb = (int)std::min<unsigned>(Fem::kDotBlocks, blocks(F.ndof, kDotThreads));
+    double* part_rz = F.part;
+    double* part_rr = F.part + 4 * Fem::kDotBlocks;
+    if (xref) {
+        spmv_kernel<<<g, 256, 0, st>>>(F, A, xref, q, mask, nv);
+        cg_start_kernel<<<g, 256, 0, st>>>(F, b, q, diag, r, z, p, mask, nv);
+        launch_dot(F, r, r, nv, kR0, 0, st);
+    }
     spmv_kernel<<<g, 256, 0, st>>>(F, A, x, q, mask, nv);
     cg_start_kernel<<<g, 256, 0, st>>>(F, b, q, diag, r, z, p, mask, nv);
-    launch_dot(F, r, r, nv, kR0, 0, st);
+    if (!xref) launch_dot(F, r, r, nv, kR0, 0, st);
+    launch_dot(F, r, r, nv, kRR, 0, st);
     launch_dot(F, r, z, nv, kRZ, 0, st);
     double r0[4] = {0, 0, 0, 0};
     int it = 0;
     bool done = false;
     for (;;) {
         if (it % kCheckEvery == 0 || it >= maxit) {
-            launch_dot(F, r, r, nv, kRR, 0, st);
             cudaError_t e = cudaMemcpyAsync(F.scal_host, F.scal, sizeof(double) * kNScal, cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) return e;
@@ -543,10 +639,10 @@ cudaError_t pcg(const Fem& F, const double* A, const double* diag, const double*
                 if (std::sqrt(F.scal_host[kRR + c]) > tol * r0[c]) done = false;
             if (done || it >= maxit) break;
         }
-        spmv_kernel<<<g, 256, 0, st>>>(F, A, p, q, mask, nv);
-        launch_dot(F, p, q, nv, kDot, 1, st);                      // alpha = rz / pq
-        cg_update_kernel<<<g, 256, 0, st>>>((int)n, nv, F.scal, diag, p, q, x, r, z);
-        launch_dot(F, r, z, nv, kRZ, 2, st);                       // beta = rz_new / rz
+        spmv_dot_kernel<<<nb, kDotThreads, 0, st>>>(F, A, p, q, mask, nv, F.part);
+        scalar_kernel<<<1, 32, 0, st>>>(F.part, nb, nv, kDot, 1, F.scal);          // alpha = rz / pq
+        update_dot_kernel<<<nb, kDotThreads, 0, st>>>((int)n, nv, F.scal, diag, p, q, x, r, z, part_rz, part_rr);
+        scalar_beta_kernel<<<1, 32, 0, st>>>(part_rz, part_rr, nb, nv, F.scal);    // beta, rz, rr
         cg_direction_kernel<<<g, 256, 0, st>>>((int)n, nv, F.scal, z, p);
         ++it;
     }
@@ -558,7 +654,7 @@ cudaError_t pcg(const Fem& F, const double* A, const double* diag, const double*
 
 }  // namespace
 
-cudaError_t node_fields_solve(const Fem& F, const double* stats, const lpdf_params& P, float* out, double tol,
+cudaError_t node_fields_solve(Fem& F, const double* stats, const lpdf_params& P, float* out, double tol,
                               int maxit, int* iters, cudaStream_t st)
 {
     const int ns = P.ns;
@@ -580,6 +676,9 @@ cudaError_t node_fields_solve(const Fem& F, const double* stats, const lpdf_para
     double* rhs = w;    w += 4 * n;
     double* tmp = w;    w += 4 * n;
     double* cgs = w;    w += 16 * n;      // r, z, p, q of the CG
+    double* xref = w;   w += 4 * n;       // the zero-interior start (reference of the test)
+    double* wp_prev = w; w += 4 * n;      // previous solutions (warm start)
+    double* p_prev = w; w += n;
     double* ew = F.work + Fem::kWorkPerDof * n;   // element scratch, 16 per element
     const unsigned gd = blocks((int64_t)n), ge = blocks(F.E);
     iters[0] = iters[1] = 0;
@@ -594,10 +693,14 @@ cudaError_t node_fields_solve(const Fem& F, const double* stats, const lpdf_para
     if (P.gmodel == 0) {
         elem_L2_kernel<<<ge, 256, 0, st>>>(F, k, eps, P.CL, P.Ceta, P.nu, ew);
         assemble_kernel<<<gd, 256, 0, st>>>(F, ew, F.Aval, diag);
-        er_setup_kernel<<<gd, 256, 0, st>>>(F, eps, P.C0, tmp, wp);
+        const bool warm = P.cg_warm_start && F.has_wp;
+        er_setup_kernel<<<gd, 256, 0, st>>>(F, eps, P.C0, tmp, wp, warm ? wp_prev : nullptr, xref);
         spmv_kernel<<<gd, 256, 0, st>>>(F, F.Mval, tmp, rhs, 0, 4);     // b = M wp^h
-        cudaError_t e = pcg(F, F.Aval, diag, rhs, wp, 4, 1, tol, maxit, &iters[0], cgs, st);
+        cudaError_t e = pcg(F, F.Aval, diag, rhs, wp, xref, 4, 1, tol, maxit, &iters[0], cgs, st);
         if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync(wp_prev, wp, sizeof(double) * 4 * n, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+        F.has_wp = true;
     }
     if (P.pressure_solve) {
         pressure_T_kernel<<<gd, 256, 0, st>>>(F, U, R, tmp);
@@ -605,15 +708,25 @@ cudaError_t node_fields_solve(const Fem& F, const double* stats, const lpdf_para
         pressure_rhs_kernel<<<gd, 256, 0, st>>>(F, ew, rhs);
         diag_kernel<<<gd, 256, 0, st>>>(F, F.Kval, diag);
         double* p = tmp;
-        fill_kernel<<<gd, 256, 0, st>>>((int)n, 0.0, p);
-        // consistent singular system (the right-hand side sums to zero): CG from zero stays in
-        // the range up to rounding; the constant is removed afterwards
-        cudaError_t e = pcg(F, F.Kval, diag, rhs, p, 1, 0, tol, maxit, &iters[1], cgs, st);
+        const bool warm = P.cg_warm_start && F.has_p;
+        if (warm) {
+            cudaError_t e = cudaMemcpyAsync(p, p_prev, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return e;
+        } else {
+            fill_kernel<<<gd, 256, 0, st>>>((int)n, 0.0, p);
+        }
+        // consistent singular system (the right-hand side sums to zero): CG stays in the range up
+        // to rounding; the constant is removed afterwards. Reference start: zero.
+        fill_kernel<<<gd, 256, 0, st>>>((int)n, 0.0, xref);
+        cudaError_t e = pcg(F, F.Kval, diag, rhs, p, warm ? xref : nullptr, 1, 0, tol, maxit, &iters[1], cgs, st);
         if (e != cudaSuccess) return e;
         double* ones = rhs + n;
         fill_kernel<<<gd, 256, 0, st>>>((int)n, 1.0, ones);
         launch_dot(F, p, ones, 1, kDot, 0, st);
         subtract_mean_kernel<<<gd, 256, 0, st>>>((int)n, F.scal + kDot, p);
+        e = cudaMemcpyAsync(p_prev, p, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+        F.has_p = true;
         elem_grad_kernel<<<ge, 256, 0, st>>>(F, p, 1, 1, ew);
         recover_kernel<<<gd, 256, 0, st>>>(F, ew, 2, gp, 2);
     } else {

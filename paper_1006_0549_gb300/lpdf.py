@@ -52,7 +52,7 @@ class Params(ctypes.Structure):
                 ("n_sources", ctypes.c_int32), ("src_x", ctypes.c_float * MAX_SOURCES),
                 ("src_y", ctypes.c_float * MAX_SOURCES), ("src_r", ctypes.c_float * MAX_SOURCES),
                 ("src_alpha", ctypes.c_int32 * MAX_SOURCES),
-                ("gmodel", ctypes.c_int32), ("pressure_solve", ctypes.c_int32), ("reserved_", ctypes.c_int32),
+                ("gmodel", ctypes.c_int32), ("pressure_solve", ctypes.c_int32), ("cg_warm_start", ctypes.c_int32),
                 ("dpdx0", ctypes.c_double), ("dpdy0", ctypes.c_double)]
 
 
