@@ -251,6 +251,18 @@ int lpdf_elliptic_relax_solve(const lpdf_mesh* mesh, const lpdf_params* params, 
                               float* fields, double tol, int32_t maxit, int32_t* iters, void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * lpdf_tc_gemm_bf16 -- the tensor-core tile of the learned relaxation surrogate (NEXT: an MLP
+ * in place of lpdf_elliptic_relax_solve), exposed to test it: D = A B^T on the fifth-generation
+ * tensor cores (tcgen05, BF16 inputs, FP32 accumulation in tensor memory). The paper has no
+ * counterpart. sync.
+ *   A  device, M x K BF16 row-major; B device, N x K BF16 row-major; D device, M x N FP32.
+ *   M >= 1; N a multiple of 16 in 16..256; K a multiple of 16 in 16..128.
+ * Errors: LPDF_ERR_ARG (shape, NULL), LPDF_ERR_CUDA (launch, or a bounded wait for the MMAs
+ * gave up).
+ * ------------------------------------------------------------------------------------- */
+int lpdf_tc_gemm_bf16(const void* A, const void* B, float* D, int32_t M, int32_t N, int32_t K, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * lpdf_pdf_step_static -- the same particle step as lpdf_pdf_step for callers that cannot
  * allocate device memory (the paper has no counterpart: this is an interface choice of the
  * library). Hosts that own every device buffer through their own pool or arena, or that

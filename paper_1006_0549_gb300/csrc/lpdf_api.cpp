@@ -602,4 +602,21 @@ int lpdf_elliptic_relax_solve(const lpdf_mesh* mesh, const lpdf_params* params, 
     return LPDF_OK;
 }
 
+int lpdf_tc_gemm_bf16(const void* A, const void* B, float* D, int32_t M, int32_t N, int32_t K, void* stream)
+{
+    if (!A || !B || !D) return fail(LPDF_ERR_ARG, "tc_gemm_bf16: NULL argument");
+    if (M < 1 || N < 16 || N > 256 || N % 16 || K < 16 || K > 128 || K % 16)
+        return fail(LPDF_ERR_ARG, "tc_gemm_bf16: shape M = %d, N = %d, K = %d", M, N, K);
+    static unsigned* err_dev = nullptr;
+    if (!err_dev) CUDA_TRY(cudaMalloc(&err_dev, sizeof(unsigned)));
+    const cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemsetAsync(err_dev, 0, sizeof(unsigned), st));
+    CUDA_TRY(launch_tc_gemm(A, B, D, M, N, K, err_dev, st));
+    unsigned err = 0;
+    CUDA_TRY(cudaMemcpyAsync(&err, err_dev, sizeof err, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (err) return fail(LPDF_ERR_CUDA, "tc_gemm_bf16: a bounded wait for the tensor-core MMAs gave up");
+    return LPDF_OK;
+}
+
 }  // extern "C"

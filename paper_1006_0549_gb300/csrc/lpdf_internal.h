@@ -104,6 +104,10 @@ cudaError_t launch_pdf_step_pipeline(const DevMesh& m, const DevState& cur, cons
                                      const cudaEvent_t* ev);
 cudaError_t launch_iota(int* p, int64_t n, cudaStream_t st);
 
+// tensor-core GEMM tile (lpdf_mlp.cu): D = A B^T, BF16 operands, FP32 result
+cudaError_t launch_tc_gemm(const void* A, const void* B, float* D, int M, int N, int K, unsigned* error,
+                           cudaStream_t st);
+
 // P1 finite-element tables of the gridpoint solve (lpdf_solve.cu), built once per mesh.
 // DOFs are the geometric nodes with periodic partners merged (numbered in node order).
 struct Fem {

@@ -35,7 +35,7 @@ EXPORTS = ("lpdf_params_default", "lpdf_last_error", "lpdf_version", "lpdf_mesh_
            "lpdf_mesh_info", "lpdf_mesh_neighbors", "lpdf_mesh_masters", "lpdf_ctx_create", "lpdf_ctx_free",
            "lpdf_ctx_set_params", "lpdf_ctx_size", "lpdf_particles_init", "lpdf_set_state", "lpdf_get_state",
            "lpdf_pdf_step", "lpdf_status", "lpdf_grid_statistics", "lpdf_pdf_step_static", "lpdf_sort",
-           "lpdf_elliptic_relax_solve", "lpdf_ctx_set_timing", "lpdf_ctx_timings")
+           "lpdf_elliptic_relax_solve", "lpdf_ctx_set_timing", "lpdf_ctx_timings", "lpdf_tc_gemm_bf16")
 
 
 class LpdfError(RuntimeError):
@@ -93,6 +93,7 @@ def lib():
     L.lpdf_status.argtypes = [vp, vp, vp]
     L.lpdf_grid_statistics.argtypes = [vp, vp, ctypes.c_int, vp]
     L.lpdf_pdf_step_static.argtypes = [vp, vp, i64] + [vp] * 9 + [vp, u64, vp, vp, vp]
+    L.lpdf_tc_gemm_bf16.argtypes = [vp, vp, vp, i32, i32, i32, vp]
     L.lpdf_ctx_set_timing.argtypes = [vp, ctypes.c_int]
     L.lpdf_ctx_timings.argtypes = [vp, vp, vp]
     L.lpdf_elliptic_relax_solve.argtypes = [vp, vp, vp, vp, ctypes.c_double, i32, vp, vp]
@@ -300,6 +301,15 @@ def pdf_step_static(mesh: Mesh, params: Params, state: dict, node_fields, step: 
                                                                "pid")],
                                     _ptr(node_fields), int(step), _ptr(moments), _ptr(st), _stream(stream))
     return rc, st
+
+
+def tc_gemm_bf16(A, B, D, stream=None):
+    """lpdf_tc_gemm_bf16: D = A B^T on the tensor cores (A: M x K, B: N x K BF16; D: M x N FP32;
+    torch CUDA tensors)."""
+    M, K = A.shape
+    N = B.shape[0]
+    _check(lib().lpdf_tc_gemm_bf16(_ptr(A), _ptr(B), _ptr(D), int(M), int(N), int(K), _stream(stream)))
+    return D
 
 
 def version() -> str:
