@@ -428,3 +428,28 @@ def cavity_small(seed: int = 1006054903) -> Workload:
     m = cavity_mesh(32, 32, seed)
     src = [(0.25, 0.25, 0.02, 0), (0.75, 0.25, 0.02, 1), (0.5, 0.5, 0.02, 2), (0.5, 0.8, 0.02, 3)]
     return Workload("cavity-2k-100k", m, 50, 4, 1e-4, 1e-3, seed, 1.0, src)
+
+
+def mlp_init_params(seed: int, n_in: int = 8, hidden: int = 128, n_out: int = 7) -> np.ndarray:
+    """Seeded starting parameters of the surrogate network (ABI order W1, b1, W2, b2, W3, b3, W4, b4;
+    W [out][in]): weights uniform in +-sqrt(6 / (fan_in + fan_out)) (Glorot), biases zero."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fi, fo in ((n_in, hidden), (hidden, hidden), (hidden, hidden), (hidden, n_out)):
+        a = np.sqrt(6.0 / (fi + fo))
+        parts.append(rng.uniform(-a, a, size=fo * fi))
+        parts.append(np.zeros(fo))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def mlp_random_data(n: int, seed: int, n_in: int = 8, n_out: int = 7):
+    """Seeded regression data for the network alone: features with unequal scales and offsets and
+    smooth nonlinear targets of them (float32 arrays n x n_in and n x n_out)."""
+    rng = np.random.default_rng(seed)
+    scale = np.linspace(0.5, 3.0, n_in)
+    shift = np.linspace(-1.0, 2.0, n_in)
+    feat = shift + scale * rng.standard_normal((n, n_in))
+    z = (feat - shift) / scale
+    mix = rng.standard_normal((n_in, n_out)) / np.sqrt(n_in)
+    tgt = np.sin(z @ mix) + 0.3 * (z[:, :n_out] ** 2 if n_out <= n_in else 0.0) + np.arange(n_out)
+    return feat.astype(np.float32), tgt.astype(np.float32)
