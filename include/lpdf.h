@@ -251,8 +251,8 @@ int lpdf_elliptic_relax_solve(const lpdf_mesh* mesh, const lpdf_params* params, 
                               float* fields, double tol, int32_t maxit, int32_t* iters, void* stream);
 
 /* ---------------------------------------------------------------------------------------
- * lpdf_tc_gemm_bf16 -- the tensor-core tile of the learned relaxation surrogate (NEXT: an MLP
- * in place of lpdf_elliptic_relax_solve), exposed to test it: D = A B^T on the fifth-generation
+ * lpdf_tc_gemm_bf16 -- the tensor-core tile of the learned relaxation surrogate, exposed to
+ * test it: D = A B^T on the fifth-generation
  * tensor cores (tcgen05, BF16 inputs, FP32 accumulation in tensor memory). The paper has no
  * counterpart. sync.
  *   A  device, M x K BF16 row-major; B device, N x K BF16 row-major; D device, M x N FP32.
@@ -261,6 +261,104 @@ int lpdf_elliptic_relax_solve(const lpdf_mesh* mesh, const lpdf_params* params, 
  * gave up).
  * ------------------------------------------------------------------------------------- */
 int lpdf_tc_gemm_bf16(const void* A, const void* B, float* D, int32_t M, int32_t N, int32_t K, void* stream);
+
+/* =======================================================================================
+ * The learned surrogate of lpdf_elliptic_relax_solve. The paper has no counterpart: its G_ij
+ * comes from the elliptic relaxation (the paragraph after Eq. 4); here a small network maps
+ * local quantities at each gridpoint to the same outputs, is trained on fields that the plain
+ * solve generates, and is checked against the plain solve at a fixed cadence, falling back to
+ * it when the error exceeds a threshold.
+ *
+ * Network: 8 inputs -> 128 -> 128 -> 128 (tanh) -> 7 linear outputs. Inputs are standardised
+ * with per-column means and deviations, outputs are standardised targets. The three hidden
+ * layers and the output layer run on the fifth-generation tensor cores with BF16 operands
+ * (inputs, weights, activations and, in the backward pass, the error signals are rounded to
+ * BF16) and FP32 accumulation; biases, tanh, the loss and the optimiser are FP32.
+ *
+ * Parameter vector (LPDF_MLP_NPARAMS floats, in this order): W1 [128][8], b1 [128],
+ * W2 [128][128], b2 [128], W3 [128][128], b3 [128], W4 [7][128], b4 [7]; W [out][in] row-major,
+ * layer l computes z = W a + b.
+ * Standardisation block (LPDF_MLP_NNORM floats): feature means [8], feature deviations [8],
+ * loss weights [7], target means [7], target deviations [7].
+ * Inputs (per gridpoint): wall distance, ln k, ln <omega>, b11, b22, b33, b12 and II_b = b_ij b_ij,
+ * b_ij = <u_i u_j> / (2 k) - delta_ij / 3 (b = 0 where k <= 1e-12; the logarithms of
+ * max(., 1e-12)).
+ * Targets: G11, G12, G21, G22, G33 divided by <omega>, C0 eps / (k <omega>), and the relaxed trace
+ * wp_ii = k G_ii + 3 eps / 2 over its local value -9/4 C0 eps (1 where eps <= 1e-12; this last
+ * output is a diagnostic of the wall effect and is not used by the step); <omega> and k below
+ * 1e-12 are taken as 1e-12 in the divisions.
+ * Loss: sum over rows and outputs of w_j (y_j - t_j)^2 / (7 B), y and t standardised.
+ * ===================================================================================== */
+#define LPDF_MLP_IN 8
+#define LPDF_MLP_OUT 7
+#define LPDF_MLP_HIDDEN 128
+#define LPDF_MLP_NPARAMS 35079
+#define LPDF_MLP_NNORM 37
+
+typedef struct lpdf_mlp lpdf_mlp;
+
+/* lpdf_mlp_create -- a network with zero parameters, identity standardisation (means 0,
+ * deviations 1, weights 1), and the fallback policy check_every = 50, threshold = 0.02.
+ * max_batch: the largest batch of lpdf_mlp_gradient and lpdf_mlp_train (>= 1).
+ * Errors: LPDF_ERR_ARG, LPDF_ERR_CUDA. */
+int lpdf_mlp_create(int64_t max_batch, lpdf_mlp** out);
+void lpdf_mlp_free(lpdf_mlp* m);
+
+/* lpdf_mlp_set_params -- sync. params host, LPDF_MLP_NPARAMS floats (layout above); norm host,
+ * LPDF_MLP_NNORM floats, or NULL to keep the current block. Resets the optimiser state. */
+int lpdf_mlp_set_params(lpdf_mlp* m, const float* params, const float* norm);
+/* lpdf_mlp_get_params -- sync. params and norm host out (either may be NULL). */
+int lpdf_mlp_get_params(lpdf_mlp* m, float* params, float* norm);
+
+/* lpdf_mlp_fit_norm -- async. Sets the feature and target means and deviations of the
+ * standardisation block from a data set (feat device B x 8, tgt device B x 7, FP32); a deviation
+ * below 1e-6 max(1, |mean|) is taken as 1. The loss weights are kept. */
+int lpdf_mlp_fit_norm(lpdf_mlp* m, const float* feat, const float* tgt, int64_t B, void* stream);
+
+/* lpdf_mlp_forward -- async. out device, B x 7 FP32: the outputs in target units (standardised
+ * output times the target deviation plus the target mean). feat device, B x 8 FP32. Any B >= 0. */
+int lpdf_mlp_forward(lpdf_mlp* m, const float* feat, int64_t B, float* out, void* stream);
+
+/* lpdf_mlp_gradient -- sync. The gradient of the loss on the batch (feat device B x 8, tgt device
+ * B x 7, 1 <= B <= max_batch) with respect to the parameters: grad host, LPDF_MLP_NPARAMS floats
+ * (layout above); loss host (may be NULL). The per-tile partial gradients are summed in a fixed
+ * order, so the result is bit-reproducible. */
+int lpdf_mlp_gradient(lpdf_mlp* m, const float* feat, const float* tgt, int64_t B, float* grad, double* loss,
+                      void* stream);
+
+/* lpdf_mlp_train -- sync at the end. `steps` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, bias
+ * correction, learning rate lr) on minibatches of `batch` rows: step s uses rows
+ * [c batch, (c + 1) batch) with c = s mod floor(B / batch) (shuffle the data set beforehand).
+ * feat device B x 8, tgt device B x 7; 1 <= batch <= min(B, max_batch). losses host (may be
+ * NULL): the minibatch loss before each step. The step count of the bias correction continues
+ * across calls until lpdf_mlp_set_params. */
+int lpdf_mlp_train(lpdf_mlp* m, const float* feat, const float* tgt, int64_t B, int64_t batch, int32_t steps,
+                   float lr, double* losses, void* stream);
+
+/* lpdf_surrogate_features -- async. Per geometric node of the mesh: feat device n_nodes x 8
+ * (the inputs above) from stats (device, n_nodes x (11 + 2 ns) FP64 as lpdf_grid_statistics
+ * raw = 0 writes them); with fields != NULL (device, n_nodes x nfp, e.g. from
+ * lpdf_elliptic_relax_solve) also tgt device n_nodes x 7 (the targets above; params->C0 is used).
+ * The wall distance is the distance to the nearest LPDF_EDGE_WALL or LPDF_EDGE_MOVING_WALL edge
+ * (in a periodic mesh also to their images one period away), computed on first use. */
+int lpdf_surrogate_features(const lpdf_mesh* mesh, const lpdf_params* params, const double* stats,
+                            const float* fields, float* feat, float* tgt, void* stream);
+
+/* lpdf_mlp_set_policy -- the fallback policy of lpdf_surrogate_relax_solve: every check_every-th
+ * call (the first call included; 0: never) also runs the plain solve and compares. */
+int lpdf_mlp_set_policy(lpdf_mlp* m, int32_t check_every, double threshold);
+
+/* lpdf_surrogate_relax_solve -- lpdf_elliptic_relax_solve (gmodel 0) with G_ij and C0 eps from
+ * the network. sync. Everything else (gradients, Laplacians, pressure, S_omega) is computed as
+ * in the plain solve. On a checking call the plain solve runs too, the error
+ * e = |F_net - F_plain| / |F_plain| (Frobenius norms over the node columns G11..G33 and C0 eps)
+ * is measured, the plain fields are returned, and the network is used on the following calls
+ * only if e <= threshold; otherwise the plain solve runs until the next checking call.
+ *   info host out (may be NULL), 4 doubles: 1 if this call checked, e (-1 when not checked),
+ *   1 if the returned fields come from the plain solve, the call count so far.
+ * Errors: as lpdf_elliptic_relax_solve; LPDF_ERR_ARG when params->gmodel != 0. */
+int lpdf_surrogate_relax_solve(const lpdf_mesh* mesh, lpdf_mlp* m, const lpdf_params* params, const double* stats,
+                               float* fields, double tol, int32_t maxit, double* info, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * lpdf_pdf_step_static -- the same particle step as lpdf_pdf_step for callers that cannot

@@ -123,6 +123,20 @@ int check_params(const lpdf_params* p)
 
 }  // namespace
 
+int lpdf::mesh_fem(const lpdf_mesh* mesh, Fem** out)
+{
+    std::lock_guard<std::mutex> lock(mesh->fem_mutex);
+    if (!mesh->fem) {
+        Fem* F = nullptr;
+        cudaError_t e = fem_build(mesh->node_xy.data(), mesh->d.n_nodes, mesh->tri.data(), mesh->d.n_tri,
+                                  mesh->tag.data(), mesh->master, mesh->d.periodic ? mesh->box[1] - mesh->box[0] : 0.0, &F);
+        if (e != cudaSuccess) return fail(LPDF_ERR_CUDA, "gridpoint tables: %s", cudaGetErrorString(e));
+        mesh->fem = F;
+    }
+    *out = mesh->fem;
+    return LPDF_OK;
+}
+
 extern "C" {
 
 void lpdf_params_default(lpdf_params* p)
@@ -578,19 +592,10 @@ int lpdf_elliptic_relax_solve(const lpdf_mesh* mesh, const lpdf_params* params, 
                     params->pressure_solve);
     if (!(tol > 0.0) || maxit < 1)
         return fail(LPDF_ERR_ARG, "elliptic_relax_solve: tol = %g, maxit = %d", tol, maxit);
-    {
-        std::lock_guard<std::mutex> lock(mesh->fem_mutex);
-        if (!mesh->fem) {
-            Fem* F = nullptr;
-            cudaError_t e = fem_build(mesh->node_xy.data(), mesh->d.n_nodes, mesh->tri.data(), mesh->d.n_tri,
-                                      mesh->tag.data(), mesh->master, &F);
-            if (e != cudaSuccess)
-                return fail(LPDF_ERR_CUDA, "elliptic_relax_solve: table upload: %s", cudaGetErrorString(e));
-            mesh->fem = F;
-        }
-    }
+    Fem* F = nullptr;
+    if (const int rc = mesh_fem(mesh, &F)) return rc;
     int it[2] = {0, 0};
-    const cudaError_t e = node_fields_solve(*mesh->fem, stats, *params, fields, tol, maxit, it, (cudaStream_t)stream);
+    const cudaError_t e = node_fields_solve(*F, stats, *params, fields, tol, maxit, it, (cudaStream_t)stream);
     if (iters) {
         iters[0] = it[0];
         iters[1] = it[1];

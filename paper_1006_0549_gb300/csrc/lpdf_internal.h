@@ -137,14 +137,63 @@ struct Fem {
     double* scal_host = nullptr; // pinned copy
     bool has_wp = false;         // the scratch holds a previous relaxation / pressure solution
     bool has_p = false;
+    // wall distance of every geometric node (inputs of the learned surrogate)
+    double* xy = nullptr;        // 2 per geometric node
+    double* seg = nullptr;       // 4 per wall edge: (xa, ya, xb, yb)
+    int nseg = 0;
+    double period = 0.0;         // x period (0: none)
+    double* wdist = nullptr;     // per geometric node, filled on first use
+    bool has_wdist = false;
 };
 cudaError_t fem_build(const double* node_xy, int n_nodes, const int32_t* tri, int n_tri, const int32_t* tag,
-                      const std::vector<int32_t>& master, Fem** out);
+                      const std::vector<int32_t>& master, double period, Fem** out);
 void fem_free(Fem* F);
 // statistics (n_nodes x (11 + 2 ns), lpdf_grid_statistics raw = 0) -> node fields; iters[2];
-// cudaErrorNotReady when a CG did not converge within maxit
+// cudaErrorNotReady when a CG did not converge within maxit. With surr != NULL (n_nodes x 16
+// standardised surrogate outputs, standardisation block surr_norm) the relaxation solve is
+// replaced by the surrogate's G_ij and C_0 epsilon.
 cudaError_t node_fields_solve(Fem& F, const double* stats, const lpdf_params& P, float* out, double tol,
-                              int maxit, int* iters, cudaStream_t st);
+                              int maxit, int* iters, cudaStream_t st, const float* surr = nullptr,
+                              const float* surr_norm = nullptr);
+// per geometric node: the 8 surrogate inputs (feat, n_nodes x 8) and, when fields != NULL, the 7
+// targets taken from those node fields (tgt, n_nodes x 7)
+cudaError_t surrogate_features(Fem& F, const double* stats, int ns, const float* fields, double C0, float* feat,
+                               float* tgt, cudaStream_t st);
+// out2 = {sum (a - b)^2, sum b^2} over the G_ij and C_0 epsilon columns of two node-field tables
+cudaError_t fields_compare(const float* a, const float* b, int n_nodes, int nfp, double* out2, cudaStream_t st);
+
+// the learned surrogate network (8 -> 128 -> 128 -> 128 -> 7, tanh, BF16 operands)
+namespace mlp {
+constexpr int kIn = 8, kInP = 16, kH = 128, kOut = 7, kOutP = 16;
+// FP32 master parameters, padded: W1[128][16] (inputs 8..15 zero), b1[128], W2[128][128], b2[128],
+// W3[128][128], b3[128], W4[16][128] (rows 7..15 zero), b4[16]
+constexpr int oW1 = 0, ob1 = oW1 + kH * kInP, oW2 = ob1 + kH, ob2 = oW2 + kH * kH, oW3 = ob2 + kH, ob3 = oW3 + kH * kH,
+              oW4 = ob3 + kH, ob4 = oW4 + kOutP * kH, kParams = ob4 + kOutP;
+// BF16 packs: row-major [out][in] for the forward, [in][out] for the backward
+constexpr int pW1 = 0, pW2 = pW1 + kH * kInP, pW3 = pW2 + kH * kH, pW4 = pW3 + kH * kH, pT2 = pW4 + kOutP * kH,
+              pT3 = pT2 + kH * kH, pT4 = pT3 + kH * kH, kPack = pT4 + kH * kOutP;
+// per-CTA gradient partials: W^T layouts [in][out] and the biases
+constexpr int gW1 = 0, gW2 = gW1 + kInP * kH, gW3 = gW2 + kH * kH, gW4 = gW3 + kH * kH, gb1 = gW4 + kH * kOutP,
+              gb2 = gb1 + kH, gb3 = gb2 + kH, gb4 = gb3 + kH, kPart = gb4 + kOutP;
+// standardisation block: feature means and deviations, loss weights, target means and deviations
+constexpr int nFM = 0, nFS = nFM + kIn, nW = nFS + kIn, nTM = nW + kOut, nTS = nTM + kOut, kNorm = nTS + kOut;
+}  // namespace mlp
+cudaError_t mlp_configure();
+cudaError_t launch_mlp_forward(const float* feat, int64_t B, const float* P, const void* pack, const float* norm,
+                               float* out, float* out_user, void* act, unsigned* error, cudaStream_t st);
+// per-CTA partials into part ((B + 127) / 128 x kPart), then their sum in CTA order into grad
+cudaError_t launch_mlp_backward(const float* feat, const float* tgt, int64_t B, const void* pack, const float* norm,
+                                const float* out, const void* act, float* part, float* grad, unsigned* error,
+                                cudaStream_t st);
+cudaError_t launch_mlp_adam(float* P, const float* grad, float* m, float* v, float lr, int step, void* pack,
+                            cudaStream_t st);
+cudaError_t launch_mlp_loss(const float* out, const float* tgt, int64_t B, const float* norm, double* loss,
+                            cudaStream_t st);
+// feature and target means and deviations of a data set into norm (weights untouched)
+cudaError_t launch_mlp_fit_norm(const float* feat, const float* tgt, int64_t B, float* norm, cudaStream_t st);
+
+// the gridpoint tables of a mesh, built on first use (LPDF_OK or an error code with the message set)
+int mesh_fem(const struct ::lpdf_mesh* mesh, Fem** out);
 
 StepParams make_step_params(const lpdf_params& p, const struct ::lpdf_mesh* m, uint64_t step);
 // records the calling thread's error message (lpdf_last_error) and returns `code`

@@ -413,7 +413,8 @@ __global__ void fields_kernel(const Fem F, int ns, int nfp, const double* __rest
                               const double* __restrict__ k, const double* __restrict__ eps,
                               const double* __restrict__ gU, const double* __restrict__ lapU,
                               const double* __restrict__ gp, const double* __restrict__ wp, int gmodel, double C0,
-                              double Comega1, double Comega2, double dpdx0, double dpdy0, float* __restrict__ out)
+                              double Comega1, double Comega2, double dpdx0, double dpdy0,
+                              const float* __restrict__ surr, const float* __restrict__ snorm, float* __restrict__ out)
 {
     const int nd = blockIdx.x * blockDim.x + threadIdx.x;
     if (nd >= F.N) return;
@@ -424,10 +425,21 @@ __global__ void fields_kernel(const Fem F, int ns, int nfp, const double* __rest
     const double kk = k[d], e = eps[d], Om = om[d];
     const double prod = -(r[0] * g[0] + r[1] * g[1] + r[1] * g[2] + r[3] * g[3] + r[2] * g[4] + r[4] * g[5]);
     const double Som = e > 1e-12 ? Comega2 - Comega1 * prod / e : Comega2;
-    double G11, G12, G22, G33, c0e;
-    if (gmodel == 1) {
+    double G11, G12, G21, G22, G33, c0e;
+    if (surr) {
+        // the surrogate's targets: G_ij / <omega> and C_0 epsilon / (k <omega>), standardised
+        double y[6];
+        for (int j = 0; j < 6; ++j)
+            y[j] = (double)surr[(size_t)nd * mlp::kOutP + j] * snorm[mlp::nTS + j] + snorm[mlp::nTM + j];
+        G11 = Om * y[0];
+        G12 = Om * y[1];
+        G21 = Om * y[2];
+        G22 = Om * y[3];
+        G33 = Om * y[4];
+        c0e = fmax(0.0, kk * Om * y[5]);
+    } else if (gmodel == 1) {
         G11 = G22 = G33 = -(0.5 + 0.75 * C0) * Om;
-        G12 = 0.0;
+        G12 = G21 = 0.0;
         c0e = C0 * e;
     } else {
         const double kc = fmax(kk, 1e-12);
@@ -436,6 +448,7 @@ __global__ void fields_kernel(const Fem F, int ns, int nfp, const double* __rest
         G22 = (wp[2 * n + d] - 0.5 * e) / kc;
         G33 = (wp[3 * n + d] - 0.5 * e) / kc;
         c0e = fmax(0.0, -2.0 / 3.0 * (e + r[0] * G11 + 2.0 * r[1] * G12 + r[3] * G22 + r[5] * G33));
+        G21 = G12;
     }
     float* o = out + (size_t)nd * nfp;
     o[LPDF_F_U + 0] = (float)U[3 * d];
@@ -447,7 +460,7 @@ __global__ void fields_kernel(const Fem F, int ns, int nfp, const double* __rest
     o[LPDF_F_DPDX + 1] = (float)(gp[2 * d + 1] + dpdy0);
     o[LPDF_F_G11] = (float)G11;
     o[LPDF_F_G11 + 1] = (float)G12;
-    o[LPDF_F_G11 + 2] = (float)G12;
+    o[LPDF_F_G11 + 2] = (float)G21;
     o[LPDF_F_G11 + 3] = (float)G22;
     o[LPDF_F_G11 + 4] = (float)G33;
     o[LPDF_F_C0EPS] = (float)c0e;
@@ -457,12 +470,105 @@ __global__ void fields_kernel(const Fem F, int ns, int nfp, const double* __rest
     for (int i = LPDF_F_PHI0 + ns; i < nfp; ++i) o[i] = 0.0f;
 }
 
+// ---------------------------------------------------------------- learned-surrogate inputs
+// distance of every geometric node to the nearest wall edge (and its images one period away)
+__global__ void wall_distance_kernel(int N, const double* __restrict__ xy, const double* __restrict__ seg, int nseg,
+                                     double period, double* __restrict__ dist)
+{
+    const int nd = blockIdx.x * blockDim.x + threadIdx.x;
+    if (nd >= N) return;
+    const double px = xy[2 * nd], py = xy[2 * nd + 1];
+    double best = 1e300;
+    const int ni = period > 0.0 ? 1 : 0;
+    for (int s = 0; s < nseg; ++s) {
+        const double ax = seg[4 * s], ay = seg[4 * s + 1], tx = seg[4 * s + 2] - ax, ty = seg[4 * s + 3] - ay;
+        const double tt = tx * tx + ty * ty;
+        for (int im = -ni; im <= ni; ++im) {
+            const double qx = px - ax - im * period, qy = py - ay;
+            const double t = fmin(1.0, fmax(0.0, (qx * tx + qy * ty) / tt));
+            const double dx = qx - t * tx, dy = qy - t * ty;
+            best = fmin(best, dx * dx + dy * dy);
+        }
+    }
+    dist[nd] = nseg > 0 ? sqrt(best) : 0.0;
+}
+
+// inputs: wall distance, log k, log <omega>, b11, b22, b33, b12, II_b = b_ij b_ij with the
+// anisotropy b_ij = <u_i u_j> / (2 k) - delta_ij / 3; targets (from node fields): G11, G12, G21,
+// G22, G33 over <omega>, C_0 epsilon / (k <omega>) and the relaxed trace wp_ii over its local value
+// -9/4 C_0 epsilon (wp_ii = k G_ii + 3 epsilon / 2)
+__global__ void features_kernel(const Fem F, const double* __restrict__ stats, int nq,
+                                const float* __restrict__ fields, int nfp, double C0, float* __restrict__ feat,
+                                float* __restrict__ tgt)
+{
+    const int nd = blockIdx.x * blockDim.x + threadIdx.x;
+    if (nd >= F.N) return;
+    const double* st = stats + (size_t)F.dof_node[F.dof[nd]] * nq;
+    const double uu = st[4], uv = st[5], uw = st[6], vv = st[7], vw = st[8], ww = st[9], Om = st[10];
+    const double k = 0.5 * (uu + vv + ww);
+    double b11 = 0.0, b22 = 0.0, b33 = 0.0, b12 = 0.0, b13 = 0.0, b23 = 0.0;
+    if (k > 1e-12) {
+        const double ik = 0.5 / k;
+        b11 = uu * ik - 1.0 / 3.0;
+        b22 = vv * ik - 1.0 / 3.0;
+        b33 = ww * ik - 1.0 / 3.0;
+        b12 = uv * ik;
+        b13 = uw * ik;
+        b23 = vw * ik;
+    }
+    float* f = feat + (size_t)nd * mlp::kIn;
+    f[0] = (float)F.wdist[nd];
+    f[1] = (float)log(fmax(k, 1e-12));
+    f[2] = (float)log(fmax(Om, 1e-12));
+    f[3] = (float)b11;
+    f[4] = (float)b22;
+    f[5] = (float)b33;
+    f[6] = (float)b12;
+    f[7] = (float)(b11 * b11 + b22 * b22 + b33 * b33 + 2.0 * (b12 * b12 + b13 * b13 + b23 * b23));
+    if (!tgt) return;
+    const float* o = fields + (size_t)nd * nfp;
+    const double Omc = fmax(Om, 1e-12), kc = fmax(k, 1e-12), e = k * Om;
+    float* y = tgt + (size_t)nd * mlp::kOut;
+    for (int j = 0; j < 5; ++j) y[j] = (float)((double)o[LPDF_F_G11 + j] / Omc);
+    y[5] = (float)((double)o[LPDF_F_C0EPS] / (kc * Omc));
+    const double tr = k * ((double)o[LPDF_F_G11] + (double)o[LPDF_F_G11 + 3] + (double)o[LPDF_F_G11 + 4]) + 1.5 * e;
+    y[6] = (float)(e > 1e-12 ? tr / (-2.25 * C0 * e) : 1.0);
+}
+
+// {sum (a - b)^2, sum b^2} over the G_ij and C_0 epsilon columns (one block)
+__global__ void fields_compare_kernel(const float* __restrict__ a, const float* __restrict__ b, int N, int nfp,
+                                      double* __restrict__ out)
+{
+    __shared__ double sh[2][1024];
+    double d2 = 0.0, b2 = 0.0;
+    for (int i = threadIdx.x; i < N * 6; i += blockDim.x) {
+        const size_t at = (size_t)(i / 6) * nfp + LPDF_F_G11 + i % 6;
+        const double x = a[at], y = b[at];
+        d2 += (x - y) * (x - y);
+        b2 += y * y;
+    }
+    sh[0][threadIdx.x] = d2;
+    sh[1][threadIdx.x] = b2;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sh[0][0];
+        out[1] = sh[1][0];
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------- host side
 
 cudaError_t fem_build(const double* node_xy, int N, const int32_t* tri, int E, const int32_t* tag,
-                      const std::vector<int32_t>& master, Fem** out)
+                      const std::vector<int32_t>& master, double period, Fem** out)
 {
     *out = nullptr;
     std::vector<int> dof(N), dof_node;
@@ -547,6 +653,15 @@ cudaError_t fem_build(const double* node_xy, int N, const int32_t* tri, int E, c
                 normal[2 * d + 1] += tx / len;
             }
         }
+    std::vector<double> seg;
+    for (int e = 0; e < E; ++e)
+        for (int k = 0; k < 3; ++k) {
+            const int t = tag[3 * e + k];
+            if (t != LPDF_EDGE_WALL && t != LPDF_EDGE_MOVING_WALL) continue;
+            const int a = tri[3 * e + k], b = tri[3 * e + (k + 1) % 3];
+            seg.insert(seg.end(), {node_xy[2 * a], node_xy[2 * a + 1], node_xy[2 * b], node_xy[2 * b + 1]});
+        }
+    const std::vector<double> xy(node_xy, node_xy + 2 * (size_t)N);
     for (int d = 0; d < ndof; ++d)
         if (wall[d]) {
             const double l = std::hypot(normal[2 * d], normal[2 * d + 1]);
@@ -558,13 +673,17 @@ cudaError_t fem_build(const double* node_xy, int N, const int32_t* tri, int E, c
     F->nnz = (int)col.size();
     F->E = E;
     F->N = N;
+    F->nseg = (int)(seg.size() / 4);
+    F->period = period;
+    if (seg.empty()) seg.assign(4, 0.0);
     cudaError_t e = cudaSuccess;
     if ((e = upload(&F->dof, dof)) || (e = upload(&F->dof_node, dof_node)) || (e = upload(&F->edof, edof)) ||
         (e = upload(&F->area, area)) || (e = upload(&F->grad, grad)) || (e = upload(&F->de_ptr, de_ptr)) ||
         (e = upload(&F->de_el, de_el)) || (e = upload(&F->darea, darea)) || (e = upload(&F->row, row)) ||
         (e = upload(&F->col, col)) || (e = upload(&F->cptr, cptr)) || (e = upload(&F->cel, cel)) ||
         (e = upload(&F->Mval, Mval)) || (e = upload(&F->Kval, Kval)) || (e = upload(&F->wall, wall)) ||
-        (e = upload(&F->normal, normal)) ||
+        (e = upload(&F->normal, normal)) || (e = upload(&F->xy, xy)) || (e = upload(&F->seg, seg)) ||
+        (e = cudaMalloc((void**)&F->wdist, sizeof(double) * std::max(1, N))) ||
         (e = cudaMalloc((void**)&F->Aval, sizeof(double) * std::max(1, F->nnz))) ||
         (e = cudaMalloc((void**)&F->work, sizeof(double) * (Fem::kWorkPerDof * (size_t)ndof + 16 * (size_t)E))) ||
         (e = cudaMalloc((void**)&F->part, sizeof(double) * 12 * Fem::kDotBlocks)) ||
@@ -581,7 +700,8 @@ void fem_free(Fem* F)
 {
     if (!F) return;
     void* ps[] = {F->dof, F->dof_node, F->edof, F->area, F->grad, F->de_ptr, F->de_el, F->darea, F->row, F->col,
-                  F->cptr, F->cel, F->Mval, F->Kval, F->Aval, F->wall, F->normal, F->work, F->part, F->scal};
+                  F->cptr, F->cel, F->Mval, F->Kval, F->Aval, F->wall, F->normal, F->work, F->part, F->scal,
+                  F->xy, F->seg, F->wdist};
     for (void* p : ps) cudaFree(p);
     cudaFreeHost(F->scal_host);
     delete F;
@@ -655,7 +775,7 @@ cudaError_t pcg(const Fem& F, const double* A, const double* diag, const double*
 }  // namespace
 
 cudaError_t node_fields_solve(Fem& F, const double* stats, const lpdf_params& P, float* out, double tol,
-                              int maxit, int* iters, cudaStream_t st)
+                              int maxit, int* iters, cudaStream_t st, const float* surr, const float* surr_norm)
 {
     const int ns = P.ns;
     const size_t n = F.ndof;
@@ -690,7 +810,7 @@ cudaError_t node_fields_solve(Fem& F, const double* stats, const lpdf_params& P,
         elem_div_kernel<<<ge, 256, 0, st>>>(F, gU + 2 * i, 6, ew);
         recover_kernel<<<gd, 256, 0, st>>>(F, ew, 1, lapU + i, 3);
     }
-    if (P.gmodel == 0) {
+    if (P.gmodel == 0 && !surr) {
         elem_L2_kernel<<<ge, 256, 0, st>>>(F, k, eps, P.CL, P.Ceta, P.nu, ew);
         assemble_kernel<<<gd, 256, 0, st>>>(F, ew, F.Aval, diag);
         const bool warm = P.cg_warm_start && F.has_wp;
@@ -733,7 +853,25 @@ cudaError_t node_fields_solve(Fem& F, const double* stats, const lpdf_params& P,
         fill_kernel<<<blocks(2 * (int64_t)n), 256, 0, st>>>(2 * (int)n, 0.0, gp);
     }
     fields_kernel<<<blocks(F.N), 256, 0, st>>>(F, ns, nfp, U, R, om, phi, k, eps, gU, lapU, gp, wp, P.gmodel, P.C0,
-                                               P.Comega1, P.Comega2, P.dpdx0, P.dpdy0, out);
+                                               P.Comega1, P.Comega2, P.dpdx0, P.dpdy0, surr, surr_norm, out);
+    return cudaGetLastError();
+}
+
+cudaError_t surrogate_features(Fem& F, const double* stats, int ns, const float* fields, double C0, float* feat,
+                               float* tgt, cudaStream_t st)
+{
+    if (!F.has_wdist) {
+        wall_distance_kernel<<<blocks(F.N), 256, 0, st>>>(F.N, F.xy, F.seg, F.nseg, F.period, F.wdist);
+        F.has_wdist = true;
+    }
+    features_kernel<<<blocks(F.N), 256, 0, st>>>(F, stats, nquant(ns), fields, nfields_padded(ns), C0, feat,
+                                                 fields ? tgt : nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t fields_compare(const float* a, const float* b, int n_nodes, int nfp, double* out2, cudaStream_t st)
+{
+    fields_compare_kernel<<<1, 1024, 0, st>>>(a, b, n_nodes, nfp, out2);
     return cudaGetLastError();
 }
 

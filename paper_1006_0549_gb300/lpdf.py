@@ -35,7 +35,14 @@ EXPORTS = ("lpdf_params_default", "lpdf_last_error", "lpdf_version", "lpdf_mesh_
            "lpdf_mesh_info", "lpdf_mesh_neighbors", "lpdf_mesh_masters", "lpdf_ctx_create", "lpdf_ctx_free",
            "lpdf_ctx_set_params", "lpdf_ctx_size", "lpdf_particles_init", "lpdf_set_state", "lpdf_get_state",
            "lpdf_pdf_step", "lpdf_status", "lpdf_grid_statistics", "lpdf_pdf_step_static", "lpdf_sort",
-           "lpdf_elliptic_relax_solve", "lpdf_ctx_set_timing", "lpdf_ctx_timings", "lpdf_tc_gemm_bf16")
+           "lpdf_elliptic_relax_solve", "lpdf_ctx_set_timing", "lpdf_ctx_timings", "lpdf_tc_gemm_bf16",
+           "lpdf_mlp_create", "lpdf_mlp_free", "lpdf_mlp_set_params", "lpdf_mlp_get_params", "lpdf_mlp_fit_norm",
+           "lpdf_mlp_forward", "lpdf_mlp_gradient", "lpdf_mlp_train", "lpdf_surrogate_features",
+           "lpdf_mlp_set_policy", "lpdf_surrogate_relax_solve")
+
+MLP_IN, MLP_OUT, MLP_HIDDEN = 8, 7, 128
+MLP_NPARAMS = 35079
+MLP_NNORM = 37
 
 
 class LpdfError(RuntimeError):
@@ -97,10 +104,23 @@ def lib():
     L.lpdf_ctx_set_timing.argtypes = [vp, ctypes.c_int]
     L.lpdf_ctx_timings.argtypes = [vp, vp, vp]
     L.lpdf_elliptic_relax_solve.argtypes = [vp, vp, vp, vp, ctypes.c_double, i32, vp, vp]
+    L.lpdf_mlp_create.argtypes = [i64, vp]
+    L.lpdf_mlp_free.argtypes = [vp]
+    L.lpdf_mlp_free.restype = None
+    L.lpdf_mlp_set_params.argtypes = [vp, vp, vp]
+    L.lpdf_mlp_get_params.argtypes = [vp, vp, vp]
+    L.lpdf_mlp_fit_norm.argtypes = [vp, vp, vp, i64, vp]
+    L.lpdf_mlp_forward.argtypes = [vp, vp, i64, vp, vp]
+    L.lpdf_mlp_gradient.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+    L.lpdf_mlp_train.argtypes = [vp, vp, vp, i64, i64, i32, ctypes.c_float, vp, vp]
+    L.lpdf_surrogate_features.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.lpdf_mlp_set_policy.argtypes = [vp, i32, ctypes.c_double]
+    L.lpdf_surrogate_relax_solve.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, i32, vp, vp]
     for name in EXPORTS:
         f = getattr(L, name)
         if f.restype is ctypes.c_int or (name not in ("lpdf_params_default", "lpdf_mesh_free", "lpdf_ctx_free",
-                                                      "lpdf_last_error", "lpdf_version", "lpdf_ctx_size")):
+                                                      "lpdf_last_error", "lpdf_version", "lpdf_ctx_size",
+                                                      "lpdf_mlp_free")):
             f.restype = ctypes.c_int
     _lib = L
     return L
@@ -183,6 +203,22 @@ class Mesh:
         _check(lib().lpdf_elliptic_relax_solve(self.h, ctypes.byref(params), _ptr(stats), _ptr(out), float(tol),
                                                int(maxit), _ptr(it), _stream(stream)))
         return int(it[0]), int(it[1])
+
+    def surrogate_features(self, params: Params, stats, feat, fields=None, tgt=None, stream=None):
+        """lpdf_surrogate_features: per-node network inputs (feat, n_nodes x 8 float32, CUDA) and,
+        with fields given, the targets taken from them (tgt, n_nodes x 7 float32, CUDA)."""
+        _check(lib().lpdf_surrogate_features(self.h, ctypes.byref(params), _ptr(stats), _ptr(fields), _ptr(feat),
+                                             _ptr(tgt), _stream(stream)))
+        return feat, tgt
+
+    def surrogate_relax_solve(self, net: "MLP", params: Params, stats, out, tol: float = 1e-10, maxit: int = 20000,
+                              stream=None):
+        """lpdf_surrogate_relax_solve: node fields with G_ij and C0 eps from the network, checked
+        against the plain solve at the network's cadence. Returns (checked, error, used_plain, calls)."""
+        info = np.zeros(4, dtype=np.float64)
+        _check(lib().lpdf_surrogate_relax_solve(self.h, net.h, ctypes.byref(params), _ptr(stats), _ptr(out),
+                                                float(tol), int(maxit), _ptr(info), _stream(stream)))
+        return bool(info[0]), float(info[1]), bool(info[2]), int(info[3])
 
     def __del__(self):
         try:
@@ -310,6 +346,64 @@ def tc_gemm_bf16(A, B, D, stream=None):
     N = B.shape[0]
     _check(lib().lpdf_tc_gemm_bf16(_ptr(A), _ptr(B), _ptr(D), int(M), int(N), int(K), _stream(stream)))
     return D
+
+
+class MLP:
+    """lpdf_mlp: the learned surrogate network (8 -> 128 -> 128 -> 128 -> 7, BF16 tensor cores)."""
+
+    def __init__(self, max_batch: int):
+        h = ctypes.c_void_p()
+        _check(lib().lpdf_mlp_create(int(max_batch), ctypes.byref(h)))
+        self.h = h
+        self.max_batch = int(max_batch)
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                lib().lpdf_mlp_free(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def set_params(self, params, norm=None):
+        """params: MLP_NPARAMS float32 (host); norm: MLP_NNORM float32 (host) or None."""
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        n = None if norm is None else np.ascontiguousarray(norm, dtype=np.float32)
+        if p.size != MLP_NPARAMS or (n is not None and n.size != MLP_NNORM):
+            raise ValueError("parameter or standardisation block of the wrong size")
+        _check(lib().lpdf_mlp_set_params(self.h, _ptr(p), _ptr(n)))
+
+    def get_params(self):
+        p = np.zeros(MLP_NPARAMS, dtype=np.float32)
+        n = np.zeros(MLP_NNORM, dtype=np.float32)
+        _check(lib().lpdf_mlp_get_params(self.h, _ptr(p), _ptr(n)))
+        return p, n
+
+    def fit_norm(self, feat, tgt, stream=None):
+        _check(lib().lpdf_mlp_fit_norm(self.h, _ptr(feat), _ptr(tgt), int(feat.shape[0]), _stream(stream)))
+
+    def forward(self, feat, out, stream=None):
+        """out (B x 7 float32, CUDA) = the network on feat (B x 8 float32, CUDA), in target units."""
+        _check(lib().lpdf_mlp_forward(self.h, _ptr(feat), int(feat.shape[0]), _ptr(out), _stream(stream)))
+        return out
+
+    def gradient(self, feat, tgt, stream=None):
+        """(gradient (MLP_NPARAMS float32, host), loss) on the batch (feat, tgt)."""
+        g = np.zeros(MLP_NPARAMS, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(lib().lpdf_mlp_gradient(self.h, _ptr(feat), _ptr(tgt), int(feat.shape[0]), _ptr(g),
+                                       ctypes.byref(loss), _stream(stream)))
+        return g, loss.value
+
+    def train(self, feat, tgt, batch: int, steps: int, lr: float, stream=None):
+        """Adam steps on minibatches; returns the minibatch losses (before each step)."""
+        losses = np.zeros(max(int(steps), 1), dtype=np.float64)
+        _check(lib().lpdf_mlp_train(self.h, _ptr(feat), _ptr(tgt), int(feat.shape[0]), int(batch), int(steps),
+                                    float(lr), _ptr(losses), _stream(stream)))
+        return losses[:int(steps)]
+
+    def set_policy(self, check_every: int = 50, threshold: float = 0.02):
+        _check(lib().lpdf_mlp_set_policy(self.h, int(check_every), float(threshold)))
 
 
 def version() -> str:
