@@ -34,9 +34,9 @@ UNIT = "particle-updates/s"
 # algorithmic bytes of one particle update (ns = 1): read x, y, u, v, w, omega, psi, elem, pid
 # (36 B) and write x, y, u, v, w, omega, psi, elem (32 B)
 BYTES_PER_UPDATE = 68
-# kernels of one lpdf_pdf_step: advance, histogram, 3 scan kernels, record scatter, record offsets,
-# particle scatter, moments
-LAUNCHES_PER_STEP = 9
+# kernels of one lpdf_pdf_step: element-field table, advance, histogram, 3 scan kernels, record
+# scatter, record offsets, particle scatter, moments
+LAUNCHES_PER_STEP = 10
 
 
 def _env_int(k, d):
@@ -255,6 +255,70 @@ def run_gpu(args, rank, world, dist):
                 h2d=int(h_fields.numel() * 4), d2h=int(h_stats.numel() * 8), wk=wk, solve=solve)
 
 
+def run_surrogate(wk, train_steps: int, run_steps: int, check_every: int, threshold: float):
+    """The learned surrogate of the gridpoint solve beside the plain solve, in the coupled time loop
+    of the same workload: train on the fields of `train_steps` plain steps (on the GPU, with the
+    library's forward and backward kernels), then continue from one state for `run_steps` steps with
+    the plain solve, with the plain solve under another random seed (the ensemble's statistical
+    spread) and with the surrogate; report the solve times and the differences in the Reynolds
+    stresses and the scalar variance."""
+    import torch
+    from paper_1006_0549_gb300 import lpdf, timeloop as tl
+    params = lpdf.params_for(wk, gmodel=0, pressure_solve=0, dpdx0=-1.0)
+    loop = tl.TimeLoop(wk, params)
+    t = time.perf_counter()
+    feat, tgt = tl.collect_training_data(loop, train_steps)
+    torch.cuda.synchronize()
+    collect_s = time.perf_counter() - t
+    t = time.perf_counter()
+    net, losses = tl.train_surrogate(feat, tgt)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t
+    net.set_policy(check_every, threshold)
+    snap = loop.snapshot()
+
+    def run(p, use_net):
+        loop.restore(snap, p)
+        times, errs, used = [], [], 0
+        for _ in range(run_steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            if use_net:
+                checked, err, used_plain, _ = loop.solve_surrogate(net)
+                if checked:
+                    errs.append(err)
+                used += 0 if used_plain else 1
+            else:
+                loop.solve_plain()
+            e1.record()
+            torch.cuda.synchronize()
+            if not use_net or not used_plain:
+                times.append(e0.elapsed_time(e1))
+            loop.advance()
+        loop.ctx.status()
+        return loop.S.cpu().numpy(), (float(np.median(times)) if times else None), errs, used
+
+    plain, t_plain, _, _ = run(params, False)
+    other = lpdf.params_for(wk, gmodel=0, pressure_solve=0, dpdx0=-1.0)
+    other.seed = params.seed + 12345
+    spread, _, _, _ = run(other, False)
+    surr, t_surr, errs, used = run(params, True)
+    R, PHI = [4, 5, 6, 7, 8, 9], [11 + wk.ns + a for a in range(wk.ns)]
+    return {"workload": f"{wk.name}, coupled loop (elliptic relaxation, fixed mean pressure gradient)",
+            "train_steps": train_steps, "train_rows": int(feat.shape[0]), "adam_steps": int(len(losses)),
+            "final_loss": float(np.mean(losses[-200:])), "collect_s": collect_s, "train_s": train_s,
+            "run_steps": run_steps, "check_every": check_every, "threshold": threshold,
+            "check_errors": errs, "network_used_on": used,
+            "plain_solve_ms": t_plain, "surrogate_solve_ms": t_surr,
+            "speedup": (t_plain / t_surr) if t_surr else None,
+            "reynolds_stress_rel_diff": {"surrogate_vs_plain": tl.relative_difference(surr, plain, R),
+                                         "other_seed_vs_plain": tl.relative_difference(spread, plain, R)},
+            "scalar_variance_rel_diff": {"surrogate_vs_plain": tl.relative_difference(surr, plain, PHI),
+                                         "other_seed_vs_plain": tl.relative_difference(spread, plain, PHI)},
+            "note": "errors: Frobenius norms over all nodes after run_steps; solve times: CUDA events, median "
+                    "over the calls that ran the plain solve alone / the network alone"}
+
+
 def cpu_baseline_sample(wk, n_sample: int):
     """FP64 oracle (single-threaded C) on the first n_sample particles of a fresh initialisation
     of the same workload: one step plus the gridpoint moments."""
@@ -283,6 +347,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=4_000_000)
+    ap.add_argument("--surrogate-train-steps", type=int, default=100,
+                    help="plain steps whose fields train the surrogate (0: no surrogate report)")
+    ap.add_argument("--surrogate-run-steps", type=int, default=40)
     ap.add_argument("--ppe", type=int, default=500,
                     help="particles per element (500 = the 25M-particle workload; smaller only for profiling)")
     args = ap.parse_args()
@@ -353,6 +420,9 @@ def main():
     step_gbs = BYTES_PER_UPDATE * P / (ms_step * 1e-3) / 1e9
     traffic = ncu_traffic(P)
     cpu_n, cpu_dt = cpu_baseline_sample(r["wk"], args.cpu_sample)
+    surrogate = None
+    if args.surrogate_train_steps > 0:
+        surrogate = run_surrogate(r["wk"], args.surrogate_train_steps, args.surrogate_run_steps, 10, 0.02)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -375,6 +445,7 @@ def main():
                         "the particle state stays resident in HBM"},
         "gpu_launches": K * LAUNCHES_PER_STEP,
         "gridpoint_solve": r["solve"],
+        "surrogate": surrogate,
     }
     print(json.dumps(line))
     if dist is not None:

@@ -280,9 +280,10 @@ int lpdf_tc_gemm_bf16(const void* A, const void* B, float* D, int32_t M, int32_t
  * layer l computes z = W a + b.
  * Standardisation block (LPDF_MLP_NNORM floats): feature means [8], feature deviations [8],
  * loss weights [7], target means [7], target deviations [7].
- * Inputs (per gridpoint): wall distance, ln k, ln <omega>, b11, b22, b33, b12 and II_b = b_ij b_ij,
- * b_ij = <u_i u_j> / (2 k) - delta_ij / 3 (b = 0 where k <= 1e-12; the logarithms of
- * max(., 1e-12)).
+ * Inputs (per gridpoint): wall distance, ln k, ln <omega>, b11, b22, b12, II_b = b_ij b_ij and
+ * ln(eps_w / eps), with b_ij = <u_i u_j> / (2 k) - delta_ij / 3 (b = 0 where k <= 1e-12), eps =
+ * k <omega> and eps_w its value at the nearest wall point (linear along the wall edge; 0 input
+ * without walls); the logarithms take max(., 1e-12).
  * Targets: G11, G12, G21, G22, G33 divided by <omega>, C0 eps / (k <omega>), and the relaxed trace
  * wp_ii = k G_ii + 3 eps / 2 over its local value -9/4 C0 eps (1 where eps <= 1e-12; this last
  * output is a diagnostic of the wall effect and is not used by the step); <omega> and k below

@@ -7,8 +7,11 @@ no learned part. What is stated here is the definition of the network that stand
 solve and of its training:
 
 * inputs per gridpoint: wall distance, ln k, ln <omega>, the anisotropy b_ij = <u_i u_j>/(2k) -
-  delta_ij/3 (b11, b22, b33, b12) and its second invariant II_b = b_ij b_ij, with k =
-  <u_i u_i>/2 (the paragraph before Eq. 5);
+  delta_ij/3 (b11, b22, b12; b33 = -b11 - b22 is implied) and its second invariant II_b =
+  b_ij b_ij, with k = <u_i u_i>/2 (the paragraph before Eq. 5), and the wall effect
+  ln(eps_w / eps): eps = k <omega> (the paragraph before Eq. 5), eps_w its value at the nearest
+  wall point, interpolated linearly along that wall edge (the wall enters the relaxation only
+  through its boundary values, which scale with the wall's eps);
 * targets: G11, G12, G21, G22, G33 over <omega>, C0 eps/(k <omega>) and the relaxed trace
   wp_ii = k G_ii + 3 eps/2 over its local value -9/4 C0 eps (eps = k <omega>);
 * network 8 -> 128 -> 128 -> 128 -> 7, tanh on the hidden layers, standardised inputs and
@@ -159,26 +162,37 @@ def adam(p, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 
 # ------------------------------------------------------------------ inputs and targets per node
 
+def wall_edges(mesh):
+    """(n, 2) end nodes of the wall edges (tags 1, 2), in element order."""
+    return np.array([(mesh.tri[e, k], mesh.tri[e, (k + 1) % 3]) for e in range(mesh.tri.shape[0])
+                     for k in range(3) if mesh.edge_tag[e, k] in (1, 2)], dtype=np.int64).reshape(-1, 2)
+
+
+def nearest_wall_point(mesh):
+    """Per node: distance to the nearest wall point, its wall edge and its position t on the edge
+    (0 at the first end node). Edges in element order, each tried at x - period, x, x + period; the
+    first strictly nearest point wins."""
+    xy = np.asarray(mesh.node_xy, dtype=np.float64)
+    edges = wall_edges(mesh)
+    n = xy.shape[0]
+    best, bs, bt = np.full(n, np.inf), np.zeros(n, dtype=np.int64), np.zeros(n)
+    shifts = [0.0] if not mesh.period_x > 0 else [-mesh.period_x, 0.0, mesh.period_x]
+    for i, (a, b) in enumerate(edges):
+        t = xy[b] - xy[a]
+        for sx in shifts:
+            q = xy - xy[a] - np.array([sx, 0.0])
+            s = np.clip(q @ t / (t @ t), 0.0, 1.0)
+            d2 = (q[:, 0] - s * t[0]) ** 2 + (q[:, 1] - s * t[1]) ** 2
+            closer = d2 < best
+            best[closer], bs[closer], bt[closer] = d2[closer], i, s[closer]
+    if len(edges) == 0:
+        best[:] = 0.0
+    return np.sqrt(best), bs, bt
+
+
 def wall_distance(mesh):
     """Distance of every node to the nearest wall edge (tags 1, 2), periodic images included."""
-    xy = np.asarray(mesh.node_xy, dtype=np.float64)
-    segs = []
-    for e in range(mesh.tri.shape[0]):
-        for k in range(3):
-            if mesh.edge_tag[e, k] in (1, 2):
-                segs.append((xy[mesh.tri[e, k]], xy[mesh.tri[e, (k + 1) % 3]]))
-    if not segs:
-        return np.zeros(xy.shape[0])
-    shifts = [0.0] if not mesh.period_x > 0 else [-mesh.period_x, 0.0, mesh.period_x]
-    best = np.full(xy.shape[0], np.inf)
-    for a, b in segs:
-        t = b - a
-        for sx in shifts:
-            q = xy - a - np.array([sx, 0.0])
-            s = np.clip(q @ t / (t @ t), 0.0, 1.0)
-            d = np.hypot(q[:, 0] - s * t[0], q[:, 1] - s * t[1])
-            best = np.minimum(best, d)
-    return best
+    return nearest_wall_point(mesh)[0]
 
 
 def features(mesh, stats):
@@ -193,15 +207,20 @@ def features(mesh, stats):
     live = k > K_MIN
     b = np.zeros_like(R)
     b[live] = R[live] / (2.0 * k[live, None, None]) - np.eye(3) / 3.0
+    eps = k * om
+    dist, edge, t = nearest_wall_point(mesh)
     f = np.zeros((st.shape[0], IN))
-    f[:, 0] = wall_distance(mesh)
+    f[:, 0] = dist
     f[:, 1] = np.log(np.maximum(k, K_MIN))
     f[:, 2] = np.log(np.maximum(om, OM_MIN))
     f[:, 3] = b[:, 0, 0]
     f[:, 4] = b[:, 1, 1]
-    f[:, 5] = b[:, 2, 2]
-    f[:, 6] = b[:, 0, 1]
-    f[:, 7] = np.einsum("nij,nij->n", b, b)
+    f[:, 5] = b[:, 0, 1]
+    f[:, 6] = np.einsum("nij,nij->n", b, b)
+    edges = wall_edges(mesh)
+    if len(edges):
+        eps_w = (1.0 - t) * eps[edges[edge, 0]] + t * eps[edges[edge, 1]]
+        f[:, 7] = np.log(np.maximum(eps_w, EPS_MIN) / np.maximum(eps, EPS_MIN))
     return f
 
 

@@ -140,9 +140,12 @@ struct Fem {
     // wall distance of every geometric node (inputs of the learned surrogate)
     double* xy = nullptr;        // 2 per geometric node
     double* seg = nullptr;       // 4 per wall edge: (xa, ya, xb, yb)
+    int* segn = nullptr;         // 2 per wall edge: its geometric end nodes a, b
     int nseg = 0;
     double period = 0.0;         // x period (0: none)
-    double* wdist = nullptr;     // per geometric node, filled on first use
+    double* wdist = nullptr;     // per geometric node, filled on first use: distance to the wall,
+    int* wseg = nullptr;         //   the wall edge of the nearest wall point
+    double* wt = nullptr;        //   and its position on that edge (0 at a, 1 at b)
     bool has_wdist = false;
 };
 cudaError_t fem_build(const double* node_xy, int n_nodes, const int32_t* tri, int n_tri, const int32_t* tag,

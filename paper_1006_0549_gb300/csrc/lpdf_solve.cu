@@ -471,14 +471,18 @@ __global__ void fields_kernel(const Fem F, int ns, int nfp, const double* __rest
 }
 
 // ---------------------------------------------------------------- learned-surrogate inputs
-// distance of every geometric node to the nearest wall edge (and its images one period away)
+// nearest wall point of every geometric node: distance, wall edge and position on it (the edges
+// in order, each with its images one period to the left, in place and to the right; the first
+// strictly nearest point wins)
 __global__ void wall_distance_kernel(int N, const double* __restrict__ xy, const double* __restrict__ seg, int nseg,
-                                     double period, double* __restrict__ dist)
+                                     double period, double* __restrict__ dist, int* __restrict__ wseg,
+                                     double* __restrict__ wt)
 {
     const int nd = blockIdx.x * blockDim.x + threadIdx.x;
     if (nd >= N) return;
     const double px = xy[2 * nd], py = xy[2 * nd + 1];
-    double best = 1e300;
+    double best = 1e300, bt = 0.0;
+    int bs = 0;
     const int ni = period > 0.0 ? 1 : 0;
     for (int s = 0; s < nseg; ++s) {
         const double ax = seg[4 * s], ay = seg[4 * s + 1], tx = seg[4 * s + 2] - ax, ty = seg[4 * s + 3] - ay;
@@ -487,14 +491,22 @@ __global__ void wall_distance_kernel(int N, const double* __restrict__ xy, const
             const double qx = px - ax - im * period, qy = py - ay;
             const double t = fmin(1.0, fmax(0.0, (qx * tx + qy * ty) / tt));
             const double dx = qx - t * tx, dy = qy - t * ty;
-            best = fmin(best, dx * dx + dy * dy);
+            const double d2 = dx * dx + dy * dy;
+            if (d2 < best) {
+                best = d2;
+                bs = s;
+                bt = t;
+            }
         }
     }
     dist[nd] = nseg > 0 ? sqrt(best) : 0.0;
+    wseg[nd] = bs;
+    wt[nd] = bt;
 }
 
-// inputs: wall distance, log k, log <omega>, b11, b22, b33, b12, II_b = b_ij b_ij with the
-// anisotropy b_ij = <u_i u_j> / (2 k) - delta_ij / 3; targets (from node fields): G11, G12, G21,
+// inputs: wall distance, log k, log <omega>, b11, b22, b12, II_b = b_ij b_ij with the anisotropy
+// b_ij = <u_i u_j> / (2 k) - delta_ij / 3, and log(eps_w / eps) with eps_w the dissipation
+// k <omega> interpolated linearly along the wall edge to the nearest wall point; targets (from node fields): G11, G12, G21,
 // G22, G33 over <omega>, C_0 epsilon / (k <omega>) and the relaxed trace wp_ii over its local value
 // -9/4 C_0 epsilon (wp_ii = k G_ii + 3 epsilon / 2)
 __global__ void features_kernel(const Fem F, const double* __restrict__ stats, int nq,
@@ -506,6 +518,15 @@ __global__ void features_kernel(const Fem F, const double* __restrict__ stats, i
     const double* st = stats + (size_t)F.dof_node[F.dof[nd]] * nq;
     const double uu = st[4], uv = st[5], uw = st[6], vv = st[7], vw = st[8], ww = st[9], Om = st[10];
     const double k = 0.5 * (uu + vv + ww);
+    double eps_w = 0.0;
+    if (F.nseg > 0) {
+        const int s = F.wseg[nd];
+        const double t = F.wt[nd];
+        const double* sa = stats + (size_t)F.dof_node[F.dof[F.segn[2 * s]]] * nq;
+        const double* sb = stats + (size_t)F.dof_node[F.dof[F.segn[2 * s + 1]]] * nq;
+        const double ea = 0.5 * (sa[4] + sa[7] + sa[9]) * sa[10], eb = 0.5 * (sb[4] + sb[7] + sb[9]) * sb[10];
+        eps_w = (1.0 - t) * ea + t * eb;
+    }
     double b11 = 0.0, b22 = 0.0, b33 = 0.0, b12 = 0.0, b13 = 0.0, b23 = 0.0;
     if (k > 1e-12) {
         const double ik = 0.5 / k;
@@ -522,9 +543,9 @@ __global__ void features_kernel(const Fem F, const double* __restrict__ stats, i
     f[2] = (float)log(fmax(Om, 1e-12));
     f[3] = (float)b11;
     f[4] = (float)b22;
-    f[5] = (float)b33;
-    f[6] = (float)b12;
-    f[7] = (float)(b11 * b11 + b22 * b22 + b33 * b33 + 2.0 * (b12 * b12 + b13 * b13 + b23 * b23));
+    f[5] = (float)b12;
+    f[6] = (float)(b11 * b11 + b22 * b22 + b33 * b33 + 2.0 * (b12 * b12 + b13 * b13 + b23 * b23));
+    f[7] = (float)(F.nseg > 0 ? log(fmax(eps_w, 1e-12) / fmax(k * Om, 1e-12)) : 0.0);
     if (!tgt) return;
     const float* o = fields + (size_t)nd * nfp;
     const double Omc = fmax(Om, 1e-12), kc = fmax(k, 1e-12), e = k * Om;
@@ -654,12 +675,14 @@ cudaError_t fem_build(const double* node_xy, int N, const int32_t* tri, int E, c
             }
         }
     std::vector<double> seg;
+    std::vector<int> segn;
     for (int e = 0; e < E; ++e)
         for (int k = 0; k < 3; ++k) {
             const int t = tag[3 * e + k];
             if (t != LPDF_EDGE_WALL && t != LPDF_EDGE_MOVING_WALL) continue;
             const int a = tri[3 * e + k], b = tri[3 * e + (k + 1) % 3];
             seg.insert(seg.end(), {node_xy[2 * a], node_xy[2 * a + 1], node_xy[2 * b], node_xy[2 * b + 1]});
+            segn.insert(segn.end(), {a, b});
         }
     const std::vector<double> xy(node_xy, node_xy + 2 * (size_t)N);
     for (int d = 0; d < ndof; ++d)
@@ -675,7 +698,10 @@ cudaError_t fem_build(const double* node_xy, int N, const int32_t* tri, int E, c
     F->N = N;
     F->nseg = (int)(seg.size() / 4);
     F->period = period;
-    if (seg.empty()) seg.assign(4, 0.0);
+    if (seg.empty()) {
+        seg.assign(4, 0.0);
+        segn.assign(2, 0);
+    }
     cudaError_t e = cudaSuccess;
     if ((e = upload(&F->dof, dof)) || (e = upload(&F->dof_node, dof_node)) || (e = upload(&F->edof, edof)) ||
         (e = upload(&F->area, area)) || (e = upload(&F->grad, grad)) || (e = upload(&F->de_ptr, de_ptr)) ||
@@ -683,7 +709,9 @@ cudaError_t fem_build(const double* node_xy, int N, const int32_t* tri, int E, c
         (e = upload(&F->col, col)) || (e = upload(&F->cptr, cptr)) || (e = upload(&F->cel, cel)) ||
         (e = upload(&F->Mval, Mval)) || (e = upload(&F->Kval, Kval)) || (e = upload(&F->wall, wall)) ||
         (e = upload(&F->normal, normal)) || (e = upload(&F->xy, xy)) || (e = upload(&F->seg, seg)) ||
-        (e = cudaMalloc((void**)&F->wdist, sizeof(double) * std::max(1, N))) ||
+        (e = upload(&F->segn, segn)) || (e = cudaMalloc((void**)&F->wdist, sizeof(double) * std::max(1, N))) ||
+        (e = cudaMalloc((void**)&F->wseg, sizeof(int) * std::max(1, N))) ||
+        (e = cudaMalloc((void**)&F->wt, sizeof(double) * std::max(1, N))) ||
         (e = cudaMalloc((void**)&F->Aval, sizeof(double) * std::max(1, F->nnz))) ||
         (e = cudaMalloc((void**)&F->work, sizeof(double) * (Fem::kWorkPerDof * (size_t)ndof + 16 * (size_t)E))) ||
         (e = cudaMalloc((void**)&F->part, sizeof(double) * 12 * Fem::kDotBlocks)) ||
@@ -701,7 +729,7 @@ void fem_free(Fem* F)
     if (!F) return;
     void* ps[] = {F->dof, F->dof_node, F->edof, F->area, F->grad, F->de_ptr, F->de_el, F->darea, F->row, F->col,
                   F->cptr, F->cel, F->Mval, F->Kval, F->Aval, F->wall, F->normal, F->work, F->part, F->scal,
-                  F->xy, F->seg, F->wdist};
+                  F->xy, F->seg, F->segn, F->wdist, F->wseg, F->wt};
     for (void* p : ps) cudaFree(p);
     cudaFreeHost(F->scal_host);
     delete F;
@@ -861,7 +889,8 @@ cudaError_t surrogate_features(Fem& F, const double* stats, int ns, const float*
                                float* tgt, cudaStream_t st)
 {
     if (!F.has_wdist) {
-        wall_distance_kernel<<<blocks(F.N), 256, 0, st>>>(F.N, F.xy, F.seg, F.nseg, F.period, F.wdist);
+        wall_distance_kernel<<<blocks(F.N), 256, 0, st>>>(F.N, F.xy, F.seg, F.nseg, F.period, F.wdist, F.wseg,
+                                                          F.wt);
         F.has_wdist = true;
     }
     features_kernel<<<blocks(F.N), 256, 0, st>>>(F, stats, nquant(ns), fields, nfields_padded(ns), C0, feat,

@@ -1,0 +1,106 @@
+"""The coupled time loop of the method through the C-ABI: particle step (lpdf_pdf_step), gridpoint
+statistics (lpdf_grid_statistics), gridpoint solve for the next step's node fields
+(lpdf_elliptic_relax_solve, or the learned surrogate through lpdf_surrogate_relax_solve).
+Introduction, items i-iii: statistics are extracted on the grid, Eulerian quantities are solved on
+it, and the particles are advanced with them. Orchestration only: every computation is a library call.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import lpdf
+from . import workloads as wl
+
+
+class TimeLoop:
+    """One ensemble on one mesh, with its statistics and node-field buffers on the device."""
+
+    def __init__(self, wk: wl.Workload, params: lpdf.Params, tol: float = 1e-8, maxit: int = 20000,
+                 init_seed: int = 5, capacity: int | None = None):
+        import torch
+        self.torch = torch
+        self.wk = wk
+        self.mesh = lpdf.Mesh(wk.mesh)
+        self.params = params
+        self.tol, self.maxit = tol, maxit
+        N = wk.mesh.n_nodes
+        self.N = N
+        self.nq = 11 + 2 * wk.ns
+        self.nfp = wl.n_fields_padded(wk.ns)
+        cap = capacity or wk.n_particles + 1024
+        self.ctx = lpdf.Context(self.mesh, params, cap)
+        self.ctx.particles_init(wk.n_per_elem, torch.from_numpy(wl.node_init_fields(wk.mesh)).cuda(), m_erlang=4)
+        self.S = torch.zeros((N, self.nq), dtype=torch.float64, device="cuda")
+        self.F = torch.from_numpy(wl.synthetic_node_fields(wk.mesh, wk.ns, seed=init_seed)).cuda()
+        self.step_no = 0
+        # the first step runs on seeded synthetic node fields; its statistics start the loop
+        self.advance()
+
+    def advance(self):
+        """One particle step with the current node fields, then the statistics of the new state."""
+        self.step_no += 1
+        self.ctx.pdf_step(self.F, self.step_no)
+        self.ctx.grid_statistics(self.S, raw=False)
+
+    def solve_plain(self):
+        return self.mesh.elliptic_relax_solve(self.params, self.S, self.F, self.tol, self.maxit)
+
+    def solve_surrogate(self, net: lpdf.MLP):
+        return self.mesh.surrogate_relax_solve(net, self.params, self.S, self.F, self.tol, self.maxit)
+
+    def features(self, with_targets: bool = True):
+        """Network inputs (and targets from the current node fields) of the current statistics."""
+        torch = self.torch
+        f = torch.empty((self.N, lpdf.MLP_IN), dtype=torch.float32, device="cuda")
+        t = torch.empty((self.N, lpdf.MLP_OUT), dtype=torch.float32, device="cuda") if with_targets else None
+        self.mesh.surrogate_features(self.params, self.S, f, self.F if with_targets else None, t)
+        return f, t
+
+    def snapshot(self):
+        return self.ctx.get_state(), self.S.clone(), self.F.clone(), self.step_no
+
+    def restore(self, snap, params: lpdf.Params | None = None):
+        st, S, F, n = snap
+        self.ctx.set_state(st)
+        self.S.copy_(S)
+        self.F.copy_(F)
+        self.step_no = n
+        if params is not None:
+            self.params = params
+            self.ctx.set_params(params)
+
+
+def collect_training_data(loop: TimeLoop, steps: int):
+    """`steps` plain steps; returns the network inputs and targets of every solve (device)."""
+    torch = loop.torch
+    feats, tgts = [], []
+    for _ in range(steps):
+        loop.solve_plain()
+        f, t = loop.features(True)
+        feats.append(f)
+        tgts.append(t)
+        loop.advance()
+    return torch.cat(feats), torch.cat(tgts)
+
+
+def train_surrogate(feat, tgt, seed: int = 7, batch: int = 1024,
+                    schedule=((1e-3, 4000), (3e-4, 3000), (1e-4, 3000))):
+    """A network trained on (feat, tgt) with Adam, in shuffled minibatches (a seeded permutation),
+    with a stepwise decaying learning rate. Returns (network, loss history)."""
+    import torch
+    B = feat.shape[0]
+    perm = torch.from_numpy(np.random.default_rng(seed).permutation(B)).to(feat.device)
+    feat, tgt = feat[perm].contiguous(), tgt[perm].contiguous()
+    net = lpdf.MLP(batch)
+    net.set_params(wl.mlp_init_params(seed))
+    net.fit_norm(feat, tgt)
+    n = B // batch * batch
+    hist = [net.train(feat[:n], tgt[:n], batch=batch, steps=k, lr=lr) for lr, k in schedule]
+    return net, np.concatenate(hist)
+
+
+def relative_difference(a, b, cols):
+    """|a - b| / |b| (Frobenius) over the given statistics columns."""
+    a = np.asarray(a)[:, cols]
+    b = np.asarray(b)[:, cols]
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))

@@ -143,15 +143,40 @@ def test_anisotropy_inputs_for_isotropic_and_one_component_stresses():
     st[:, 10] = 2.0
     f = om.features(mesh, st)
     assert np.allclose(f[:, 1], np.log(0.45)) and np.allclose(f[:, 2], np.log(2.0))
-    assert np.allclose(f[:, 3:8], 0.0, atol=1e-15)
+    assert np.allclose(f[:, 3:8], 0.0, atol=1e-15)   # uniform eps: the wall ratio is 1 too
     st[:, 4], st[:, 7], st[:, 9] = 0.8, 0.0, 0.0  # one component: b = diag(2/3, -1/3, -1/3)
     f = om.features(mesh, st)
-    assert np.allclose(f[:, 3:6], [2 / 3, -1 / 3, -1 / 3]) and np.allclose(f[:, 7], 2.0 / 3.0)
+    assert np.allclose(f[:, 3:6], [2 / 3, -1 / 3, 0.0]) and np.allclose(f[:, 6], 2.0 / 3.0)
     st[:, 4], st[:, 5], st[:, 7] = 0.4, 0.4, 0.4  # two-component, fully correlated shear
     f = om.features(mesh, st)
-    assert np.allclose(f[:, 3:7], [1 / 6, 1 / 6, -1 / 3, 1 / 2])
-    assert np.allclose(f[:, 7], 1 / 36 + 1 / 36 + 1 / 9 + 2 * 1 / 4)
-    assert np.allclose(f[:, 3] + f[:, 4] + f[:, 5], 0.0)
+    # b = [[1/6, 1/2, 0], [1/2, 1/6, 0], [0, 0, -1/3]]
+    assert np.allclose(f[:, 3:6], [1 / 6, 1 / 6, 1 / 2])
+    assert np.allclose(f[:, 6], 1 / 36 + 1 / 36 + 1 / 9 + 2 * 1 / 4)
+
+
+def test_wall_dissipation_input_follows_the_nearest_wall_point():
+    # channel: eps = k <omega> varies with y only, so the nearest wall point of a node at height
+    # y < 1 lies on the bottom wall (y = 0) and the input is ln(eps(0) / eps(y))
+    mesh = wl.channel_mesh(12, 9, 4)
+    y = mesh.node_xy[:, 1]
+    st = np.zeros((mesh.n_nodes, 13))
+    st[:, 4] = st[:, 7] = st[:, 9] = 2.0 / 3.0            # k = 1
+    st[:, 10] = 1.0 + 3.0 * np.abs(y - 1.0)                 # eps = 4 at both walls, 1 at the centre
+    f = om.features(mesh, st)
+    assert np.allclose(f[:, 7], np.log(4.0 / st[:, 10]), atol=1e-12)
+    # on the wall itself the input is 0
+    assert np.allclose(f[(y == 0.0) | (y == 2.0), 7], 0.0)
+    # cavity: linear eps along the bottom wall, interpolated to the foot of the perpendicular
+    cav = wl.cavity_mesh(8, 8, 5)
+    x, y = cav.node_xy[:, 0], cav.node_xy[:, 1]
+    st = np.zeros((cav.n_nodes, 13))
+    st[:, 4] = st[:, 7] = st[:, 9] = 2.0 / 3.0
+    st[:, 10] = 1.0 + x                                      # eps = 1 + x everywhere
+    f = om.features(cav, st)
+    near_bottom = (y < x) & (y < 1 - x) & (y < 1 - y)
+    assert np.allclose(f[near_bottom, 7], 0.0, atol=1e-12)   # foot of the perpendicular at the same x
+    near_left = (x < y) & (x < 1 - y) & (x < 1 - x)
+    assert np.allclose(f[near_left, 7], np.log(1.0 / (1.0 + x[near_left])), atol=1e-12)
 
 
 def test_targets_of_the_simplified_langevin_model():
