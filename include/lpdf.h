@@ -122,6 +122,27 @@ int lpdf_mesh_neighbors(const lpdf_mesh* mesh, int32_t* out);
 int lpdf_mesh_masters(const lpdf_mesh* mesh, int32_t* out);
 
 /* ---------------------------------------------------------------------------------------
+ * lpdf_mesh_load_multi -- n_comp independent meshes held as one (their disjoint union), so that
+ * many ensembles of uneven size advance in the same kernel launches (the paper has no
+ * counterpart: a batching choice of this library). sync.
+ *   node_xy, tri, edge_tag, n_nodes, n_tri  as for lpdf_mesh_load, over all components; tri
+ *            holds global node ids.
+ *   node_off, tri_off  host, n_comp + 1 each: component c owns nodes [node_off[c],
+ *            node_off[c + 1]) and elements [tri_off[c], tri_off[c + 1]) (node_off[0] = tri_off[0]
+ *            = 0, node_off[n_comp] = n_nodes, tri_off[n_comp] = n_tri); an element may only use
+ *            nodes of its own component.
+ *   period_x  as for lpdf_mesh_load, shared by every component (> 0: all components are
+ *            periodic in x with this period).
+ * Each component has its own bounding box as its half-open domain, pairs its periodic edges and
+ * nodes within itself and never exchanges particles with another. Node fields and statistics
+ * are per node of the union; lpdf_pdf_step_static rejects these meshes.
+ * Errors: as lpdf_mesh_load; LPDF_ERR_ARG for offsets that do not cover the mesh.
+ * ------------------------------------------------------------------------------------- */
+int lpdf_mesh_load_multi(const double* node_xy, int32_t n_nodes, const int32_t* tri, int32_t n_tri,
+                         const int32_t* edge_tag, int32_t n_comp, const int32_t* node_off, const int32_t* tri_off,
+                         double period_x, lpdf_mesh** out);
+
+/* ---------------------------------------------------------------------------------------
  * lpdf_ctx_create -- particle ensemble on one mesh with room for `capacity` particles
  * (device SoA state x, y, u, v, w, omega, psi[ns], elem, pid, plus the moment accumulators).
  * params->ns must be in 1..LPDF_MAX_SCALARS. sync. The mesh must outlive the context.
@@ -132,6 +153,17 @@ void lpdf_ctx_free(lpdf_ctx* ctx);
 int lpdf_ctx_set_params(lpdf_ctx* ctx, const lpdf_params* params);
 int64_t lpdf_ctx_size(const lpdf_ctx* ctx);
 
+/* Per-component Philox key and scalar sources of a multi-component mesh (default: every
+ * component takes params->seed and params' sources). */
+typedef struct {
+    uint64_t seed;
+    int32_t n_sources;
+    float src_x[LPDF_MAX_SOURCES], src_y[LPDF_MAX_SOURCES], src_r[LPDF_MAX_SOURCES];
+    int32_t src_alpha[LPDF_MAX_SOURCES];
+} lpdf_component;
+/* sync. comps host, n = the mesh's component count. Errors: LPDF_ERR_ARG. */
+int lpdf_ctx_set_components(lpdf_ctx* ctx, const lpdf_component* comps, int32_t n);
+
 /* ---------------------------------------------------------------------------------------
  * lpdf_particles_init -- n_per_elem particles per element, pid = e*n_per_elem + j: position
  * uniform in the element, then located exactly; U = <U>(X) + sigma(X) z; omega Erlang(m_erlang)
@@ -140,6 +172,12 @@ int64_t lpdf_ctx_size(const lpdf_ctx* ctx);
  * Random numbers: Philox4x32-10 counter (pid, 0, 0, 1<<16 | block), key = seed. async.
  * Errors: LPDF_ERR_ARG (capacity too small, m_erlang outside 1..6).
  * ------------------------------------------------------------------------------------- */
+/* lpdf_particles_init_multi -- as lpdf_particles_init with n_per_elem[c] (host, one per
+ * component) particles per element of component c. The components' particles follow one another
+ * in component order, pids count from 0 within each component, and each component draws with
+ * its own seed, so component c starts exactly as a single-mesh context of that component would. */
+int lpdf_particles_init_multi(lpdf_ctx* ctx, const int32_t* n_per_elem, const float* node_init, int32_t m_erlang,
+                              void* stream);
 int lpdf_particles_init(lpdf_ctx* ctx, int32_t n_per_elem, const float* node_init, int32_t m_erlang,
                         void* stream);
 
@@ -172,6 +210,35 @@ int lpdf_get_state(const lpdf_ctx* ctx, float* x, float* y, float* u, float* v, 
  * call itself only reports argument and launch errors.
  * ------------------------------------------------------------------------------------- */
 int lpdf_pdf_step(lpdf_ctx* ctx, const float* node_fields, uint64_t step, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * lpdf_pdf_steps -- nsteps consecutive steps step0, step0 + 1, ... with the same node fields,
+ * bit-identical to nsteps lpdf_pdf_step calls. async. Pairs of steps replay a CUDA graph of two
+ * whole steps (captured on first use for these fields and this buffer; the step number is read
+ * from device memory, so replays need no host work); an odd last step runs as lpdf_pdf_step.
+ * lpdf_ctx_set_timing does not record graph-replayed steps. Changing the state, the order, the
+ * parameters, the components or the launch configuration drops the graphs.
+ * ------------------------------------------------------------------------------------- */
+int lpdf_pdf_steps(lpdf_ctx* ctx, const float* node_fields, uint64_t step0, int32_t nsteps, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Launch configuration of the step's kernels. Every configuration gives bit-identical results.
+ *   adv (advance kernel): 0 = 256 threads per CTA, >= 4 CTAs per SM (64 registers);
+ *       1 = 256, >= 6 (40 registers); 2 = 128, >= 8; 3 = 256, >= 4 on a persistent grid
+ *       (CTAs stride over 256-particle tiles); 4 = 256, >= 6, persistent.
+ *   mom (moments kernel, a warp per element): 0 = 256 threads, >= 2 CTAs per SM; 1 = 128, >= 4;
+ *       2 = 512, >= 1; 3 = 256, >= 3.
+ * lpdf_ctx_set_tune sets it (LPDF_ERR_ARG outside those ranges). lpdf_ctx_autotune times every
+ * advance variant, then every moments variant with the best advance variant, each for one
+ * warm-up step and steps_per_trial timed steps (CUDA events on `stream`) of this context's own
+ * ensemble and fields, and keeps the fastest. The trial steps are real steps, numbered from
+ * step0: *steps_used (host, may be NULL) tells how many were taken. choice (host, 2 ints, may
+ * be NULL) = (adv, mom); trial_ms (host, 9 doubles, may be NULL) = milliseconds per step of
+ * each trial (5 advance, then 4 moments variants). sync.
+ * ------------------------------------------------------------------------------------- */
+int lpdf_ctx_set_tune(lpdf_ctx* ctx, int32_t adv, int32_t mom);
+int lpdf_ctx_autotune(lpdf_ctx* ctx, const float* node_fields, uint64_t step0, int32_t steps_per_trial,
+                      int32_t* choice, double* trial_ms, int32_t* steps_used, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * lpdf_sort -- physically re-buckets the ensemble by element: afterwards the particles of every

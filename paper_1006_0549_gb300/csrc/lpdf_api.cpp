@@ -46,6 +46,33 @@ cudaError_t dalloc(T** p, size_t n)
 
 bool is_f32(double v) { return (double)(float)v == v; }
 
+CompParams comp_params(uint64_t seed, int n_src, const float* sx, const float* sy, const float* sr, const int32_t* sa)
+{
+    CompParams c{};
+    c.key0 = (uint32_t)seed;
+    c.key1 = (uint32_t)(seed >> 32);
+    c.n_src = n_src;
+    for (int i = 0; i < n_src; ++i) {
+        c.src_x[i] = sx[i];
+        c.src_y[i] = sy[i];
+        c.src_r[i] = sr[i];
+        c.src_alpha[i] = sa[i];
+    }
+    return c;
+}
+
+// drops the captured step graphs (the state, its order or the configuration changed)
+void drop_graphs(lpdf_ctx* c)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+        c->graph[k] = nullptr;
+        c->graph_fields[k] = nullptr;
+        c->graph_state[k] = nullptr;
+        c->graph_perm[k] = nullptr;
+    }
+}
+
 cudaError_t alloc_pipe(PipeScratch& w, int64_t cap, size_t E, int ns)
 {
     const size_t nrec = (size_t)((cap + 255) / 256) * 256;
@@ -62,7 +89,7 @@ cudaError_t alloc_pipe(PipeScratch& w, int64_t cap, size_t E, int ns)
 void free_mesh_device(DevMesh& d)
 {
     cudaFree(d.ex); cudaFree(d.ey); cudaFree(d.en); cudaFree(d.ev); cudaFree(d.em); cudaFree(d.master);
-    cudaFree(d.ea); cudaFree(d.eb);
+    cudaFree(d.ea); cudaFree(d.eb); cudaFree(d.ecomp); cudaFree(d.cframe);
     d = DevMesh();
 }
 
@@ -129,7 +156,7 @@ int lpdf::mesh_fem(const lpdf_mesh* mesh, Fem** out)
     if (!mesh->fem) {
         Fem* F = nullptr;
         cudaError_t e = fem_build(mesh->node_xy.data(), mesh->d.n_nodes, mesh->tri.data(), mesh->d.n_tri,
-                                  mesh->tag.data(), mesh->master, mesh->d.periodic ? mesh->box[1] - mesh->box[0] : 0.0, &F);
+                                  mesh->tag.data(), mesh->master, mesh->node_comp, mesh->period, &F);
         if (e != cudaSuccess) return fail(LPDF_ERR_CUDA, "gridpoint tables: %s", cudaGetErrorString(e));
         mesh->fem = F;
     }
@@ -162,27 +189,55 @@ void lpdf_params_default(lpdf_params* p)
 const char* lpdf_last_error(void) { return g_err.c_str(); }
 const char* lpdf_version(void) { return "lpdf 0.1 (sm_103a)"; }
 
-int lpdf_mesh_load(const double* node_xy, int32_t n_nodes, const int32_t* tri, int32_t n_tri,
-                   const int32_t* edge_tag, double period_x, lpdf_mesh** out)
+}  // extern "C"
+
+namespace {
+
+// The mesh tables of n_comp independent components (n_comp = 1: an ordinary mesh). Component c
+// owns nodes [node_off[c], node_off[c + 1]) and elements [tri_off[c], tri_off[c + 1]); its
+// frame is its own bounding box and its periodic edges and nodes pair within it.
+int build_mesh(const double* node_xy, int32_t n_nodes, const int32_t* tri, int32_t n_tri, const int32_t* edge_tag,
+               int32_t n_comp, const int32_t* node_off, const int32_t* tri_off, double period_x, lpdf_mesh** out)
 {
     if (!node_xy || !tri || !edge_tag || !out) return fail(LPDF_ERR_ARG, "mesh_load: NULL argument");
     if (n_nodes < 3 || n_tri < 1) return fail(LPDF_ERR_ARG, "mesh_load: n_nodes = %d, n_tri = %d", n_nodes, n_tri);
+    if (n_comp < 1 || node_off[0] != 0 || tri_off[0] != 0 || node_off[n_comp] != n_nodes || tri_off[n_comp] != n_tri)
+        return fail(LPDF_ERR_ARG, "mesh_load: component offsets do not cover the nodes and elements");
+    for (int c = 0; c < n_comp; ++c)
+        if (node_off[c + 1] - node_off[c] < 3 || tri_off[c + 1] <= tri_off[c])
+            return fail(LPDF_ERR_ARG, "mesh_load: component %d is empty", c);
     *out = nullptr;
-    double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
-    for (int i = 0; i < n_nodes; ++i) {
-        const double x = node_xy[2 * i], y = node_xy[2 * i + 1];
-        if (!is_f32(x) || !is_f32(y)) return fail(LPDF_ERR_ARG, "node %d coordinates are not FP32 values", i);
-        x0 = std::min(x0, x); x1 = std::max(x1, x); y0 = std::min(y0, y); y1 = std::max(y1, y);
-    }
     const bool periodic = period_x > 0.0;
-    if (periodic && (float)(x1 - x0) != (float)period_x)
-        return fail(LPDF_ERR_MESH, "period %.9g differs from the x extent %.9g", period_x, x1 - x0);
+    std::vector<double> fr(4 * (size_t)n_comp);   // per component x0, x1, y0, y1
+    std::vector<int32_t> ncomp(n_nodes), ecomp(n_tri);
+    for (int c = 0; c < n_comp; ++c) {
+        double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+        for (int i = node_off[c]; i < node_off[c + 1]; ++i) {
+            const double x = node_xy[2 * i], y = node_xy[2 * i + 1];
+            if (!is_f32(x) || !is_f32(y)) return fail(LPDF_ERR_ARG, "node %d coordinates are not FP32 values", i);
+            x0 = std::min(x0, x); x1 = std::max(x1, x); y0 = std::min(y0, y); y1 = std::max(y1, y);
+            ncomp[i] = c;
+        }
+        if (periodic && (float)(x1 - x0) != (float)period_x)
+            return fail(LPDF_ERR_MESH, "component %d: period %.9g differs from the x extent %.9g", c, period_x, x1 - x0);
+        fr[4 * c] = x0; fr[4 * c + 1] = x1; fr[4 * c + 2] = y0; fr[4 * c + 3] = y1;
+        for (int e = tri_off[c]; e < tri_off[c + 1]; ++e) ecomp[e] = c;
+    }
+    double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+    for (int c = 0; c < n_comp; ++c) {
+        x0 = std::min(x0, fr[4 * c]); x1 = std::max(x1, fr[4 * c + 1]);
+        y0 = std::min(y0, fr[4 * c + 2]); y1 = std::max(y1, fr[4 * c + 3]);
+    }
     std::vector<float> ex(4 * (size_t)n_tri), ey(4 * (size_t)n_tri), ea(4 * (size_t)n_tri), eb(4 * (size_t)n_tri);
     std::vector<int32_t> en(4 * (size_t)n_tri, -1), ev(4 * (size_t)n_tri, 0), em(4 * (size_t)n_tri, 0);
     for (int e = 0; e < n_tri; ++e) {
         const int* t = tri + 3 * e;
-        for (int k = 0; k < 3; ++k)
+        for (int k = 0; k < 3; ++k) {
             if (t[k] < 0 || t[k] >= n_nodes) return fail(LPDF_ERR_MESH, "element %d has node id %d", e, t[k]);
+            if (ncomp[t[k]] != ecomp[e])
+                return fail(LPDF_ERR_MESH, "element %d of component %d uses node %d of component %d", e, ecomp[e], t[k],
+                            ncomp[t[k]]);
+        }
         const double ax = node_xy[2 * t[0]], ay = node_xy[2 * t[0] + 1];
         const double bx = node_xy[2 * t[1]], by = node_xy[2 * t[1] + 1];
         const double cx = node_xy[2 * t[2]], cy = node_xy[2 * t[2] + 1];
@@ -233,25 +288,27 @@ int lpdf_mesh_load(const double* node_xy, int32_t n_nodes, const int32_t* tri, i
                 if (!periodic) return fail(LPDF_ERR_MESH, "periodic edge without period_x");
                 const double ax = node_xy[2 * a], bx = node_xy[2 * b];
                 const double ymin = std::min(node_xy[2 * a + 1], node_xy[2 * b + 1]);
-                if (ax == x0 && bx == x0) left_edges.push_back({ymin, (int64_t)e * 3 + k});
-                else if (ax == x1 && bx == x1) right_edges.push_back({ymin, (int64_t)e * 3 + k});
+                const double cx0 = fr[4 * ecomp[e]], cx1 = fr[4 * ecomp[e] + 1];
+                if (ax == cx0 && bx == cx0) left_edges.push_back({ymin, (int64_t)e * 3 + k});
+                else if (ax == cx1 && bx == cx1) right_edges.push_back({ymin, (int64_t)e * 3 + k});
                 else return fail(LPDF_ERR_MESH, "periodic edge of element %d is not on x0 or x1", e);
             }
         }
     if (periodic) {
         if (left_edges.size() != right_edges.size())
             return fail(LPDF_ERR_MESH, "%zu left vs %zu right periodic edges", left_edges.size(), right_edges.size());
-        std::map<std::pair<double, double>, int64_t> rmap;
+        // partners are found within the component, by the y values of their ends
+        std::map<std::tuple<int, double, double>, int64_t> rmap;
         for (auto& r : right_edges) {
             const int e = (int)(r.second / 3), k = (int)(r.second % 3);
             const int a = tri[3 * e + k], b = tri[3 * e + (k + 1) % 3];
-            rmap[{node_xy[2 * a + 1], node_xy[2 * b + 1]}] = r.second;
+            rmap[{ecomp[e], node_xy[2 * a + 1], node_xy[2 * b + 1]}] = r.second;
         }
         for (auto& l : left_edges) {
             const int e = (int)(l.second / 3), k = (int)(l.second % 3);
             const int a = tri[3 * e + k], b = tri[3 * e + (k + 1) % 3];
             // the partner runs the other way: its (a, b) y values are this edge's (b, a)
-            auto it = rmap.find({node_xy[2 * b + 1], node_xy[2 * a + 1]});
+            auto it = rmap.find({ecomp[e], node_xy[2 * b + 1], node_xy[2 * a + 1]});
             if (it == rmap.end()) return fail(LPDF_ERR_MESH, "left periodic edge of element %d has no partner", e);
             const int f = (int)(it->second / 3), kk = (int)(it->second % 3);
             en[4 * e + k] = f;
@@ -260,16 +317,16 @@ int lpdf_mesh_load(const double* node_xy, int32_t n_nodes, const int32_t* tri, i
             en[4 * f + 3] |= (1 << kk);
         }
     }
-    // periodic node pairing: node on x1 -> node on x0 with the same y
+    // periodic node pairing: node on x1 -> node on x0 of its component with the same y
     std::vector<int32_t> master(n_nodes);
     for (int i = 0; i < n_nodes; ++i) master[i] = i;
     if (periodic) {
-        std::map<double, int> left_nodes;
+        std::map<std::pair<int, double>, int> left_nodes;
         for (int i = 0; i < n_nodes; ++i)
-            if (node_xy[2 * i] == x0) left_nodes[node_xy[2 * i + 1]] = i;
+            if (node_xy[2 * i] == fr[4 * ncomp[i]]) left_nodes[{ncomp[i], node_xy[2 * i + 1]}] = i;
         for (int i = 0; i < n_nodes; ++i)
-            if (node_xy[2 * i] == x1) {
-                auto it = left_nodes.find(node_xy[2 * i + 1]);
+            if (node_xy[2 * i] == fr[4 * ncomp[i] + 1]) {
+                auto it = left_nodes.find({ncomp[i], node_xy[2 * i + 1]});
                 if (it == left_nodes.end()) return fail(LPDF_ERR_MESH, "node %d on x1 has no partner on x0", i);
                 master[i] = it->second;
             }
@@ -284,6 +341,9 @@ int lpdf_mesh_load(const double* node_xy, int32_t n_nodes, const int32_t* tri, i
     d.n_tri = n_tri;
     d.x0 = (float)x0; d.x1 = (float)x1; d.y0 = (float)y0; d.y1 = (float)y1;
     d.periodic = periodic ? 1 : 0;
+    d.n_comp = n_comp;
+    std::vector<float> cf(4 * (size_t)n_comp);
+    for (size_t q = 0; q < cf.size(); ++q) cf[q] = (float)fr[q];
     d.period = periodic ? (float)period_x : 0.0f;
     m->box[0] = x0; m->box[1] = x1; m->box[2] = y0; m->box[3] = y1;
     cudaError_t ce = cudaSuccess;
@@ -298,7 +358,10 @@ int lpdf_mesh_load(const double* node_xy, int32_t n_nodes, const int32_t* tri, i
         (ce = cudaMemcpy(d.en, en.data(), sizeof(int32_t) * en.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (ce = cudaMemcpy(d.ev, ev.data(), sizeof(int32_t) * ev.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (ce = cudaMemcpy(d.em, em.data(), sizeof(int32_t) * em.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (ce = cudaMemcpy(d.master, master.data(), sizeof(int32_t) * master.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        (ce = cudaMemcpy(d.master, master.data(), sizeof(int32_t) * master.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (n_comp > 1 && ((ce = dalloc(&d.ecomp, n_tri)) != cudaSuccess || (ce = dalloc(&d.cframe, n_comp)) != cudaSuccess ||
+                        (ce = cudaMemcpy(d.ecomp, ecomp.data(), sizeof(int32_t) * n_tri, cudaMemcpyHostToDevice)) != cudaSuccess ||
+                        (ce = cudaMemcpy(d.cframe, cf.data(), sizeof(float) * cf.size(), cudaMemcpyHostToDevice)) != cudaSuccess))) {
         free_mesh_device(d);
         delete m;
         return fail(LPDF_ERR_CUDA, "mesh upload: %s", cudaGetErrorString(ce));
@@ -310,8 +373,30 @@ int lpdf_mesh_load(const double* node_xy, int32_t n_nodes, const int32_t* tri, i
     m->node_xy.assign(node_xy, node_xy + 2 * (size_t)n_nodes);
     m->tri.assign(tri, tri + 3 * (size_t)n_tri);
     m->tag.assign(edge_tag, edge_tag + 3 * (size_t)n_tri);
+    m->node_comp = std::move(ncomp);
+    m->elem_comp = std::move(ecomp);
+    m->period = periodic ? period_x : 0.0;
     *out = m;
     return LPDF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lpdf_mesh_load(const double* node_xy, int32_t n_nodes, const int32_t* tri, int32_t n_tri,
+                   const int32_t* edge_tag, double period_x, lpdf_mesh** out)
+{
+    const int32_t node_off[2] = {0, n_nodes}, tri_off[2] = {0, n_tri};
+    return build_mesh(node_xy, n_nodes, tri, n_tri, edge_tag, 1, node_off, tri_off, period_x, out);
+}
+
+int lpdf_mesh_load_multi(const double* node_xy, int32_t n_nodes, const int32_t* tri, int32_t n_tri,
+                         const int32_t* edge_tag, int32_t n_comp, const int32_t* node_off, const int32_t* tri_off,
+                         double period_x, lpdf_mesh** out)
+{
+    if (n_comp < 1 || !node_off || !tri_off) return fail(LPDF_ERR_ARG, "mesh_load_multi: n_comp = %d", n_comp);
+    return build_mesh(node_xy, n_nodes, tri, n_tri, edge_tag, n_comp, node_off, tri_off, period_x, out);
 }
 
 void lpdf_mesh_free(lpdf_mesh* mesh)
@@ -375,11 +460,21 @@ int lpdf_ctx_create(const lpdf_mesh* mesh, const lpdf_params* params, int64_t ca
         (ce = dalloc(&c->sort.cnt, E + 1)) || (ce = dalloc(&c->sort.cursor, E + 1)) ||
         (ce = dalloc(&c->sort.start, E + 2)) || (ce = dalloc(&c->sort.perm, cap)) ||
         (ce = dalloc(&c->node_acc, (size_t)mesh->d.n_nodes * nq)) || (ce = dalloc(&c->status, 4)) ||
-        (ce = alloc_pipe(c->pipe, cap, E, c->ns))) {
+        (ce = alloc_pipe(c->pipe, cap, E, c->ns)) || (ce = dalloc(&c->comp, mesh->d.n_comp)) ||
+        (ce = dalloc(&c->init_pbase, mesh->d.n_comp + 1)) || (ce = dalloc(&c->init_ppe, mesh->d.n_comp)) ||
+        (ce = dalloc(&c->init_toff, mesh->d.n_comp + 1)) || (ce = dalloc(&c->init_key, 2 * mesh->d.n_comp)) ||
+        (ce = dalloc(&c->step_dev, 1))) {
         lpdf_ctx_free(c);
         return fail(LPDF_ERR_CUDA, "ctx_create: %s", cudaGetErrorString(ce));
     }
     cudaMemset(c->node_acc, 0, sizeof(unsigned long long) * (size_t)mesh->d.n_nodes * nq);
+    c->comp_host.assign(mesh->d.n_comp, comp_params(params->seed, params->n_sources, params->src_x, params->src_y,
+                                                    params->src_r, params->src_alpha));
+    if ((ce = cudaMemcpy(c->comp, c->comp_host.data(), sizeof(CompParams) * c->comp_host.size(),
+                         cudaMemcpyHostToDevice)) != cudaSuccess) {
+        lpdf_ctx_free(c);
+        return fail(LPDF_ERR_CUDA, "ctx_create: %s", cudaGetErrorString(ce));
+    }
     const unsigned long long st0[4] = {0ull, 0ull, ~0ull, 0ull};
     if ((ce = cudaMemcpy(c->status, st0, sizeof st0, cudaMemcpyHostToDevice)) != cudaSuccess) {
         lpdf_ctx_free(c);
@@ -405,6 +500,10 @@ void lpdf_ctx_free(lpdf_ctx* c)
                   w.krstart, w.klist, w.klist2, w.scan_part, w.efields};
     for (void* q : pp) cudaFree(q);
     cudaFree(c->node_acc); cudaFree(c->status);
+    cudaFree(c->comp); cudaFree(c->init_pbase); cudaFree(c->init_ppe); cudaFree(c->init_toff); cudaFree(c->init_key);
+    cudaFree(c->step_dev);
+    drop_graphs(c);
+    if (c->graph_stream) cudaStreamDestroy(c->graph_stream);
     delete c;
 }
 
@@ -415,25 +514,92 @@ int lpdf_ctx_set_params(lpdf_ctx* c, const lpdf_params* p)
     if (rc) return rc;
     if (p->ns != c->ns) return fail(LPDF_ERR_ARG, "ns cannot change (%d -> %d)", c->ns, p->ns);
     c->params = *p;
+    drop_graphs(c);
+    if (!c->comp_set) {
+        c->comp_host.assign(c->mesh->d.n_comp, comp_params(p->seed, p->n_sources, p->src_x, p->src_y, p->src_r,
+                                                           p->src_alpha));
+        CUDA_TRY(cudaMemcpy(c->comp, c->comp_host.data(), sizeof(CompParams) * c->comp_host.size(),
+                            cudaMemcpyHostToDevice));
+    }
+    return LPDF_OK;
+}
+
+int lpdf_ctx_set_components(lpdf_ctx* c, const lpdf_component* comps, int32_t n)
+{
+    if (!c || !comps) return fail(LPDF_ERR_ARG, "ctx_set_components: NULL argument");
+    if (n != c->mesh->d.n_comp)
+        return fail(LPDF_ERR_ARG, "ctx_set_components: %d components for a mesh of %d", n, c->mesh->d.n_comp);
+    for (int k = 0; k < n; ++k) {
+        const lpdf_component& q = comps[k];
+        if (q.n_sources < 0 || q.n_sources > LPDF_MAX_SOURCES)
+            return fail(LPDF_ERR_ARG, "component %d: n_sources = %d", k, q.n_sources);
+        for (int i = 0; i < q.n_sources; ++i)
+            if (q.src_alpha[i] < 0 || q.src_alpha[i] >= c->ns)
+                return fail(LPDF_ERR_ARG, "component %d: source %d sets scalar %d, but ns = %d", k, i, q.src_alpha[i],
+                            c->ns);
+    }
+    for (int k = 0; k < n; ++k) {
+        const lpdf_component& q = comps[k];
+        c->comp_host[k] = comp_params(q.seed, q.n_sources, q.src_x, q.src_y, q.src_r, q.src_alpha);
+    }
+    CUDA_TRY(cudaMemcpy(c->comp, c->comp_host.data(), sizeof(CompParams) * n, cudaMemcpyHostToDevice));
+    c->comp_set = true;
+    drop_graphs(c);
     return LPDF_OK;
 }
 
 int64_t lpdf_ctx_size(const lpdf_ctx* c) { return c ? c->s.n : -1; }
 
+static int init_with(lpdf_ctx* c, const std::vector<int>& ppe, const float* node_init, int32_t m_erlang,
+                     cudaStream_t st)
+{
+    if (m_erlang < 1 || m_erlang > 6) return fail(LPDF_ERR_ARG, "m_erlang = %d outside 1..6", m_erlang);
+    const DevMesh& d = c->mesh->d;
+    const int nc = d.n_comp;
+    std::vector<long long> pbase(nc + 1, 0);
+    std::vector<int> toff(nc + 1, 0);
+    std::vector<uint32_t> key(2 * nc);
+    // element ranges of the components, from the element -> component map the mesh keeps on the host
+    int e = 0;
+    for (int k = 0; k < nc; ++k) {
+        toff[k] = e;
+        while (e < d.n_tri && (nc == 1 || c->mesh->elem_comp[e] == k)) ++e;
+        if (ppe[k] < 1) return fail(LPDF_ERR_ARG, "particles per element of component %d = %d", k, ppe[k]);
+        pbase[k + 1] = pbase[k] + (long long)(e - toff[k]) * ppe[k];
+        key[2 * k] = c->comp_host[k].key0;
+        key[2 * k + 1] = c->comp_host[k].key1;
+    }
+    toff[nc] = e;
+    const int64_t P = pbase[nc];
+    if (P > c->s.cap) return fail(LPDF_ERR_ARG, "%lld particles exceed capacity %lld", (long long)P, (long long)c->s.cap);
+    for (int k = 0; k < nc; ++k)
+        if (pbase[k + 1] - pbase[k] > (long long)UINT32_MAX) return fail(LPDF_ERR_ARG, "particle ids are 32-bit");
+    CUDA_TRY(cudaMemcpy(c->init_pbase, pbase.data(), sizeof(long long) * pbase.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->init_ppe, ppe.data(), sizeof(int) * nc, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->init_toff, toff.data(), sizeof(int) * toff.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->init_key, key.data(), sizeof(uint32_t) * key.size(), cudaMemcpyHostToDevice));
+    c->s.n = P;
+    drop_graphs(c);
+    const InitLayout L{c->init_pbase, c->init_ppe, c->init_toff, c->init_key, nc};
+    CUDA_TRY(launch_particles_init(d, c->s, c->ns, L, P, node_init, m_erlang, c->status, st));
+    // generated element by element: the buffer is already in element order
+    CUDA_TRY(launch_iota(c->pipe.perm, P, st));
+    return LPDF_OK;
+}
+
 int lpdf_particles_init(lpdf_ctx* c, int32_t n_per_elem, const float* node_init, int32_t m_erlang, void* stream)
 {
     if (!c || !node_init) return fail(LPDF_ERR_ARG, "particles_init: NULL argument");
     if (n_per_elem < 1) return fail(LPDF_ERR_ARG, "n_per_elem = %d", n_per_elem);
-    if (m_erlang < 1 || m_erlang > 6) return fail(LPDF_ERR_ARG, "m_erlang = %d outside 1..6", m_erlang);
-    const int64_t P = (int64_t)c->mesh->d.n_tri * n_per_elem;
-    if (P > c->s.cap) return fail(LPDF_ERR_ARG, "%lld particles exceed capacity %lld", (long long)P, (long long)c->s.cap);
-    if (P > (int64_t)UINT32_MAX) return fail(LPDF_ERR_ARG, "particle ids are 32-bit");
-    c->s.n = P;
-    CUDA_TRY(launch_particles_init(c->mesh->d, c->s, c->ns, n_per_elem, node_init, m_erlang, c->params.seed,
-                                   c->status, (cudaStream_t)stream));
-    // generated element by element: the buffer is already in element order
-    CUDA_TRY(launch_iota(c->pipe.perm, P, (cudaStream_t)stream));
-    return LPDF_OK;
+    return init_with(c, std::vector<int>(c->mesh->d.n_comp, n_per_elem), node_init, m_erlang, (cudaStream_t)stream);
+}
+
+int lpdf_particles_init_multi(lpdf_ctx* c, const int32_t* n_per_elem, const float* node_init, int32_t m_erlang,
+                              void* stream)
+{
+    if (!c || !n_per_elem || !node_init) return fail(LPDF_ERR_ARG, "particles_init_multi: NULL argument");
+    return init_with(c, std::vector<int>(n_per_elem, n_per_elem + c->mesh->d.n_comp), node_init, m_erlang,
+                     (cudaStream_t)stream);
 }
 
 static int copy_state(lpdf_ctx* c, int64_t n, bool in, float* x, float* y, float* u, float* v, float* w, float* om,
@@ -463,6 +629,7 @@ int lpdf_set_state(lpdf_ctx* c, int64_t n, const float* x, const float* y, const
                    const float* w, const float* om, const float* psi, const int32_t* elem, const uint32_t* pid,
                    int on_device, void* stream)
 {
+    if (c) drop_graphs(c);
     if (!c) return fail(LPDF_ERR_ARG, "ctx is NULL");
     if (n < 0 || n > c->s.cap) return fail(LPDF_ERR_ARG, "n = %lld outside 0..%lld", (long long)n, (long long)c->s.cap);
     if (n > 0 && (!x || !y || !u || !v || !w || !om || !psi || !elem || !pid))
@@ -486,6 +653,7 @@ int lpdf_get_state(const lpdf_ctx* c, float* x, float* y, float* u, float* v, fl
 
 int lpdf_sort(lpdf_ctx* c, void* stream)
 {
+    if (c) drop_graphs(c);
     if (!c) return fail(LPDF_ERR_ARG, "sort: NULL argument");
     c->s2.n = c->s.n;
     CUDA_TRY(launch_sort(c->mesh->d, c->s, c->ns, c->s2, c->sort, c->status, (cudaStream_t)stream));
@@ -501,7 +669,8 @@ int lpdf_pdf_step(lpdf_ctx* c, const float* node_fields, uint64_t step, void* st
     ++c->nsteps;
     const int nq = nquant(c->ns);
     CUDA_TRY(cudaMemsetAsync(c->node_acc, 0, sizeof(unsigned long long) * (size_t)c->mesh->d.n_nodes * nq, st));
-    const StepParams p = make_step_params(c->params, c->mesh, step);
+    StepParams p = make_step_params(c->params, c->mesh, step);
+    p.comp = c->mesh->d.n_comp > 1 ? c->comp : nullptr;
     c->s2.n = c->s.n;
     std::array<cudaEvent_t, 4> ev{};
     if (c->timing) {
@@ -516,11 +685,153 @@ int lpdf_pdf_step(lpdf_ctx* c, const float* node_fields, uint64_t step, void* st
         c->ev_pending.push_back(ev);
     }
     CUDA_TRY(launch_pdf_step_pipeline(c->mesh->d, c->s, c->s2, c->ns, node_fields, p, c->pipe, c->node_acc,
-                                      c->status, st, c->timing ? ev.data() : nullptr));
+                                      c->status, st, c->timing ? ev.data() : nullptr, c->tune));
     // the new state is in the second buffer, listed in element order by perm_new
     std::swap(c->s, c->s2);
     std::swap(c->pipe.perm, c->pipe.perm_new);
     return LPDF_OK;
+}
+
+static int capture_steps(lpdf_ctx* c, const float* fields, int slot)
+{
+    if (c->graph[slot]) cudaGraphExecDestroy(c->graph[slot]);
+    c->graph[slot] = nullptr;
+    if (!c->graph_stream) CUDA_TRY(cudaStreamCreateWithFlags(&c->graph_stream, cudaStreamNonBlocking));
+    const cudaStream_t cs = c->graph_stream;
+    (void)sm_count();   // device queries stay outside the capture
+    CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const int nq = nquant(c->ns);
+    DevState a = c->s, b = c->s2;
+    PipeScratch w = c->pipe;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMemsetAsync(c->node_acc, 0, sizeof(unsigned long long) * (size_t)c->mesh->d.n_nodes * nq, cs);
+        StepParams p = make_step_params(c->params, c->mesh, 0);
+        p.comp = c->mesh->d.n_comp > 1 ? c->comp : nullptr;
+        p.step_dev = c->step_dev;
+        p.step_add = (unsigned)k;
+        b.n = a.n;
+        if (e == cudaSuccess)
+            e = launch_pdf_step_pipeline(c->mesh->d, a, b, c->ns, fields, p, w, c->node_acc, c->status, cs, nullptr,
+                                         c->tune);
+        std::swap(a, b);
+        std::swap(w.perm, w.perm_new);
+    }
+    if (e == cudaSuccess) e = launch_step_counter(c->step_dev, 0ull, 2ull, cs);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph[slot], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->graph[slot] = nullptr;
+        return fail(LPDF_ERR_CUDA, "pdf_steps: graph capture: %s", cudaGetErrorString(e));
+    }
+    c->graph_fields[slot] = fields;
+    c->graph_state[slot] = c->s.x;
+    c->graph_perm[slot] = c->pipe.perm;
+    return LPDF_OK;
+}
+
+int lpdf_pdf_steps(lpdf_ctx* c, const float* node_fields, uint64_t step0, int32_t nsteps, void* stream)
+{
+    if (!c || !node_fields) return fail(LPDF_ERR_ARG, "pdf_steps: NULL argument");
+    if (nsteps < 0) return fail(LPDF_ERR_ARG, "pdf_steps: nsteps = %d", nsteps);
+    const cudaStream_t st = (cudaStream_t)stream;
+    const int pairs = nsteps / 2;
+    if (pairs > 0 && c->s.n > 0) {
+        int slot = -1;
+        for (int k = 0; k < 2; ++k)
+            if (c->graph[k] && c->graph_fields[k] == node_fields && c->graph_state[k] == c->s.x &&
+                c->graph_perm[k] == c->pipe.perm)
+                slot = k;
+        if (slot < 0) {
+            slot = c->graph_next;
+            c->graph_next ^= 1;
+            if (const int rc = capture_steps(c, node_fields, slot)) return rc;
+        }
+        CUDA_TRY(launch_step_counter(c->step_dev, step0, 0ull, st));
+        for (int k = 0; k < pairs; ++k) CUDA_TRY(cudaGraphLaunch(c->graph[slot], st));
+        c->nsteps += 2 * pairs;
+    } else if (pairs > 0) {
+        for (int k = 0; k < 2 * pairs; ++k)
+            if (const int rc = lpdf_pdf_step(c, node_fields, step0 + k, stream)) return rc;
+    }
+    if (nsteps % 2) return lpdf_pdf_step(c, node_fields, step0 + 2 * (uint64_t)pairs, stream);
+    return LPDF_OK;
+}
+
+int lpdf_ctx_set_tune(lpdf_ctx* c, int32_t adv, int32_t mom)
+{
+    if (!c) return fail(LPDF_ERR_ARG, "ctx is NULL");
+    if (adv < 0 || adv >= kAdvVariants || mom < 0 || mom >= kMomVariants)
+        return fail(LPDF_ERR_ARG, "set_tune: adv = %d (0..%d), mom = %d (0..%d)", adv, kAdvVariants - 1, mom,
+                    kMomVariants - 1);
+    c->tune.adv = adv;
+    c->tune.mom = mom;
+    drop_graphs(c);
+    return LPDF_OK;
+}
+
+int lpdf_ctx_autotune(lpdf_ctx* c, const float* node_fields, uint64_t step0, int32_t steps_per_trial, int32_t* choice,
+                      double* trial_ms, int32_t* steps_used, void* stream)
+{
+    if (!c || !node_fields) return fail(LPDF_ERR_ARG, "autotune: NULL argument");
+    if (steps_per_trial < 1) return fail(LPDF_ERR_ARG, "autotune: steps_per_trial = %d", steps_per_trial);
+    const cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    uint64_t step = step0;
+    int rc = LPDF_OK;
+    auto trial = [&](int adv, int mom, double& ms) -> int {
+        c->tune.adv = adv;
+        c->tune.mom = mom;
+        if (int r = lpdf_pdf_step(c, node_fields, step++, stream)) return r;   // warm-up of this variant
+        if (cudaEventRecord(e0, st) != cudaSuccess) return fail(LPDF_ERR_CUDA, "autotune: event record");
+        for (int k = 0; k < steps_per_trial; ++k)
+            if (int r = lpdf_pdf_step(c, node_fields, step++, stream)) return r;
+        float t = 0.0f;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+            return fail(LPDF_ERR_CUDA, "autotune: event timing");
+        ms = t / steps_per_trial;
+        return LPDF_OK;
+    };
+    const bool timing = c->timing;
+    c->timing = false;
+    StepTune best = c->tune;
+    double best_ms = 1e300;
+    for (int v = 0; v < kAdvVariants && rc == LPDF_OK; ++v) {
+        double ms = 0.0;
+        rc = trial(v, best.mom, ms);
+        if (trial_ms) trial_ms[v] = ms;
+        if (rc == LPDF_OK && ms < best_ms) {
+            best_ms = ms;
+            best.adv = v;
+        }
+    }
+    best_ms = 1e300;
+    for (int v = 0; v < kMomVariants && rc == LPDF_OK; ++v) {
+        double ms = 0.0;
+        rc = trial(best.adv, v, ms);
+        if (trial_ms) trial_ms[kAdvVariants + v] = ms;
+        if (rc == LPDF_OK && ms < best_ms) {
+            best_ms = ms;
+            best.mom = v;
+        }
+    }
+    c->timing = timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->tune = best;
+    drop_graphs(c);
+    if (choice) {
+        choice[0] = best.adv;
+        choice[1] = best.mom;
+    }
+    if (steps_used) *steps_used = (int32_t)(step - step0);
+    return rc;
 }
 
 int lpdf_ctx_set_timing(lpdf_ctx* c, int enable)

@@ -429,8 +429,10 @@ __device__ __forceinline__ void interpolate_fields(const DevMesh& M, const float
 }
 
 // On return p holds the new state except the element, which is the walk's start: the old
-// element, or 0 when the old one is outside the mesh (`bad`).
-template <int NS, bool kElementTable = false>
+// element, or 0 when the old one is outside the mesh (`bad`). kMulti: the mesh holds several
+// independent components; the particle's component (that of its element) gives the frame, the
+// Philox key and the sources.
+template <int NS, bool kElementTable = false, bool kMulti = false>
 __device__ __forceinline__ void advance_particle(const DevMesh& M, const float* __restrict__ F, const StepParams& P,
                                                  ParticleState<NS>& p, unsigned& err, bool& bad)
 {
@@ -438,12 +440,39 @@ __device__ __forceinline__ void advance_particle(const DevMesh& M, const float* 
     const float x = p.x, y = p.y, u = p.u, v = p.v, w = p.w, om = p.om;
     bad = (unsigned)p.elem >= (unsigned)M.n_tri;
     const int e = bad ? 0 : p.elem;
+    float fx0 = M.x0, fx1 = M.x1, fy0 = M.y0, fy1 = M.y1;
+    uint32_t key0 = P.key0, key1 = P.key1;
+    int n_src = P.n_src;
+    const float *src_x = P.src_x, *src_y = P.src_y, *src_r = P.src_r;
+    const int* src_alpha = P.src_alpha;
+    if (kMulti) {
+        const int c = __ldg(&M.ecomp[e]);
+        const float4 fr = __ldg(&M.cframe[c]);
+        fx0 = fr.x;
+        fx1 = fr.y;
+        fy0 = fr.z;
+        fy1 = fr.w;
+        const CompParams& cp = P.comp[c];
+        key0 = cp.key0;
+        key1 = cp.key1;
+        n_src = cp.n_src;
+        src_x = cp.src_x;
+        src_y = cp.src_y;
+        src_r = cp.src_r;
+        src_alpha = cp.src_alpha;
+    }
     // linear shape-function interpolation of the node fields
     float Fi[NFP];
     interpolate_fields<NS, kElementTable>(M, F, e, x, y, Fi);
     // Wiener increments: Philox blocks 0 and 1 of counter (pid, step, 0<<16 | block)
-    const uint4 r0 = philox4x32_10(make_uint4(p.pid, P.step_lo, P.step_hi, 0u), P.key0, P.key1);
-    const uint4 r1 = philox4x32_10(make_uint4(p.pid, P.step_lo, P.step_hi, 1u), P.key0, P.key1);
+    uint32_t step_lo = P.step_lo, step_hi = P.step_hi;
+    if (P.step_dev) {
+        const unsigned long long sn = *P.step_dev + P.step_add;
+        step_lo = (uint32_t)sn;
+        step_hi = (uint32_t)(sn >> 32);
+    }
+    const uint4 r0 = philox4x32_10(make_uint4(p.pid, step_lo, step_hi, 0u), key0, key1);
+    const uint4 r1 = philox4x32_10(make_uint4(p.pid, step_lo, step_hi, 1u), key0, key1);
     float z0, z1, z2, z3, z4, z5;
     box_muller(r0.x, r0.y, z0, z1);
     box_muller(r0.z, r0.w, z2, z3);
@@ -472,27 +501,27 @@ __device__ __forceinline__ void advance_particle(const DevMesh& M, const float* 
     float qx = x + u * P.dt + P.s2nu * dW1;
     float qy = y + v * P.dt + P.s2nu * dW2;
     if (M.periodic) {
-        if (qx < M.x0) qx += M.period;
-        else if (qx >= M.x1) qx -= M.period;
-        if (qx < M.x0 || qx >= M.x1) qx -= floorf((qx - M.x0) / M.period) * M.period;   // moves > one period
+        if (qx < fx0) qx += M.period;
+        else if (qx >= fx1) qx -= M.period;
+        if (qx < fx0 || qx >= fx1) qx -= floorf((qx - fx0) / M.period) * M.period;   // moves > one period
     }
 #pragma unroll 1
     for (int it = 0; it < 8; ++it) {
-        if (qy < M.y0) { qy = 2.0f * M.y0 - qy; un = -un; vn = -vn; wn = -wn; }
-        else if (qy > M.y1) { qy = 2.0f * M.y1 - qy; un = 2.0f * P.lid_u - un; vn = -vn; wn = -wn; }
-        else if (!M.periodic && qx < M.x0) { qx = 2.0f * M.x0 - qx; un = -un; vn = -vn; wn = -wn; }
-        else if (!M.periodic && qx > M.x1) { qx = 2.0f * M.x1 - qx; un = -un; vn = -vn; wn = -wn; }
+        if (qy < fy0) { qy = 2.0f * fy0 - qy; un = -un; vn = -vn; wn = -wn; }
+        else if (qy > fy1) { qy = 2.0f * fy1 - qy; un = 2.0f * P.lid_u - un; vn = -vn; wn = -wn; }
+        else if (!M.periodic && qx < fx0) { qx = 2.0f * fx0 - qx; un = -un; vn = -vn; wn = -wn; }
+        else if (!M.periodic && qx > fx1) { qx = 2.0f * fx1 - qx; un = -un; vn = -vn; wn = -wn; }
         else break;
     }
     // half-open domain [x0, x1) x [y0, y1)
-    if (qx >= M.x1) qx = M.periodic ? M.x0 : nextafterf(M.x1, -CUDART_INF_F);
-    if (qy >= M.y1) qy = nextafterf(M.y1, -CUDART_INF_F);
+    if (qx >= fx1) qx = M.periodic ? fx0 : nextafterf(fx1, -CUDART_INF_F);
+    if (qy >= fy1) qy = nextafterf(fy1, -CUDART_INF_F);
     // concentrated scalar sources
-    for (int q = 0; q < P.n_src; ++q)
-        if (in_source(qx, qy, P.src_x[q], P.src_y[q], P.src_r[q])) {
+    for (int q = 0; q < n_src; ++q)
+        if (in_source(qx, qy, src_x[q], src_y[q], src_r[q])) {
 #pragma unroll
             for (int a = 0; a < NS; ++a)
-                if (a == P.src_alpha[q]) p.psi[a] = 1.0f;
+                if (a == src_alpha[q]) p.psi[a] = 1.0f;
         }
     if (!(isfinite(un) && isfinite(vn) && isfinite(wn) && isfinite(omn) && isfinite(qx) && isfinite(qy)))
         err |= kErrNonFinite;

@@ -38,6 +38,19 @@ struct DevMesh {
     // lambda_0 = 1 - lambda_1 - lambda_2, (dx, dy) = p - vertex 0
     float4* ea = nullptr;     // (x_v0, y_v0, b1, g1)
     float4* eb = nullptr;     // (b2, g2, centroid x, 0)
+    // several independent meshes in one (lpdf_mesh_load_multi): the component of every element
+    // and each component's half-open frame [x0, x1) x [y0, y1); n_comp = 1 leaves both NULL
+    int n_comp = 1;
+    int* ecomp = nullptr;
+    float4* cframe = nullptr;
+};
+
+// per-component Philox key and scalar sources of a multi-component ensemble
+struct CompParams {
+    uint32_t key0, key1;
+    int n_src, pad;
+    float src_x[LPDF_MAX_SOURCES], src_y[LPDF_MAX_SOURCES], src_r[LPDF_MAX_SOURCES];
+    int src_alpha[LPDF_MAX_SOURCES];
 };
 
 struct StepParams {
@@ -47,6 +60,9 @@ struct StepParams {
     int n_src;
     float src_x[LPDF_MAX_SOURCES], src_y[LPDF_MAX_SOURCES], src_r[LPDF_MAX_SOURCES];
     int src_alpha[LPDF_MAX_SOURCES];
+    const CompParams* comp;   // per component (multi-component meshes), else NULL
+    const unsigned long long* step_dev;   // if set, the step number is *step_dev + step_add
+    unsigned step_add;
 };
 
 struct DevState {
@@ -63,9 +79,17 @@ enum : unsigned { kErrLost = 1u, kErrNonFinite = 2u, kErrOverflow = 4u, kErrTime
 cudaError_t launch_pdf_step(const DevMesh& m, const DevState& s, int ns, const float* fields,
                             const StepParams& p, unsigned long long* node_acc, unsigned long long* status,
                             cudaStream_t st);
-cudaError_t launch_particles_init(const DevMesh& m, const DevState& s, int ns, int n_per_elem,
-                                  const float* node_init, int m_erlang, uint64_t seed,
-                                  unsigned long long* status, cudaStream_t st);
+// particle layout of an initialisation: component c holds particles [pbase[c], pbase[c + 1]),
+// ppe[c] per element of its elements (from tri_off[c]); Philox key (key[2c], key[2c + 1])
+struct InitLayout {
+    const long long* pbase;
+    const int* ppe;
+    const int* tri_off;
+    const uint32_t* key;
+    int n_comp;
+};
+cudaError_t launch_particles_init(const DevMesh& m, const DevState& s, int ns, const InitLayout& L, int64_t P,
+                                  const float* node_init, int m_erlang, unsigned long long* status, cudaStream_t st);
 cudaError_t launch_grid_statistics(const DevMesh& m, int ns, const unsigned long long* node_acc, double* out,
                                    int raw, cudaStream_t st);
 
@@ -98,11 +122,23 @@ struct PipeScratch {
 };
 // ev (may be NULL): 4 events recorded before the advance kernel, after it, after the re-bucketing
 // kernels and after the moments kernel
+// launch configuration of the step's kernels (lpdf_ctx_autotune); every choice gives
+// bit-identical results. adv: advance kernel 0 = 256 threads, >= 4 CTAs/SM; 1 = 256, >= 6;
+// 2 = 128, >= 8; 3 = 256, >= 4, persistent grid; 4 = 256, >= 6, persistent. mom: moments kernel
+// 0 = 256 threads, >= 2 CTAs/SM; 1 = 128, >= 4; 2 = 512, >= 1; 3 = 256, >= 3.
+struct StepTune {
+    int adv = 0, mom = 0;
+};
+constexpr int kAdvVariants = 5, kMomVariants = 4;
 cudaError_t launch_pdf_step_pipeline(const DevMesh& m, const DevState& cur, const DevState& nxt, int ns,
                                      const float* fields, const StepParams& p, PipeScratch& w,
                                      unsigned long long* node_acc, unsigned long long* status, cudaStream_t st,
-                                     const cudaEvent_t* ev);
+                                     const cudaEvent_t* ev, const StepTune& tune);
 cudaError_t launch_iota(int* p, int64_t n, cudaStream_t st);
+// SMs of the current device (queried once; call it before a stream capture)
+int sm_count();
+// *c = set (add = 0) or *c += add, one thread
+cudaError_t launch_step_counter(unsigned long long* c, unsigned long long set, unsigned long long add, cudaStream_t st);
 
 // tensor-core GEMM tile (lpdf_mlp.cu): D = A B^T, BF16 operands, FP32 result
 cudaError_t launch_tc_gemm(const void* A, const void* B, float* D, int M, int N, int K, unsigned* error,
@@ -140,8 +176,10 @@ struct Fem {
     // wall distance of every geometric node (inputs of the learned surrogate)
     double* xy = nullptr;        // 2 per geometric node
     double* seg = nullptr;       // 4 per wall edge: (xa, ya, xb, yb)
-    int* segn = nullptr;         // 2 per wall edge: its geometric end nodes a, b
-    int nseg = 0;
+    int* segn = nullptr;         // 2 per wall edge: its geometric end nodes a, b (grouped by component)
+    int* seg_off = nullptr;      // per component: its wall edges [seg_off[c], seg_off[c + 1])
+    int* ncomp = nullptr;        // component of every geometric node
+    int nseg = 0, n_comp = 1;
     double period = 0.0;         // x period (0: none)
     double* wdist = nullptr;     // per geometric node, filled on first use: distance to the wall,
     int* wseg = nullptr;         //   the wall edge of the nearest wall point
@@ -149,7 +187,8 @@ struct Fem {
     bool has_wdist = false;
 };
 cudaError_t fem_build(const double* node_xy, int n_nodes, const int32_t* tri, int n_tri, const int32_t* tag,
-                      const std::vector<int32_t>& master, double period, Fem** out);
+                      const std::vector<int32_t>& master, const std::vector<int32_t>& node_comp, double period,
+                      Fem** out);
 void fem_free(Fem* F);
 // statistics (n_nodes x (11 + 2 ns), lpdf_grid_statistics raw = 0) -> node fields; iters[2];
 // cudaErrorNotReady when a CG did not converge within maxit. With surr != NULL (n_nodes x 16
@@ -212,6 +251,9 @@ struct lpdf_mesh {
     std::vector<int32_t> master;   // host copy
     std::vector<double> node_xy;   // host copies of the input (for the gridpoint solve)
     std::vector<int32_t> tri, tag;
+    std::vector<int32_t> node_comp;  // component of every node
+    std::vector<int32_t> elem_comp;  // component of every element
+    double period = 0.0;             // x period (0: walls)
     double box[4];
     int device;
     mutable std::mutex fem_mutex;
@@ -230,6 +272,23 @@ struct lpdf_ctx {
     int ns;
     int64_t nsteps = 0;                       // pdf_step calls so far
     // per-kernel timing (lpdf_ctx_set_timing): event quadruples of the recorded steps
+    lpdf::StepTune tune;                      // lpdf_ctx_autotune's choice
+    lpdf::CompParams* comp = nullptr;         // per component (multi-component meshes), device
+    std::vector<lpdf::CompParams> comp_host;
+    bool comp_set = false;                    // lpdf_ctx_set_components was called
+    // the last initialisation layout (device): pbase, ppe, tri_off, keys
+    long long* init_pbase = nullptr;
+    int* init_ppe = nullptr;
+    int* init_toff = nullptr;
+    uint32_t* init_key = nullptr;
+    const float* graph_state[2] = {nullptr, nullptr};   // the buffer and order each graph was captured on
+    const int* graph_perm[2] = {nullptr, nullptr};
+    int graph_next = 0;                       // the slot the next capture replaces
+    cudaStream_t graph_stream = nullptr;
+    // CUDA graphs of two consecutive steps (lpdf_pdf_steps), for the fields pointer they captured
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    const float* graph_fields[2] = {nullptr, nullptr};
+    unsigned long long* step_dev = nullptr;   // the step number the graph's kernels read
     bool timing = false;
     std::vector<cudaEvent_t> ev_free;
     std::vector<std::array<cudaEvent_t, 4>> ev_pending;

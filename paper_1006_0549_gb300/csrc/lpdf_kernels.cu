@@ -1,5 +1,5 @@
 // Particle initialisation and gridpoint statistics (sm_103a). The particle step itself is in
-// lpdf_step.cu.
+// lpdf_pipeline.cu (and lpdf_step.cu for the no-allocation entry point).
 #include "lpdf_device.cuh"
 
 namespace lpdf {
@@ -8,17 +8,27 @@ namespace lpdf {
 // Particle initialisation: uniform position in the generating element (s = sqrt(r1):
 // lambda = (1-s, s(1-r2), s r2)), exact location, Gaussian velocity about the interpolated
 // mean, Erlang(m) frequency with the interpolated mean, psi = 0. Philox tag 1, blocks 0..2.
+// Component c (one for an ordinary mesh) holds particles [pbase[c], pbase[c + 1]), ppe[c] per
+// element of its element range, with ids counted from 0 and its own Philox key.
 // ------------------------------------------------------------------------------------------
 template <int NS>
-__global__ void particles_init_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevState S, int n_per_elem, const float* __restrict__ init,
-                                      int m_erlang, uint32_t k0, uint32_t k1, unsigned long long* status)
+__global__ void particles_init_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevState S,
+                                      const __grid_constant__ InitLayout L, const float* __restrict__ init,
+                                      int m_erlang, unsigned long long* status)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t P = (int64_t)M.n_tri * n_per_elem;
     unsigned err = 0;
-    if (i < P) {
-        const int e = (int)(i / n_per_elem);
-        const uint32_t pid = (uint32_t)i;
+    if (i < L.pbase[L.n_comp]) {
+        int lo = 0, hi = L.n_comp - 1;   // the component: pbase[lo] <= i < pbase[lo + 1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (L.pbase[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        const int64_t local = i - L.pbase[lo];
+        const int e = L.tri_off[lo] + (int)(local / L.ppe[lo]);
+        const uint32_t pid = (uint32_t)local;
+        const uint32_t k0 = L.key[2 * lo], k1 = L.key[2 * lo + 1];
         const uint4 a = philox4x32_10(make_uint4(pid, 0u, 0u, (1u << 16) | 0u), k0, k1);
         const uint4 b = philox4x32_10(make_uint4(pid, 0u, 0u, (1u << 16) | 1u), k0, k1);
         const uint4 c = philox4x32_10(make_uint4(pid, 0u, 0u, (1u << 16) | 2u), k0, k1);
@@ -27,8 +37,15 @@ __global__ void particles_init_kernel(const __grid_constant__ DevMesh M, const _
         const float l0 = 1.0f - sq, l1 = sq * (1.0f - r2), l2 = sq * r2;
         float px = fmaf(l0, X.x, fmaf(l1, X.y, l2 * X.z));
         float py = fmaf(l0, Y.x, fmaf(l1, Y.y, l2 * Y.z));
-        if (px >= M.x1) px = M.periodic ? M.x0 : nextafterf(M.x1, -CUDART_INF_F);
-        if (py >= M.y1) py = nextafterf(M.y1, -CUDART_INF_F);
+        float fx0 = M.x0, fx1 = M.x1, fy1 = M.y1;
+        if (M.n_comp > 1) {
+            const float4 fr = __ldg(&M.cframe[lo]);
+            fx0 = fr.x;
+            fx1 = fr.y;
+            fy1 = fr.w;
+        }
+        if (px >= fx1) px = M.periodic ? fx0 : nextafterf(fx1, -CUDART_INF_F);
+        if (py >= fy1) py = nextafterf(fy1, -CUDART_INF_F);
         int hops = 0;
         float lw[3];
         int ne = locate_walk(M, e, px, py, hops, lw);
@@ -60,18 +77,16 @@ __global__ void particles_init_kernel(const __grid_constant__ DevMesh M, const _
     if (err) atomicOr(&status[0], (unsigned long long)err);
 }
 
-cudaError_t launch_particles_init(const DevMesh& m, const DevState& s, int ns, int n_per_elem, const float* node_init,
-                                  int m_erlang, uint64_t seed, unsigned long long* status, cudaStream_t st)
+cudaError_t launch_particles_init(const DevMesh& m, const DevState& s, int ns, const InitLayout& L, int64_t P,
+                                  const float* node_init, int m_erlang, unsigned long long* status, cudaStream_t st)
 {
-    const int64_t P = (int64_t)m.n_tri * n_per_elem;
     const unsigned grid = (unsigned)((P + 255) / 256);
     if (grid == 0) return cudaSuccess;
-    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     switch (ns) {
-        case 1: particles_init_kernel<1><<<grid, 256, 0, st>>>(m, s, n_per_elem, node_init, m_erlang, k0, k1, status); break;
-        case 2: particles_init_kernel<2><<<grid, 256, 0, st>>>(m, s, n_per_elem, node_init, m_erlang, k0, k1, status); break;
-        case 3: particles_init_kernel<3><<<grid, 256, 0, st>>>(m, s, n_per_elem, node_init, m_erlang, k0, k1, status); break;
-        case 4: particles_init_kernel<4><<<grid, 256, 0, st>>>(m, s, n_per_elem, node_init, m_erlang, k0, k1, status); break;
+        case 1: particles_init_kernel<1><<<grid, 256, 0, st>>>(m, s, L, node_init, m_erlang, status); break;
+        case 2: particles_init_kernel<2><<<grid, 256, 0, st>>>(m, s, L, node_init, m_erlang, status); break;
+        case 3: particles_init_kernel<3><<<grid, 256, 0, st>>>(m, s, L, node_init, m_erlang, status); break;
+        case 4: particles_init_kernel<4><<<grid, 256, 0, st>>>(m, s, L, node_init, m_erlang, status); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -68,72 +68,87 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int& total
 // ------------------------------------------------------------------------------------------
 // K1
 // ------------------------------------------------------------------------------------------
-template <int NS>
-__global__ void __launch_bounds__(kBlk, 4)
+// one particle: position i of the next buffer takes particle perm[i] of the current one
+template <int NS, bool kMulti>
+__device__ __forceinline__ void advance_one(const DevMesh& M, const DevState& cur, const DevState& nxt,
+                                            const int* __restrict__ perm, const float* __restrict__ EF,
+                                            const StepParams& P, unsigned long long* __restrict__ status, int64_t i,
+                                            unsigned& err, int& hops)
+{
+    const int src = perm[i];
+    ParticleState<NS> p;
+    p.x = cur.x[src];
+    p.y = cur.y[src];
+    p.u = cur.u[src];
+    p.v = cur.v[src];
+    p.w = cur.w[src];
+    p.om = cur.om[src];
+#pragma unroll
+    for (int a = 0; a < NS; ++a) p.psi[a] = cur.psi[(size_t)a * cur.cap + src];
+    p.elem = cur.elem[src];
+    p.pid = cur.pid[src];
+    bool bad;
+    advance_particle<NS, true, kMulti>(M, EF, P, p, err, bad);
+    // barycentric neighbour walk from the old element
+    const int e0 = p.elem;
+    int e = e0, h = 0, ne = e0;
+    bool lost = false;
+#pragma unroll 1
+    for (;;) {
+        int next = -1;
+        int r = walk_test_fast(M, e, p.x, p.y, next);
+        if (r < 0) {
+            float lam[3];
+            r = walk_test(M, e, p.x, p.y, lam, next) ? 1 : 0;
+        }
+        if (r == 1) {
+            ne = e;
+            hops += h;
+            break;
+        }
+        if (next < 0 || h >= kHopCap) {
+            lost = true;
+            hops += next < 0 ? h : kHopCap + 1;
+            break;
+        }
+        e = next;
+        ++h;
+    }
+    if (lost) ne = e0;
+    if (lost || bad) {
+        err |= kErrLost;
+        atomicAdd(&status[1], 1ull);
+        atomicCAS(&status[2], ~0ull, (unsigned long long)p.pid);
+    }
+    nxt.x[i] = p.x;
+    nxt.y[i] = p.y;
+    nxt.u[i] = p.u;
+    nxt.v[i] = p.v;
+    nxt.w[i] = p.w;
+    nxt.om[i] = p.om;
+#pragma unroll
+    for (int a = 0; a < NS; ++a) nxt.psi[(size_t)a * nxt.cap + i] = p.psi[a];
+    nxt.elem[i] = ne;
+    nxt.pid[i] = p.pid;
+}
+
+// K1 variants (the autotuner picks one per context; all give bit-identical results): ABLK
+// threads per CTA, at least MINB CTAs per SM (the register cap), and either one particle per
+// thread over the whole grid or a persistent grid striding over ABLK-particle tiles.
+template <int NS, bool kMulti, int ABLK, int MINB, bool kPersist>
+__global__ void __launch_bounds__(ABLK, MINB)
 advance_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevState cur,
                const __grid_constant__ DevState nxt, const int* __restrict__ perm, const float* __restrict__ EF,
                const __grid_constant__ StepParams P, unsigned long long* __restrict__ status)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x;
     unsigned err = 0;
     int hops = 0;
-    if (i < cur.n) {
-        const int src = perm[i];
-        ParticleState<NS> p;
-        p.x = cur.x[src];
-        p.y = cur.y[src];
-        p.u = cur.u[src];
-        p.v = cur.v[src];
-        p.w = cur.w[src];
-        p.om = cur.om[src];
-#pragma unroll
-        for (int a = 0; a < NS; ++a) p.psi[a] = cur.psi[(size_t)a * cur.cap + src];
-        p.elem = cur.elem[src];
-        p.pid = cur.pid[src];
-        bool bad;
-        advance_particle<NS, true>(M, EF, P, p, err, bad);
-        // barycentric neighbour walk from the old element
-        const int e0 = p.elem;
-        int e = e0, h = 0, ne = e0;
-        bool lost = false;
+    const int64_t ntiles = (cur.n + ABLK - 1) / ABLK;
 #pragma unroll 1
-        for (;;) {
-            int next = -1;
-            int r = walk_test_fast(M, e, p.x, p.y, next);
-            if (r < 0) {
-                float lam[3];
-                r = walk_test(M, e, p.x, p.y, lam, next) ? 1 : 0;
-            }
-            if (r == 1) {
-                ne = e;
-                hops += h;
-                break;
-            }
-            if (next < 0 || h >= kHopCap) {
-                lost = true;
-                hops += next < 0 ? h : kHopCap + 1;
-                break;
-            }
-            e = next;
-            ++h;
-        }
-        if (lost) ne = e0;
-        if (lost || bad) {
-            err |= kErrLost;
-            atomicAdd(&status[1], 1ull);
-            atomicCAS(&status[2], ~0ull, (unsigned long long)p.pid);
-        }
-        nxt.x[i] = p.x;
-        nxt.y[i] = p.y;
-        nxt.u[i] = p.u;
-        nxt.v[i] = p.v;
-        nxt.w[i] = p.w;
-        nxt.om[i] = p.om;
-#pragma unroll
-        for (int a = 0; a < NS; ++a) nxt.psi[(size_t)a * nxt.cap + i] = p.psi[a];
-        nxt.elem[i] = ne;
-        nxt.pid[i] = p.pid;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += kPersist ? gridDim.x : ntiles) {
+        const int64_t i = tile * ABLK + threadIdx.x;
+        if (i < cur.n) advance_one<NS, kMulti>(M, cur, nxt, perm, EF, P, status, i, err, hops);
     }
     const unsigned e_or = __reduce_or_sync(kFull, err);
     const int h_sum = __reduce_add_sync(kFull, hops);
@@ -444,8 +459,8 @@ __global__ void particle_scatter_kernel(int64_t n, const uint16_t* __restrict__ 
 // ------------------------------------------------------------------------------------------
 // K2
 // ------------------------------------------------------------------------------------------
-template <int NS>
-__global__ void __launch_bounds__(256, 2) moments_kernel(const __grid_constant__ DevMesh M,
+template <int NS, int MBLK, int MMINB>
+__global__ void __launch_bounds__(MBLK, MMINB) moments_kernel(const __grid_constant__ DevMesh M,
                                                       const __grid_constant__ DevState S,
                                                       const int* __restrict__ perm, const int* __restrict__ kstart,
                                                       unsigned long long* __restrict__ node_acc,
@@ -548,6 +563,12 @@ __global__ void iota_kernel(int* __restrict__ p, int64_t n)
     if (i < n) p[i] = (int)i;
 }
 
+// the step counter of graph-replayed steps: set (add = 0) or advance (set = 0)
+__global__ void step_counter_kernel(unsigned long long* __restrict__ c, unsigned long long set, unsigned long long add)
+{
+    *c = add ? *c + add : set;
+}
+
 inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 cudaError_t scan_pair(const int* in0, int* out0, const int* in1, int* out1, int n, int* part, cudaStream_t st)
@@ -561,10 +582,57 @@ cudaError_t scan_pair(const int* in0, int* out0, const int* in1, int* out1, int 
     return cudaGetLastError();
 }
 
+int sm_count_cached()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+template <int NS, bool kMulti, int ABLK, int MINB, bool kPersist>
+void launch_advance_v(const DevMesh& m, const DevState& cur, const DevState& nxt, const int* perm, const float* ef,
+                      const StepParams& p, unsigned long long* status, cudaStream_t st)
+{
+    const int64_t ntiles = (cur.n + ABLK - 1) / ABLK;
+    const int64_t grid = kPersist ? std::min<int64_t>(ntiles, (int64_t)sm_count_cached() * MINB) : ntiles;
+    advance_kernel<NS, kMulti, ABLK, MINB, kPersist><<<(unsigned)grid, ABLK, 0, st>>>(m, cur, nxt, perm, ef, p, status);
+}
+
+template <int NS, bool kMulti>
+void launch_advance(int v, const DevMesh& m, const DevState& cur, const DevState& nxt, const int* perm,
+                    const float* ef, const StepParams& p, unsigned long long* status, cudaStream_t st)
+{
+    switch (v) {
+        case 1: launch_advance_v<NS, kMulti, 256, 6, false>(m, cur, nxt, perm, ef, p, status, st); break;
+        case 2: launch_advance_v<NS, kMulti, 128, 8, false>(m, cur, nxt, perm, ef, p, status, st); break;
+        case 3: launch_advance_v<NS, kMulti, 256, 4, true>(m, cur, nxt, perm, ef, p, status, st); break;
+        case 4: launch_advance_v<NS, kMulti, 256, 6, true>(m, cur, nxt, perm, ef, p, status, st); break;
+        default: launch_advance_v<NS, kMulti, 256, 4, false>(m, cur, nxt, perm, ef, p, status, st); break;
+    }
+}
+
+template <int NS>
+void launch_moments(int v, const DevMesh& m, const DevState& s, const int* perm, const int* kstart,
+                    unsigned long long* node_acc, unsigned long long* status, cudaStream_t st)
+{
+    const int64_t threads = (int64_t)m.n_tri * 32;
+    switch (v) {
+        case 1: moments_kernel<NS, 128, 4><<<nblocks(threads, 128), 128, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
+        case 2: moments_kernel<NS, 512, 1><<<nblocks(threads, 512), 512, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
+        case 3: moments_kernel<NS, 256, 3><<<nblocks(threads, 256), 256, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
+        default: moments_kernel<NS, 256, 2><<<nblocks(threads, 256), 256, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
+    }
+}
+
 template <int NS>
 cudaError_t run_pipeline(const DevMesh& m, const DevState& cur, const DevState& nxt, const float* fields,
                          const StepParams& p, PipeScratch& w, unsigned long long* node_acc, unsigned long long* status,
-                         cudaStream_t st, const cudaEvent_t* ev)
+                         cudaStream_t st, const cudaEvent_t* ev, const StepTune& tune)
 {
     const int64_t n = cur.n;
     if (n == 0) return cudaSuccess;
@@ -578,7 +646,8 @@ cudaError_t run_pipeline(const DevMesh& m, const DevState& cur, const DevState& 
     if (ev) cudaEventRecord(ev[0], st);
     constexpr int NQ4 = (22 + NS + 3) / 4;
     element_fields_kernel<NS><<<nblocks((int64_t)E * NQ4, 256), 256, 0, st>>>(m, fields, w.efields);
-    advance_kernel<NS><<<(unsigned)nblk, kBlk, 0, st>>>(m, cur, nxt, w.perm, w.efields, p, status);
+    if (m.n_comp > 1) launch_advance<NS, true>(tune.adv, m, cur, nxt, w.perm, w.efields, p, status, st);
+    else launch_advance<NS, false>(tune.adv, m, cur, nxt, w.perm, w.efields, p, status, st);
     if (ev) cudaEventRecord(ev[1], st);
     histogram_kernel<<<(unsigned)((nblk + kHWarps - 1) / kHWarps), 32 * kHWarps, 0, st>>>(
         nxt.elem, n, w.rrank, w.rec_key, w.rec_cnt, w.nrec, kcnt, krc, status);
@@ -589,7 +658,7 @@ cudaError_t run_pipeline(const DevMesh& m, const DevState& cur, const DevState& 
                                                                        w.rec_cnt, w.rec_off);
     particle_scatter_kernel<<<nblocks(n, 256 * kScatterPer), 256, 0, st>>>(n, w.rrank, w.rec_off, w.perm_new);
     if (ev) cudaEventRecord(ev[2], st);
-    moments_kernel<NS><<<nblocks((int64_t)E * 32, 256), 256, 0, st>>>(m, nxt, w.perm_new, w.kstart, node_acc, status);
+    launch_moments<NS>(tune.mom, m, nxt, w.perm_new, w.kstart, node_acc, status, st);
     if (ev) cudaEventRecord(ev[3], st);
     return cudaGetLastError();
 }
@@ -599,15 +668,23 @@ cudaError_t run_pipeline(const DevMesh& m, const DevState& cur, const DevState& 
 cudaError_t launch_pdf_step_pipeline(const DevMesh& m, const DevState& cur, const DevState& nxt, int ns,
                                      const float* fields, const StepParams& p, PipeScratch& w,
                                      unsigned long long* node_acc, unsigned long long* status, cudaStream_t st,
-                                     const cudaEvent_t* ev)
+                                     const cudaEvent_t* ev, const StepTune& tune)
 {
     switch (ns) {
-        case 1: return run_pipeline<1>(m, cur, nxt, fields, p, w, node_acc, status, st, ev);
-        case 2: return run_pipeline<2>(m, cur, nxt, fields, p, w, node_acc, status, st, ev);
-        case 3: return run_pipeline<3>(m, cur, nxt, fields, p, w, node_acc, status, st, ev);
-        case 4: return run_pipeline<4>(m, cur, nxt, fields, p, w, node_acc, status, st, ev);
+        case 1: return run_pipeline<1>(m, cur, nxt, fields, p, w, node_acc, status, st, ev, tune);
+        case 2: return run_pipeline<2>(m, cur, nxt, fields, p, w, node_acc, status, st, ev, tune);
+        case 3: return run_pipeline<3>(m, cur, nxt, fields, p, w, node_acc, status, st, ev, tune);
+        case 4: return run_pipeline<4>(m, cur, nxt, fields, p, w, node_acc, status, st, ev, tune);
         default: return cudaErrorInvalidValue;
     }
+}
+
+int sm_count() { return sm_count_cached(); }
+
+cudaError_t launch_step_counter(unsigned long long* c, unsigned long long set, unsigned long long add, cudaStream_t st)
+{
+    step_counter_kernel<<<1, 1, 0, st>>>(c, set, add);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_iota(int* p, int64_t n, cudaStream_t st)

@@ -474,17 +474,18 @@ __global__ void fields_kernel(const Fem F, int ns, int nfp, const double* __rest
 // nearest wall point of every geometric node: distance, wall edge and position on it (the edges
 // in order, each with its images one period to the left, in place and to the right; the first
 // strictly nearest point wins)
-__global__ void wall_distance_kernel(int N, const double* __restrict__ xy, const double* __restrict__ seg, int nseg,
-                                     double period, double* __restrict__ dist, int* __restrict__ wseg,
-                                     double* __restrict__ wt)
+__global__ void wall_distance_kernel(int N, const double* __restrict__ xy, const double* __restrict__ seg,
+                                     const int* __restrict__ seg_off, const int* __restrict__ ncomp, double period,
+                                     double* __restrict__ dist, int* __restrict__ wseg, double* __restrict__ wt)
 {
     const int nd = blockIdx.x * blockDim.x + threadIdx.x;
     if (nd >= N) return;
     const double px = xy[2 * nd], py = xy[2 * nd + 1];
     double best = 1e300, bt = 0.0;
-    int bs = 0;
+    const int c = ncomp[nd], s0 = seg_off[c], s1 = seg_off[c + 1];
+    int bs = s0;
     const int ni = period > 0.0 ? 1 : 0;
-    for (int s = 0; s < nseg; ++s) {
+    for (int s = s0; s < s1; ++s) {
         const double ax = seg[4 * s], ay = seg[4 * s + 1], tx = seg[4 * s + 2] - ax, ty = seg[4 * s + 3] - ay;
         const double tt = tx * tx + ty * ty;
         for (int im = -ni; im <= ni; ++im) {
@@ -499,7 +500,7 @@ __global__ void wall_distance_kernel(int N, const double* __restrict__ xy, const
             }
         }
     }
-    dist[nd] = nseg > 0 ? sqrt(best) : 0.0;
+    dist[nd] = s1 > s0 ? sqrt(best) : 0.0;
     wseg[nd] = bs;
     wt[nd] = bt;
 }
@@ -519,7 +520,9 @@ __global__ void features_kernel(const Fem F, const double* __restrict__ stats, i
     const double uu = st[4], uv = st[5], uw = st[6], vv = st[7], vw = st[8], ww = st[9], Om = st[10];
     const double k = 0.5 * (uu + vv + ww);
     double eps_w = 0.0;
-    if (F.nseg > 0) {
+    const int comp = F.ncomp[nd];
+    const bool walls = F.seg_off[comp + 1] > F.seg_off[comp];
+    if (walls) {
         const int s = F.wseg[nd];
         const double t = F.wt[nd];
         const double* sa = stats + (size_t)F.dof_node[F.dof[F.segn[2 * s]]] * nq;
@@ -545,7 +548,7 @@ __global__ void features_kernel(const Fem F, const double* __restrict__ stats, i
     f[4] = (float)b22;
     f[5] = (float)b12;
     f[6] = (float)(b11 * b11 + b22 * b22 + b33 * b33 + 2.0 * (b12 * b12 + b13 * b13 + b23 * b23));
-    f[7] = (float)(F.nseg > 0 ? log(fmax(eps_w, 1e-12) / fmax(k * Om, 1e-12)) : 0.0);
+    f[7] = (float)(walls ? log(fmax(eps_w, 1e-12) / fmax(k * Om, 1e-12)) : 0.0);
     if (!tgt) return;
     const float* o = fields + (size_t)nd * nfp;
     const double Omc = fmax(Om, 1e-12), kc = fmax(k, 1e-12), e = k * Om;
@@ -589,7 +592,8 @@ __global__ void fields_compare_kernel(const float* __restrict__ a, const float* 
 // ------------------------------------------------------------------------- host side
 
 cudaError_t fem_build(const double* node_xy, int N, const int32_t* tri, int E, const int32_t* tag,
-                      const std::vector<int32_t>& master, double period, Fem** out)
+                      const std::vector<int32_t>& master, const std::vector<int32_t>& node_comp, double period,
+                      Fem** out)
 {
     *out = nullptr;
     std::vector<int> dof(N), dof_node;
@@ -674,8 +678,10 @@ cudaError_t fem_build(const double* node_xy, int N, const int32_t* tri, int E, c
                 normal[2 * d + 1] += tx / len;
             }
         }
+    // wall edges grouped by component (components own contiguous element ranges, in order)
+    const int n_comp = node_comp.empty() ? 1 : *std::max_element(node_comp.begin(), node_comp.end()) + 1;
     std::vector<double> seg;
-    std::vector<int> segn;
+    std::vector<int> segn, seg_off(n_comp + 1, 0);
     for (int e = 0; e < E; ++e)
         for (int k = 0; k < 3; ++k) {
             const int t = tag[3 * e + k];
@@ -683,7 +689,11 @@ cudaError_t fem_build(const double* node_xy, int N, const int32_t* tri, int E, c
             const int a = tri[3 * e + k], b = tri[3 * e + (k + 1) % 3];
             seg.insert(seg.end(), {node_xy[2 * a], node_xy[2 * a + 1], node_xy[2 * b], node_xy[2 * b + 1]});
             segn.insert(segn.end(), {a, b});
+            ++seg_off[(node_comp.empty() ? 0 : node_comp[a]) + 1];
         }
+    for (int c = 0; c < n_comp; ++c) seg_off[c + 1] += seg_off[c];
+    std::vector<int> ncomp_v(N, 0);
+    for (int i = 0; i < N && !node_comp.empty(); ++i) ncomp_v[i] = node_comp[i];
     const std::vector<double> xy(node_xy, node_xy + 2 * (size_t)N);
     for (int d = 0; d < ndof; ++d)
         if (wall[d]) {
@@ -697,6 +707,7 @@ cudaError_t fem_build(const double* node_xy, int N, const int32_t* tri, int E, c
     F->E = E;
     F->N = N;
     F->nseg = (int)(seg.size() / 4);
+    F->n_comp = n_comp;
     F->period = period;
     if (seg.empty()) {
         seg.assign(4, 0.0);
@@ -709,7 +720,7 @@ cudaError_t fem_build(const double* node_xy, int N, const int32_t* tri, int E, c
         (e = upload(&F->col, col)) || (e = upload(&F->cptr, cptr)) || (e = upload(&F->cel, cel)) ||
         (e = upload(&F->Mval, Mval)) || (e = upload(&F->Kval, Kval)) || (e = upload(&F->wall, wall)) ||
         (e = upload(&F->normal, normal)) || (e = upload(&F->xy, xy)) || (e = upload(&F->seg, seg)) ||
-        (e = upload(&F->segn, segn)) || (e = cudaMalloc((void**)&F->wdist, sizeof(double) * std::max(1, N))) ||
+        (e = upload(&F->segn, segn)) || (e = upload(&F->seg_off, seg_off)) || (e = upload(&F->ncomp, ncomp_v)) || (e = cudaMalloc((void**)&F->wdist, sizeof(double) * std::max(1, N))) ||
         (e = cudaMalloc((void**)&F->wseg, sizeof(int) * std::max(1, N))) ||
         (e = cudaMalloc((void**)&F->wt, sizeof(double) * std::max(1, N))) ||
         (e = cudaMalloc((void**)&F->Aval, sizeof(double) * std::max(1, F->nnz))) ||
@@ -729,7 +740,7 @@ void fem_free(Fem* F)
     if (!F) return;
     void* ps[] = {F->dof, F->dof_node, F->edof, F->area, F->grad, F->de_ptr, F->de_el, F->darea, F->row, F->col,
                   F->cptr, F->cel, F->Mval, F->Kval, F->Aval, F->wall, F->normal, F->work, F->part, F->scal,
-                  F->xy, F->seg, F->segn, F->wdist, F->wseg, F->wt};
+                  F->xy, F->seg, F->segn, F->seg_off, F->ncomp, F->wdist, F->wseg, F->wt};
     for (void* p : ps) cudaFree(p);
     cudaFreeHost(F->scal_host);
     delete F;
@@ -889,8 +900,8 @@ cudaError_t surrogate_features(Fem& F, const double* stats, int ns, const float*
                                float* tgt, cudaStream_t st)
 {
     if (!F.has_wdist) {
-        wall_distance_kernel<<<blocks(F.N), 256, 0, st>>>(F.N, F.xy, F.seg, F.nseg, F.period, F.wdist, F.wseg,
-                                                          F.wt);
+        wall_distance_kernel<<<blocks(F.N), 256, 0, st>>>(F.N, F.xy, F.seg, F.seg_off, F.ncomp, F.period, F.wdist,
+                                                          F.wseg, F.wt);
         F.has_wdist = true;
     }
     features_kernel<<<blocks(F.N), 256, 0, st>>>(F, stats, nquant(ns), fields, nfields_padded(ns), C0, feat,

@@ -38,7 +38,10 @@ EXPORTS = ("lpdf_params_default", "lpdf_last_error", "lpdf_version", "lpdf_mesh_
            "lpdf_elliptic_relax_solve", "lpdf_ctx_set_timing", "lpdf_ctx_timings", "lpdf_tc_gemm_bf16",
            "lpdf_mlp_create", "lpdf_mlp_free", "lpdf_mlp_set_params", "lpdf_mlp_get_params", "lpdf_mlp_fit_norm",
            "lpdf_mlp_forward", "lpdf_mlp_gradient", "lpdf_mlp_train", "lpdf_surrogate_features",
-           "lpdf_mlp_set_policy", "lpdf_surrogate_relax_solve")
+           "lpdf_mlp_set_policy", "lpdf_surrogate_relax_solve", "lpdf_mesh_load_multi", "lpdf_ctx_set_components",
+           "lpdf_particles_init_multi", "lpdf_pdf_steps", "lpdf_ctx_set_tune", "lpdf_ctx_autotune")
+
+N_ADV_VARIANTS, N_MOM_VARIANTS = 5, 4
 
 MLP_IN, MLP_OUT, MLP_HIDDEN = 8, 7, 128
 MLP_NPARAMS = 35079
@@ -49,6 +52,13 @@ class LpdfError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
         self.code = code
+
+
+class Component(ctypes.Structure):
+    """lpdf_component: per-component seed and scalar sources of a multi-component mesh."""
+    _fields_ = [("seed", ctypes.c_uint64), ("n_sources", ctypes.c_int32),
+                ("src_x", ctypes.c_float * 8), ("src_y", ctypes.c_float * 8), ("src_r", ctypes.c_float * 8),
+                ("src_alpha", ctypes.c_int32 * 8)]
 
 
 class Params(ctypes.Structure):
@@ -116,6 +126,12 @@ def lib():
     L.lpdf_surrogate_features.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.lpdf_mlp_set_policy.argtypes = [vp, i32, ctypes.c_double]
     L.lpdf_surrogate_relax_solve.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, i32, vp, vp]
+    L.lpdf_mesh_load_multi.argtypes = [vp, i32, vp, i32, vp, i32, vp, vp, ctypes.c_double, vp]
+    L.lpdf_ctx_set_components.argtypes = [vp, vp, i32]
+    L.lpdf_particles_init_multi.argtypes = [vp, vp, vp, i32, vp]
+    L.lpdf_pdf_steps.argtypes = [vp, vp, u64, i32, vp]
+    L.lpdf_ctx_set_tune.argtypes = [vp, i32, i32]
+    L.lpdf_ctx_autotune.argtypes = [vp, vp, u64, i32, vp, vp, vp, vp]
     for name in EXPORTS:
         f = getattr(L, name)
         if f.restype is ctypes.c_int or (name not in ("lpdf_params_default", "lpdf_mesh_free", "lpdf_ctx_free",
@@ -165,7 +181,7 @@ def params_for(wk: "wl.Workload", **consts) -> Params:
 
 
 class Mesh:
-    """lpdf_mesh_load / lpdf_mesh_free."""
+    """lpdf_mesh_load (or lpdf_mesh_load_multi for a wl.MultiMesh) / lpdf_mesh_free."""
 
     def __init__(self, mesh: "wl.Mesh"):
         L = lib()
@@ -173,8 +189,17 @@ class Mesh:
         tri = np.ascontiguousarray(mesh.tri, dtype=np.int32)
         tag = np.ascontiguousarray(mesh.edge_tag, dtype=np.int32)
         h = ctypes.c_void_p()
-        _check(L.lpdf_mesh_load(_ptr(xy), xy.shape[0], _ptr(tri), tri.shape[0], _ptr(tag), float(mesh.period_x),
-                                ctypes.byref(h)))
+        node_off = getattr(mesh, "node_off", None)
+        if node_off is None:
+            _check(L.lpdf_mesh_load(_ptr(xy), xy.shape[0], _ptr(tri), tri.shape[0], _ptr(tag), float(mesh.period_x),
+                                    ctypes.byref(h)))
+            self.n_comp = 1
+        else:
+            no = np.ascontiguousarray(node_off, dtype=np.int32)
+            to = np.ascontiguousarray(mesh.tri_off, dtype=np.int32)
+            _check(L.lpdf_mesh_load_multi(_ptr(xy), xy.shape[0], _ptr(tri), tri.shape[0], _ptr(tag), len(no) - 1,
+                                          _ptr(no), _ptr(to), float(mesh.period_x), ctypes.byref(h)))
+            self.n_comp = len(no) - 1
         self.h = h
         self.mesh = mesh
         self.n_nodes, self.n_tri = xy.shape[0], tri.shape[0]
@@ -258,6 +283,37 @@ class Context:
 
     def particles_init(self, n_per_elem: int, node_init, m_erlang: int = 4, stream=None):
         _check(lib().lpdf_particles_init(self.h, int(n_per_elem), _ptr(node_init), int(m_erlang), _stream(stream)))
+
+    def particles_init_multi(self, n_per_elem, node_init, m_erlang: int = 4, stream=None):
+        """lpdf_particles_init_multi: n_per_elem[c] particles per element of component c."""
+        ppe = np.ascontiguousarray(n_per_elem, dtype=np.int32)
+        _check(lib().lpdf_particles_init_multi(self.h, _ptr(ppe), _ptr(node_init), int(m_erlang), _stream(stream)))
+
+    def set_components(self, comps):
+        """lpdf_ctx_set_components: comps = [(seed, [(x, y, r, alpha), ...]), ...], one per component."""
+        arr = (Component * len(comps))()
+        for k, (seed, sources) in enumerate(comps):
+            arr[k].seed = int(seed)
+            arr[k].n_sources = len(sources)
+            for i, (sx, sy, sr, sa) in enumerate(sources):
+                arr[k].src_x[i], arr[k].src_y[i], arr[k].src_r[i], arr[k].src_alpha[i] = sx, sy, sr, sa
+        _check(lib().lpdf_ctx_set_components(self.h, arr, len(comps)))
+
+    def pdf_steps(self, node_fields, step0: int, nsteps: int, stream=None):
+        """lpdf_pdf_steps: nsteps steps from step0, pairs of steps replayed from a CUDA graph."""
+        _check(lib().lpdf_pdf_steps(self.h, _ptr(node_fields), int(step0), int(nsteps), _stream(stream)))
+
+    def set_tune(self, adv: int, mom: int):
+        _check(lib().lpdf_ctx_set_tune(self.h, int(adv), int(mom)))
+
+    def autotune(self, node_fields, step0: int, steps_per_trial: int = 3, stream=None):
+        """lpdf_ctx_autotune: returns ((adv, mom), trial milliseconds, steps used)."""
+        choice = np.zeros(2, dtype=np.int32)
+        ms = np.zeros(N_ADV_VARIANTS + N_MOM_VARIANTS, dtype=np.float64)
+        used = ctypes.c_int32()
+        _check(lib().lpdf_ctx_autotune(self.h, _ptr(node_fields), int(step0), int(steps_per_trial), _ptr(choice),
+                                       _ptr(ms), ctypes.byref(used), _stream(stream)))
+        return (int(choice[0]), int(choice[1])), ms, used.value
 
     def set_state(self, st, stream=None):
         """st: dict/State of torch CUDA tensors (on_device=1) or numpy arrays (host)."""

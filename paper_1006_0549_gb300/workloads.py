@@ -453,3 +453,70 @@ def mlp_random_data(n: int, seed: int, n_in: int = 8, n_out: int = 7):
     mix = rng.standard_normal((n_in, n_out)) / np.sqrt(n_in)
     tgt = np.sin(z @ mix) + 0.3 * (z[:, :n_out] ** 2 if n_out <= n_in else 0.0) + np.arange(n_out)
     return feat.astype(np.float32), tgt.astype(np.float32)
+
+
+@dataclasses.dataclass
+class MultiMesh(Mesh):
+    """Several independent meshes held as one (lpdf_mesh_load_multi): nodes and elements of
+    component c are [node_off[c], node_off[c + 1]) and [tri_off[c], tri_off[c + 1])."""
+    node_off: np.ndarray = None
+    tri_off: np.ndarray = None
+    parts: list = None
+
+
+def union_mesh(meshes) -> MultiMesh:
+    """The disjoint union of meshes that share one x period (or none): node ids offset per part."""
+    period = meshes[0].period_x
+    assert all(m.period_x == period for m in meshes), "components must share the x period"
+    node_off = np.zeros(len(meshes) + 1, dtype=np.int64)
+    tri_off = np.zeros(len(meshes) + 1, dtype=np.int64)
+    for k, m in enumerate(meshes):
+        node_off[k + 1] = node_off[k] + m.n_nodes
+        tri_off[k + 1] = tri_off[k] + m.n_tri
+    xy = np.concatenate([m.node_xy for m in meshes])
+    tri = np.concatenate([m.tri + node_off[k] for k, m in enumerate(meshes)]).astype(np.int32)
+    tag = np.concatenate([m.edge_tag for m in meshes]).astype(np.int32)
+    box = (min(m.box[0] for m in meshes), max(m.box[1] for m in meshes),
+           min(m.box[2] for m in meshes), max(m.box[3] for m in meshes))
+    return MultiMesh(xy, tri, tag, period, box, meshes[0].kind, 0, 0, node_off, tri_off, list(meshes))
+
+
+def stack_node_arrays(parts) -> np.ndarray:
+    """Per-node arrays of the components, one after the other (the union's node order)."""
+    return np.ascontiguousarray(np.concatenate(parts))
+
+
+@dataclasses.dataclass
+class BatchedWorkload:
+    name: str
+    mesh: MultiMesh
+    n_per_elem: list          # per component
+    seeds: list               # per component
+    sources: list             # per component: [(x, y, r, alpha)]
+    ns: int
+    nu: float
+    dt: float
+
+    @property
+    def n_particles(self) -> int:
+        return int(sum((self.mesh.tri_off[k + 1] - self.mesh.tri_off[k]) * p
+                       for k, p in enumerate(self.n_per_elem)))
+
+
+def batched_channels(n: int = 64, tri_range=(2000, 40000), ppe_range=(50, 400), seed: int = 1006054904,
+                     source_y=(0.2, 1.8)) -> BatchedWorkload:
+    """n independent channel ensembles of uneven size: component k has about E_k ~ U[tri_range]
+    triangles (nx : ny = 5 : 2, so E = 2 nx ny = 5 ny^2), ppe_k ~ U{ppe_range} particles per
+    element, seed = seed + k and one scalar line source (a disc of radius 0.02 at x = 0.25) at a
+    height ~ U[source_y]; the draws come from one generator seeded with `seed`."""
+    rng = np.random.default_rng(seed)
+    meshes, ppe, seeds, srcs = [], [], [], []
+    for k in range(n):
+        E = rng.uniform(*tri_range)
+        ny = max(2, int(round(np.sqrt(E / 5.0))))
+        nx = max(3, int(round(2.5 * ny)))
+        meshes.append(channel_mesh(nx, ny, seed + k))
+        ppe.append(int(rng.integers(ppe_range[0], ppe_range[1] + 1)))
+        seeds.append(seed + k)
+        srcs.append([(0.25, float(np.float32(rng.uniform(*source_y))), 0.02, 0)])
+    return BatchedWorkload(f"channels-x{n}", union_mesh(meshes), ppe, seeds, srcs, 1, 1.0 / 180.0, 1e-3)
