@@ -173,7 +173,9 @@ def run_gpu(args, rank, world, dist):
     wk, mesh, ctx, fields = build_workload(rank, args.ppe)
     P = ctx.n
     stream = torch.cuda.current_stream()
-    step = 0
+    # launch configuration of the step's kernels, chosen by the library's autotuner on this
+    # ensemble (every configuration gives bit-identical results)
+    tune, tune_ms, step = ctx.autotune(fields, 0, steps_per_trial=3)
     for _ in range(args.warmup):
         ctx.pdf_step(fields, step)
         step += 1
@@ -252,7 +254,55 @@ def run_gpu(args, rank, world, dist):
              "note": "lpdf_elliptic_relax_solve: recovery, FP64 elliptic-relaxation and pressure CGs, "
                      "host-timed (it synchronises); not included in the step"}
     return dict(P=P, total_ms=total_ms, per=per, kernel_ms=kernel_ms, clocks=clk.summary(), hops=hops, e2e_s=e2e_s,
-                h2d=int(h_fields.numel() * 4), d2h=int(h_stats.numel() * 8), wk=wk, solve=solve)
+                h2d=int(h_fields.numel() * 4), d2h=int(h_stats.numel() * 8), wk=wk, solve=solve,
+                tune={"advance_variant": tune[0], "moments_variant": tune[1],
+                      "trial_ms_per_step": [round(float(x), 4) for x in tune_ms]})
+
+
+def run_batched(steps: int, warmup: int):
+    """64 independent channel ensembles of uneven size (meshes of 2k-40k triangles, 50-400
+    particles per element, own seeds and source heights) in one multi-component mesh: autotuned
+    launch configuration, steps replayed from CUDA graphs, node fields fixed."""
+    import torch
+    from paper_1006_0549_gb300 import lpdf, workloads as wl
+    t = time.perf_counter()
+    wk = wl.batched_channels()
+    gm = lpdf.Mesh(wk.mesh)
+    params = lpdf.make_params(nu=wk.nu, dt=wk.dt, seed=wk.seeds[0], ns=wk.ns)
+    n = wk.n_particles
+    ctx = lpdf.Context(gm, params, n)
+    ctx.set_components(list(zip(wk.seeds, wk.sources)))
+    parts = wk.mesh.parts
+    init = torch.from_numpy(wl.stack_node_arrays([wl.node_init_fields(m) for m in parts])).cuda()
+    ctx.particles_init_multi(wk.n_per_elem, init)
+    F = torch.from_numpy(wl.stack_node_arrays([wl.synthetic_node_fields(m, wk.ns, seed=5 + k)
+                                               for k, m in enumerate(parts)])).cuda()
+    ctx.status()
+    setup_s = time.perf_counter() - t
+    tune, tune_ms, step = ctx.autotune(F, 0, steps_per_trial=3)
+    ctx.pdf_steps(F, step, warmup)
+    step += warmup
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    ctx.pdf_steps(F, step, steps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    rc, status = ctx.status(raise_on_error=False)
+    if rc != lpdf.LPDF_OK:
+        raise RuntimeError(f"batched step status {rc}: {status}")
+    return {"workload": f"{wk.name}: {len(parts)} channel ensembles in one multi-component mesh",
+            "triangles": int(wk.mesh.n_tri), "particles": int(n),
+            "triangles_per_component": [int(m.n_tri) for m in (min(parts, key=lambda m: m.n_tri),
+                                                               max(parts, key=lambda m: m.n_tri))],
+            "particles_per_element": [int(min(wk.n_per_elem)), int(max(wk.n_per_elem))],
+            "steps": steps, "ms_per_step": ms / steps, "value": n * steps / (ms * 1e-3),
+            "unit": "particle-updates/s", "graph": "pairs of steps replayed from one CUDA graph",
+            "tune": {"advance_variant": tune[0], "moments_variant": tune[1],
+                     "trial_ms_per_step": [round(float(x), 3) for x in tune_ms]},
+            "setup_s": setup_s}
 
 
 def run_surrogate(wk, train_steps: int, run_steps: int, check_every: int, threshold: float):
@@ -350,6 +400,7 @@ def main():
     ap.add_argument("--surrogate-train-steps", type=int, default=100,
                     help="plain steps whose fields train the surrogate (0: no surrogate report)")
     ap.add_argument("--surrogate-run-steps", type=int, default=40)
+    ap.add_argument("--batched", type=int, default=1, help="1: also report the 64-ensemble batched step")
     ap.add_argument("--ppe", type=int, default=500,
                     help="particles per element (500 = the 25M-particle workload; smaller only for profiling)")
     args = ap.parse_args()
@@ -420,6 +471,7 @@ def main():
     step_gbs = BYTES_PER_UPDATE * P / (ms_step * 1e-3) / 1e9
     traffic = ncu_traffic(P)
     cpu_n, cpu_dt = cpu_baseline_sample(r["wk"], args.cpu_sample)
+    batched = run_batched(args.steps, args.warmup) if args.batched else None
     surrogate = None
     if args.surrogate_train_steps > 0:
         surrogate = run_surrogate(r["wk"], args.surrogate_train_steps, args.surrogate_run_steps, 10, 0.02)
@@ -446,6 +498,8 @@ def main():
         "gpu_launches": K * LAUNCHES_PER_STEP,
         "gridpoint_solve": r["solve"],
         "surrogate": surrogate,
+        "batched": batched,
+        "tune": r["tune"],
     }
     print(json.dumps(line))
     if dist is not None:
