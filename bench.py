@@ -68,10 +68,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(n_particles: int):
-    """DRAM bytes (read + write) of one advance-kernel launch, from the committed summary of an
-    ncu capture of a smaller case scaled by the particles a launch processes; None when the
-    summary was taken on other kernel sources."""
+def ncu_traffic(n_particles: int, variant: int):
+    """DRAM bytes (read + write) of one advance-kernel launch of the given launch variant, from the
+    committed summary of ncu captures of a smaller case, scaled by the particles a launch
+    processes; None when the summary was taken on other kernel sources or lacks the variant."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     d = {}
@@ -82,8 +82,10 @@ def ncu_traffic(n_particles: int):
                 d[k.strip()] = v.strip()
     if d.get("kernel_source_hash") != kernel_source_hash():
         return None
-    per_particle = (float(d["dram__bytes_read.sum"]) + float(d["dram__bytes_write.sum"])) / float(d["particles"])
-    return per_particle * n_particles
+    key = f"variant {variant} bytes per particle"
+    if key not in d:
+        return None
+    return float(d[key]) * n_particles
 
 
 class ClockSampler:
@@ -175,7 +177,11 @@ def run_gpu(args, rank, world, dist):
     stream = torch.cuda.current_stream()
     # launch configuration of the step's kernels, chosen by the library's autotuner on this
     # ensemble (every configuration gives bit-identical results)
-    tune, tune_ms, step = ctx.autotune(fields, 0, steps_per_trial=3)
+    if args.tune == "auto":
+        tune, tune_ms, step = ctx.autotune(fields, 0, steps_per_trial=4, rounds=2)
+    else:
+        tune, tune_ms, step = tuple(int(v) for v in args.tune.split(",")), [], 0
+        ctx.set_tune(*tune)
     for _ in range(args.warmup):
         ctx.pdf_step(fields, step)
         step += 1
@@ -279,7 +285,7 @@ def run_batched(steps: int, warmup: int):
                                                for k, m in enumerate(parts)])).cuda()
     ctx.status()
     setup_s = time.perf_counter() - t
-    tune, tune_ms, step = ctx.autotune(F, 0, steps_per_trial=3)
+    tune, tune_ms, step = ctx.autotune(F, 0, steps_per_trial=3, rounds=2)
     ctx.pdf_steps(F, step, warmup)
     step += warmup
     torch.cuda.synchronize()
@@ -401,6 +407,8 @@ def main():
                     help="plain steps whose fields train the surrogate (0: no surrogate report)")
     ap.add_argument("--surrogate-run-steps", type=int, default=40)
     ap.add_argument("--batched", type=int, default=1, help="1: also report the 64-ensemble batched step")
+    ap.add_argument("--tune", default="auto",
+                    help="launch configuration of the step: 'auto' (the library's autotuner) or 'adv,mom'")
     ap.add_argument("--ppe", type=int, default=500,
                     help="particles per element (500 = the 25M-particle workload; smaller only for profiling)")
     args = ap.parse_args()
@@ -469,7 +477,7 @@ def main():
     # the advance kernel reads and writes the whole state: the step's algorithmic bytes
     achieved = BYTES_PER_UPDATE * P / (kms["advance"] * 1e-3) / 1e9
     step_gbs = BYTES_PER_UPDATE * P / (ms_step * 1e-3) / 1e9
-    traffic = ncu_traffic(P)
+    traffic = ncu_traffic(P, r["tune"]["advance_variant"])
     cpu_n, cpu_dt = cpu_baseline_sample(r["wk"], args.cpu_sample)
     batched = run_batched(args.steps, args.warmup) if args.batched else None
     surrogate = None

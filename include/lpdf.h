@@ -229,16 +229,18 @@ int lpdf_pdf_steps(lpdf_ctx* ctx, const float* node_fields, uint64_t step0, int3
  *   mom (moments kernel, a warp per element): 0 = 256 threads, >= 2 CTAs per SM; 1 = 128, >= 4;
  *       2 = 512, >= 1; 3 = 256, >= 3.
  * lpdf_ctx_set_tune sets it (LPDF_ERR_ARG outside those ranges). lpdf_ctx_autotune times every
- * advance variant, then every moments variant with the best advance variant, each for one
+ * advance variant, then every moments variant with the best advance variant. A trial is one
  * warm-up step and steps_per_trial timed steps (CUDA events on `stream`) of this context's own
- * ensemble and fields, and keeps the fastest. The trial steps are real steps, numbered from
- * step0: *steps_used (host, may be NULL) tells how many were taken. choice (host, 2 ints, may
- * be NULL) = (adv, mom); trial_ms (host, 9 doubles, may be NULL) = milliseconds per step of
- * each trial (5 advance, then 4 moments variants). sync.
+ * ensemble and fields; every variant is tried once per round, `rounds` rounds interleaved, and
+ * a variant's time is its fastest trial (the ensemble keeps changing while it is timed). The
+ * fastest variants are kept. The trial steps are real steps, numbered from step0: *steps_used
+ * (host, may be NULL) tells how many were taken. choice (host, 2 ints, may be NULL) = (adv,
+ * mom); trial_ms (host, 9 doubles, may be NULL) = milliseconds per step of each variant (5
+ * advance, then 4 moments variants). sync.
  * ------------------------------------------------------------------------------------- */
 int lpdf_ctx_set_tune(lpdf_ctx* ctx, int32_t adv, int32_t mom);
 int lpdf_ctx_autotune(lpdf_ctx* ctx, const float* node_fields, uint64_t step0, int32_t steps_per_trial,
-                      int32_t* choice, double* trial_ms, int32_t* steps_used, void* stream);
+                      int32_t rounds, int32_t* choice, double* trial_ms, int32_t* steps_used, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * lpdf_sort -- physically re-buckets the ensemble by element: afterwards the particles of every

@@ -773,11 +773,12 @@ int lpdf_ctx_set_tune(lpdf_ctx* c, int32_t adv, int32_t mom)
     return LPDF_OK;
 }
 
-int lpdf_ctx_autotune(lpdf_ctx* c, const float* node_fields, uint64_t step0, int32_t steps_per_trial, int32_t* choice,
-                      double* trial_ms, int32_t* steps_used, void* stream)
+int lpdf_ctx_autotune(lpdf_ctx* c, const float* node_fields, uint64_t step0, int32_t steps_per_trial, int32_t rounds,
+                      int32_t* choice, double* trial_ms, int32_t* steps_used, void* stream)
 {
     if (!c || !node_fields) return fail(LPDF_ERR_ARG, "autotune: NULL argument");
-    if (steps_per_trial < 1) return fail(LPDF_ERR_ARG, "autotune: steps_per_trial = %d", steps_per_trial);
+    if (steps_per_trial < 1 || rounds < 1)
+        return fail(LPDF_ERR_ARG, "autotune: steps_per_trial = %d, rounds = %d", steps_per_trial, rounds);
     const cudaStream_t st = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
@@ -801,25 +802,29 @@ int lpdf_ctx_autotune(lpdf_ctx* c, const float* node_fields, uint64_t step0, int
     const bool timing = c->timing;
     c->timing = false;
     StepTune best = c->tune;
-    double best_ms = 1e300;
-    for (int v = 0; v < kAdvVariants && rc == LPDF_OK; ++v) {
-        double ms = 0.0;
-        rc = trial(v, best.mom, ms);
-        if (trial_ms) trial_ms[v] = ms;
-        if (rc == LPDF_OK && ms < best_ms) {
-            best_ms = ms;
-            best.adv = v;
+    // every variant once per round, the rounds interleaved; a variant's time is its fastest trial
+    double t_adv[kAdvVariants], t_mom[kMomVariants];
+    for (double& t : t_adv) t = 1e300;
+    for (double& t : t_mom) t = 1e300;
+    for (int r = 0; r < rounds && rc == LPDF_OK; ++r)
+        for (int v = 0; v < kAdvVariants && rc == LPDF_OK; ++v) {
+            double ms = 0.0;
+            rc = trial(v, best.mom, ms);
+            t_adv[v] = std::min(t_adv[v], ms);
         }
-    }
-    best_ms = 1e300;
-    for (int v = 0; v < kMomVariants && rc == LPDF_OK; ++v) {
-        double ms = 0.0;
-        rc = trial(best.adv, v, ms);
-        if (trial_ms) trial_ms[kAdvVariants + v] = ms;
-        if (rc == LPDF_OK && ms < best_ms) {
-            best_ms = ms;
-            best.mom = v;
+    for (int v = 0; v < kAdvVariants; ++v)
+        if (t_adv[v] < t_adv[best.adv]) best.adv = v;
+    for (int r = 0; r < rounds && rc == LPDF_OK; ++r)
+        for (int v = 0; v < kMomVariants && rc == LPDF_OK; ++v) {
+            double ms = 0.0;
+            rc = trial(best.adv, v, ms);
+            t_mom[v] = std::min(t_mom[v], ms);
         }
+    for (int v = 0; v < kMomVariants; ++v)
+        if (t_mom[v] < t_mom[best.mom]) best.mom = v;
+    if (trial_ms) {
+        for (int v = 0; v < kAdvVariants; ++v) trial_ms[v] = t_adv[v];
+        for (int v = 0; v < kMomVariants; ++v) trial_ms[kAdvVariants + v] = t_mom[v];
     }
     c->timing = timing;
     cudaEventDestroy(e0);

@@ -147,8 +147,9 @@ __device__ __forceinline__ bool edge_owns(float ax, float ay, float bx, float by
 // (px, py) (exact inside tests in the element's own frame; lam = its barycentrics, from the
 // orientation values); otherwise `next` = the neighbour across the exit edge (the edge with the
 // most negative orientation value, the lowest local index on ties), -1 for a wall. In a
-// periodic image frame the test only navigates.
-__device__ __forceinline__ bool walk_test(const DevMesh& M, int e, float px, float py, float lam[3], int& next)
+// periodic image frame the test only navigates. Out of line: the step calls it only when the
+// certified fast test is undecided, and its registers stay out of the step's hot loop.
+static __device__ __noinline__ bool walk_test(const DevMesh& M, int e, float px, float py, float lam[3], int& next)
 {
     const float4 X = __ldg(&M.ex[e]);
     const float4 Y = __ldg(&M.ey[e]);
@@ -461,9 +462,6 @@ __device__ __forceinline__ void advance_particle(const DevMesh& M, const float* 
         src_r = cp.src_r;
         src_alpha = cp.src_alpha;
     }
-    // linear shape-function interpolation of the node fields
-    float Fi[NFP];
-    interpolate_fields<NS, kElementTable>(M, F, e, x, y, Fi);
     // Wiener increments: Philox blocks 0 and 1 of counter (pid, step, 0<<16 | block)
     uint32_t step_lo = P.step_lo, step_hi = P.step_hi;
     if (P.step_dev) {
@@ -477,6 +475,10 @@ __device__ __forceinline__ void advance_particle(const DevMesh& M, const float* 
     box_muller(r0.x, r0.y, z0, z1);
     box_muller(r0.z, r0.w, z2, z3);
     box_muller(r1.x, r1.y, z4, z5);
+    // linear shape-function interpolation of the node fields (after the random numbers: fewer
+    // registers live across the loads)
+    float Fi[NFP];
+    interpolate_fields<NS, kElementTable>(M, F, e, x, y, Fi);
     const float dW1 = P.sdt * z0, dW2 = P.sdt * z1;
     const float c0e = sqrtf(fmaxf(Fi[LPDF_F_C0EPS], 0.0f));
     const float Ur = u - Fi[LPDF_F_U + 0], Vr = v - Fi[LPDF_F_U + 1], Wr = w - Fi[LPDF_F_U + 2];

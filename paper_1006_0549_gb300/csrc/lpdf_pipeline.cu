@@ -68,6 +68,28 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int& total
 // ------------------------------------------------------------------------------------------
 // K1
 // ------------------------------------------------------------------------------------------
+// The state streams through once per step: its loads skip L1 (which keeps the element field
+// rows and mesh records that the particles of an element share) and its stores are marked
+// streaming.
+__device__ __forceinline__ float ld_stream(const float* p)
+{
+    float v;
+    asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ int ld_stream(const int* p)
+{
+    int v;
+    asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p)
+{
+    uint32_t v;
+    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
 // one particle: position i of the next buffer takes particle perm[i] of the current one
 template <int NS, bool kMulti>
 __device__ __forceinline__ void advance_one(const DevMesh& M, const DevState& cur, const DevState& nxt,
@@ -75,18 +97,18 @@ __device__ __forceinline__ void advance_one(const DevMesh& M, const DevState& cu
                                             const StepParams& P, unsigned long long* __restrict__ status, int64_t i,
                                             unsigned& err, int& hops)
 {
-    const int src = perm[i];
+    const int src = ld_stream(perm + i);
     ParticleState<NS> p;
-    p.x = cur.x[src];
-    p.y = cur.y[src];
-    p.u = cur.u[src];
-    p.v = cur.v[src];
-    p.w = cur.w[src];
-    p.om = cur.om[src];
+    p.x = ld_stream(cur.x + src);
+    p.y = ld_stream(cur.y + src);
+    p.u = ld_stream(cur.u + src);
+    p.v = ld_stream(cur.v + src);
+    p.w = ld_stream(cur.w + src);
+    p.om = ld_stream(cur.om + src);
 #pragma unroll
-    for (int a = 0; a < NS; ++a) p.psi[a] = cur.psi[(size_t)a * cur.cap + src];
-    p.elem = cur.elem[src];
-    p.pid = cur.pid[src];
+    for (int a = 0; a < NS; ++a) p.psi[a] = ld_stream(cur.psi + (size_t)a * cur.cap + src);
+    p.elem = ld_stream(cur.elem + src);
+    p.pid = ld_stream(cur.pid + src);
     bool bad;
     advance_particle<NS, true, kMulti>(M, EF, P, p, err, bad);
     // barycentric neighbour walk from the old element
@@ -120,16 +142,16 @@ __device__ __forceinline__ void advance_one(const DevMesh& M, const DevState& cu
         atomicAdd(&status[1], 1ull);
         atomicCAS(&status[2], ~0ull, (unsigned long long)p.pid);
     }
-    nxt.x[i] = p.x;
-    nxt.y[i] = p.y;
-    nxt.u[i] = p.u;
-    nxt.v[i] = p.v;
-    nxt.w[i] = p.w;
-    nxt.om[i] = p.om;
+    __stcs(nxt.x + i, p.x);
+    __stcs(nxt.y + i, p.y);
+    __stcs(nxt.u + i, p.u);
+    __stcs(nxt.v + i, p.v);
+    __stcs(nxt.w + i, p.w);
+    __stcs(nxt.om + i, p.om);
 #pragma unroll
-    for (int a = 0; a < NS; ++a) nxt.psi[(size_t)a * nxt.cap + i] = p.psi[a];
-    nxt.elem[i] = ne;
-    nxt.pid[i] = p.pid;
+    for (int a = 0; a < NS; ++a) __stcs(nxt.psi + (size_t)a * nxt.cap + i, p.psi[a]);
+    __stcs(nxt.elem + i, ne);
+    __stcs(nxt.pid + i, p.pid);
 }
 
 // K1 variants (the autotuner picks one per context; all give bit-identical results): ABLK

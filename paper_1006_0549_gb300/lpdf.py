@@ -131,7 +131,7 @@ def lib():
     L.lpdf_particles_init_multi.argtypes = [vp, vp, vp, i32, vp]
     L.lpdf_pdf_steps.argtypes = [vp, vp, u64, i32, vp]
     L.lpdf_ctx_set_tune.argtypes = [vp, i32, i32]
-    L.lpdf_ctx_autotune.argtypes = [vp, vp, u64, i32, vp, vp, vp, vp]
+    L.lpdf_ctx_autotune.argtypes = [vp, vp, u64, i32, i32, vp, vp, vp, vp]
     for name in EXPORTS:
         f = getattr(L, name)
         if f.restype is ctypes.c_int or (name not in ("lpdf_params_default", "lpdf_mesh_free", "lpdf_ctx_free",
@@ -306,13 +306,13 @@ class Context:
     def set_tune(self, adv: int, mom: int):
         _check(lib().lpdf_ctx_set_tune(self.h, int(adv), int(mom)))
 
-    def autotune(self, node_fields, step0: int, steps_per_trial: int = 3, stream=None):
-        """lpdf_ctx_autotune: returns ((adv, mom), trial milliseconds, steps used)."""
+    def autotune(self, node_fields, step0: int, steps_per_trial: int = 3, rounds: int = 2, stream=None):
+        """lpdf_ctx_autotune: returns ((adv, mom), per-variant milliseconds per step, steps used)."""
         choice = np.zeros(2, dtype=np.int32)
         ms = np.zeros(N_ADV_VARIANTS + N_MOM_VARIANTS, dtype=np.float64)
         used = ctypes.c_int32()
-        _check(lib().lpdf_ctx_autotune(self.h, _ptr(node_fields), int(step0), int(steps_per_trial), _ptr(choice),
-                                       _ptr(ms), ctypes.byref(used), _stream(stream)))
+        _check(lib().lpdf_ctx_autotune(self.h, _ptr(node_fields), int(step0), int(steps_per_trial), int(rounds),
+                                       _ptr(choice), _ptr(ms), ctypes.byref(used), _stream(stream)))
         return (int(choice[0]), int(choice[1])), ms, used.value
 
     def set_state(self, st, stream=None):

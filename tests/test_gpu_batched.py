@@ -161,9 +161,9 @@ def test_autotune_picks_a_valid_configuration(torch_cuda):
     um = wl.union_mesh(meshes)
     Fd = torch.from_numpy(wl.stack_node_arrays(fields)).cuda()
     gm, ctx = _batched_ctx(torch, um, seeds, sources, inits)
-    (adv, mom), ms, used = ctx.autotune(Fd, 0, steps_per_trial=2)
+    (adv, mom), ms, used = ctx.autotune(Fd, 0, steps_per_trial=2, rounds=2)
     assert 0 <= adv < lpdf.N_ADV_VARIANTS and 0 <= mom < lpdf.N_MOM_VARIANTS
-    assert used == (lpdf.N_ADV_VARIANTS + lpdf.N_MOM_VARIANTS) * 3
+    assert used == (lpdf.N_ADV_VARIANTS + lpdf.N_MOM_VARIANTS) * 3 * 2
     assert np.all(ms > 0.0)
     assert ms[adv] == ms[:lpdf.N_ADV_VARIANTS].min()
     assert ms[lpdf.N_ADV_VARIANTS + mom] == ms[lpdf.N_ADV_VARIANTS:].min()
