@@ -57,7 +57,7 @@ def measured_peaks():
 
 # the sources of the advance kernel: a traffic figure taken on other sources is stale
 KERNEL_SOURCES = ("lpdf_pipeline.cu", "lpdf_device.cuh", "lpdf_internal.h")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "advance_kernel_channel5M_traffic.txt")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "advance_kernel_channel25M_traffic.txt")
 
 
 def kernel_source_hash():
@@ -70,8 +70,9 @@ def kernel_source_hash():
 
 def ncu_traffic(n_particles: int, variant: int):
     """DRAM bytes (read + write) of one advance-kernel launch of the given launch variant, from the
-    committed summary of ncu captures of a smaller case, scaled by the particles a launch
-    processes; None when the summary was taken on other kernel sources or lacks the variant."""
+    committed summary of one-pass ncu captures of this workload (bytes per particle times the
+    particles of the launch); None when the summary was taken on other kernel sources or lacks
+    the variant."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     d = {}
@@ -265,6 +266,54 @@ def run_gpu(args, rank, world, dist):
                       "trial_ms_per_step": [round(float(x), 4) for x in tune_ms]})
 
 
+def run_cavity(steps: int, warmup: int, peak: float):
+    """The lid-driven cavity (199,712 triangles, 100 particles per element, four scalars from point
+    sources, lid velocity 1, nu = 1e-4): the same step on the second configuration, autotuned,
+    with fixed synthetic node fields of the cavity's structure."""
+    import torch
+    from paper_1006_0549_gb300 import lpdf, workloads as wl
+    wk = wl.cavity_20m()
+    gm = lpdf.Mesh(wk.mesh)
+    params = lpdf.params_for(wk)
+    ctx = lpdf.Context(gm, params, wk.n_particles)
+    ctx.particles_init(wk.n_per_elem, torch.from_numpy(wl.node_init_fields(wk.mesh)).cuda(), m_erlang=4)
+    F = torch.from_numpy(wl.synthetic_node_fields(wk.mesh, wk.ns, seed=5)).cuda()
+    ctx.status()
+    tune, tune_ms, step = ctx.autotune(F, 0, steps_per_trial=4, rounds=2)
+    for _ in range(warmup):
+        ctx.pdf_step(F, step)
+        step += 1
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ctx.set_timing(True)
+    ctx.timings()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        ctx.pdf_step(F, step)
+        step += 1
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    kms, ks = ctx.timings()
+    ctx.set_timing(False)
+    rc, status = ctx.status(raise_on_error=False)
+    if rc != lpdf.LPDF_OK:
+        raise RuntimeError(f"cavity step status {rc}: {status}")
+    P = ctx.n
+    # algorithmic bytes: read x, y, u, v, w, omega, psi[ns], elem, pid; write all but pid (92 B at ns = 4)
+    bytes_per_update = (8 + wk.ns) * 4 + (7 + wk.ns) * 4
+    adv = kms[0] / ks
+    achieved = bytes_per_update * P / (adv * 1e-3) / 1e9
+    return {"workload": f"{wk.name}: lid-driven cavity, {wk.mesh.n_tri} triangles, {wk.n_per_elem} particles "
+                        f"per element, {wk.ns} scalars", "particles": int(P), "steps": steps,
+            "ms_per_step": ms / steps, "value": P * steps / (ms * 1e-3), "unit": "particle-updates/s",
+            "kernels_ms_per_step": {"advance": adv, "rebucket": kms[1] / ks, "moments": kms[2] / ks},
+            "advance_roofline": {"bytes_per_update": bytes_per_update, "achieved_gbs": achieved, "frac": achieved / peak},
+            "mean_walk_hops": float(status[3]) / (P * steps),
+            "tune": {"advance_variant": tune[0], "moments_variant": tune[1]}}
+
+
 def run_batched(steps: int, warmup: int):
     """64 independent channel ensembles of uneven size (meshes of 2k-40k triangles, 50-400
     particles per element, own seeds and source heights) in one multi-component mesh: autotuned
@@ -407,6 +456,7 @@ def main():
                     help="plain steps whose fields train the surrogate (0: no surrogate report)")
     ap.add_argument("--surrogate-run-steps", type=int, default=40)
     ap.add_argument("--batched", type=int, default=1, help="1: also report the 64-ensemble batched step")
+    ap.add_argument("--cavity", type=int, default=1, help="1: also report the 20M-particle cavity step")
     ap.add_argument("--tune", default="auto",
                     help="launch configuration of the step: 'auto' (the library's autotuner) or 'adv,mom'")
     ap.add_argument("--ppe", type=int, default=500,
@@ -480,6 +530,7 @@ def main():
     traffic = ncu_traffic(P, r["tune"]["advance_variant"])
     cpu_n, cpu_dt = cpu_baseline_sample(r["wk"], args.cpu_sample)
     batched = run_batched(args.steps, args.warmup) if args.batched else None
+    cavity = run_cavity(args.steps, args.warmup, peak) if args.cavity else None
     surrogate = None
     if args.surrogate_train_steps > 0:
         surrogate = run_surrogate(r["wk"], args.surrogate_train_steps, args.surrogate_run_steps, 10, 0.02)
@@ -507,6 +558,7 @@ def main():
         "gridpoint_solve": r["solve"],
         "surrogate": surrogate,
         "batched": batched,
+        "cavity": cavity,
         "tune": r["tune"],
     }
     print(json.dumps(line))
