@@ -46,6 +46,8 @@ def lib():
                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.oracle_mesh_free.argtypes = [vp]
         L.oracle_mesh_neighbors.argtypes = [vp, vp]
+        L.oracle_mesh_edge_walls.restype = ctypes.c_int
+        L.oracle_mesh_edge_walls.argtypes = [vp]
         L.oracle_mesh_masters.argtypes = [vp, vp]
         L.oracle_philox4x32_10.argtypes = [vp, vp, vp]
         L.oracle_normals6.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, vp]
@@ -111,6 +113,11 @@ class OracleMesh:
             lib().oracle_mesh_free(self.ptr)
         except Exception:
             pass
+
+    @property
+    def edge_walls(self) -> bool:
+        """True when some wall edge is off the sides of the bounding box (walls mirrored in the walk)."""
+        return bool(lib().oracle_mesh_edge_walls(self.ptr))
 
     def neighbors(self):
         out = np.empty((self.n_tri, 3), dtype=np.int32)

@@ -43,6 +43,7 @@
 #include <string.h>
 
 #define ORACLE_HOP_CAP 64
+#define ORACLE_REFL_CAP 8
 #define ORACLE_MAX_SOURCES 8
 #define ORACLE_MAX_NS 8
 
@@ -184,6 +185,7 @@ typedef struct {
     double* cx;
     double period;
     double x0, x1, y0, y1;
+    int edge_walls;   /* 1: some wall edge is off the sides of the bounding box */
 } OMesh;
 
 void oracle_mesh_free(OMesh* m)
@@ -258,9 +260,21 @@ OMesh* oracle_mesh_new(const double* node_xy, int n_nodes, const int* tri, int n
                 if (m->x[j] == x0 && m->y[j] == m->y[i]) { m->master[i] = j; break; }
         }
     }
+    /* walls off the sides of the bounding box: mirror across wall edges during location */
+    m->edge_walls = 0;
+    for (int e = 0; e < n_tri; ++e)
+        for (int k = 0; k < 3; ++k) {
+            if (tag[3 * e + k] != 1 && tag[3 * e + k] != 2) continue;
+            int a = tri[3 * e + k], b = tri[3 * e + (k + 1) % 3];
+            double ax = m->x[a], ay = m->y[a], bx = m->x[b], by = m->y[b];
+            int on_side = (ax == bx && (ax == x0 || ax == x1)) || (ay == by && (ay == y0 || ay == y1));
+            if (!on_side) m->edge_walls = 1;
+        }
     free(cnt); free(fill); free(lst);
     return m;
 }
+
+int oracle_mesh_edge_walls(const OMesh* m) { return m->edge_walls; }
 
 int oracle_mesh_neighbors(const OMesh* m, int* out)
 {
@@ -291,11 +305,18 @@ static int edge_in(double ax, double ay, double bx, double by, double px, double
     return edge_included(ax, ay, bx, by);
 }
 
+/* inside-or-owned test of element e: a point on an edge belongs to the element for which the
+ * edge is "top-left", except that with walls off the frame (edge_walls) a point on a wall edge
+ * belongs to its element (those walls are closed) */
 int oracle_inside(const OMesh* m, int e, double px, double py)
 {
     for (int k = 0; k < 3; ++k) {
         int a = m->tri[3 * e + k], b = m->tri[3 * e + (k + 1) % 3];
-        if (!edge_in(m->x[a], m->y[a], m->x[b], m->y[b], px, py)) return 0;
+        if (m->edge_walls && m->nbr[3 * e + k] < 0) {
+            if (oracle_orient2d_sign(m->x[a], m->y[a], m->x[b], m->y[b], px, py) < 0) return 0;
+        } else if (!edge_in(m->x[a], m->y[a], m->x[b], m->y[b], px, py)) {
+            return 0;
+        }
     }
     return 1;
 }
@@ -319,7 +340,8 @@ static double image_shift(const OMesh* m, int e, double px)
 }
 
 /* Barycentric neighbour walk: start at `start`; while p is not inside, leave through the edge
- * whose barycentric is most negative (ties: lowest local index). Inside tests are exact and
+ * whose barycentric is most negative among the interior edges it lies beyond, else through the
+ * most negative wall edge (ties: lowest local index). Inside tests are exact and
  * only made in the element's own frame (image shift 0); in a shifted frame the walk only
  * navigates. Returns the owner, -1 on a wall exit (cannot happen in a convex domain), -2 when
  * the hop cap is reached. */
@@ -338,7 +360,8 @@ int oracle_locate_walk(const OMesh* m, int start, double px, double py, int* hop
             double val = (bx - ax) * (py - ay) - (by - ay) * (qx - ax);
             int in;
             if (sh == 0.0) {
-                in = edge_in(ax, ay, bx, by, qx, py);
+                in = (m->edge_walls && m->nbr[3 * e + k] < 0) ? oracle_orient2d_sign(ax, ay, bx, by, qx, py) >= 0
+                                                               : edge_in(ax, ay, bx, by, qx, py);
             } else {
                 /* shifted frame: navigation only; a point of the domain is never beyond a wall */
                 all_in = 0;
@@ -346,7 +369,9 @@ int oracle_locate_walk(const OMesh* m, int start, double px, double py, int* hop
             }
             if (!in) {
                 all_in = 0;
-                if (best < 0 || val < bestv) { best = k; bestv = val; }
+                /* the exit: the most negative across an interior edge, else across a wall */
+                int nk = m->nbr[3 * e + k] >= 0, nb = best >= 0 && m->nbr[3 * e + best] >= 0;
+                if (best < 0 || (nk && !nb) || (nk == nb && val < bestv)) { best = k; bestv = val; }
             }
         }
         if (sh == 0.0 && all_in) { if (hops_out) *hops_out = h; return e; }
@@ -361,6 +386,67 @@ int oracle_locate_walk(const OMesh* m, int start, double px, double py, int* hop
     }
     if (hops_out) *hops_out = ORACLE_HOP_CAP + 1;
     return -2;
+}
+
+/* The walk of oracle_locate_walk for walls of any shape: when it would leave through a wall edge
+ * (edge k of element e, from node a to node b), the FP32 position is mirrored across the edge's
+ * line -- t = ((p - a).d)/(d.d), foot f = a + t d, p' = 2 f - p with d = b - a, in FP64, then
+ * rounded to FP32 -- the velocity becomes 2 U_w - U (U_w = (lid_u, 0, 0) on a moving-wall edge,
+ * else 0), and the walk goes on from e; at most ORACLE_REFL_CAP mirrorings. Returns the owner or
+ * a negative value as oracle_locate_walk. */
+int oracle_locate_walk_reflect(const OMesh* m, int start, float* px, float* py, double* U, double* V, double* W,
+                               double lid_u, int* hops_out, int* nref_out)
+{
+    int e = start, nref = 0, h = 0;
+    for (;;) {
+        double sh = image_shift(m, e, *px);
+        double qx = *px + sh;
+        int best = -1;
+        double bestv = 0.0;
+        int all_in = 1;
+        for (int k = 0; k < 3; ++k) {
+            int a = m->tri[3 * e + k], b = m->tri[3 * e + (k + 1) % 3];
+            double ax = m->x[a], ay = m->y[a], bx = m->x[b], by = m->y[b];
+            double val = (bx - ax) * ((double)*py - ay) - (by - ay) * (qx - ax);
+            int in;
+            if (sh == 0.0) {
+                in = (m->edge_walls && m->nbr[3 * e + k] < 0) ? oracle_orient2d_sign(ax, ay, bx, by, qx, *py) >= 0
+                                                               : edge_in(ax, ay, bx, by, qx, *py);
+            } else {
+                all_in = 0;
+                in = (val > 0.0) || (m->nbr[3 * e + k] < 0);
+            }
+            if (!in) {
+                all_in = 0;
+                /* the exit: the most negative across an interior edge, else across a wall */
+                int nk = m->nbr[3 * e + k] >= 0, nb = best >= 0 && m->nbr[3 * e + best] >= 0;
+                if (best < 0 || (nk && !nb) || (nk == nb && val < bestv)) { best = k; bestv = val; }
+            }
+        }
+        if (sh == 0.0 && all_in) { *hops_out = h; *nref_out = nref; return e; }
+        if (best < 0) {
+            for (int k = 0; k < 3; ++k) if (m->tag[3 * e + k] == 3) { best = k; break; }
+            if (best < 0) best = 0;
+        }
+        int n = m->nbr[3 * e + best];
+        if (n < 0) {
+            if (nref >= ORACLE_REFL_CAP) { *hops_out = h; *nref_out = nref; return -1; }
+            int a = m->tri[3 * e + best], b = m->tri[3 * e + (best + 1) % 3];
+            double dx = m->x[b] - m->x[a], dy = m->y[b] - m->y[a];
+            double t = (((double)*px - m->x[a]) * dx + ((double)*py - m->y[a]) * dy) / (dx * dx + dy * dy);
+            double fx = m->x[a] + t * dx, fy = m->y[a] + t * dy;
+            *px = (float)(2.0 * fx - (double)*px);
+            *py = (float)(2.0 * fy - (double)*py);
+            *U = (m->tag[3 * e + best] == 2 ? 2.0 * lid_u : 0.0) - *U;
+            *V = -*V;
+            *W = -*W;
+            ++nref;
+            continue;
+        }
+        if (h >= ORACLE_HOP_CAP) { *hops_out = ORACLE_HOP_CAP + 1; *nref_out = nref; return -2; }
+        e = n;
+        ++h;
+    }
 }
 
 /* barycentric coordinates of p in element e (element's own frame), FP64 */
@@ -478,7 +564,7 @@ long oracle_pdf_step(const OMesh* m, const OParams* p, const float* fields, int 
             qx -= k * m->period;
         }
         int nref = 0;
-        for (int it = 0; it < 8; ++it) {
+        for (int it = 0; it < 8 && !m->edge_walls; ++it) {
             if (qy < m->y0) { qy = 2.0 * m->y0 - qy; Un = -Un; Vn = -Vn; Wn = -Wn; ++nref; }
             else if (qy > m->y1) { qy = 2.0 * m->y1 - qy; Un = 2.0 * p->lid_u - Un; Vn = -Vn; Wn = -Wn; ++nref; }
             else if (!periodic && qx < m->x0) { qx = 2.0 * m->x0 - qx; Un = -Un; Vn = -Vn; Wn = -Wn; ++nref; }
@@ -487,11 +573,19 @@ long oracle_pdf_step(const OMesh* m, const OParams* p, const float* fields, int 
         }
         float pxf = (float)qx, pyf = (float)qy;
         const float x0f = (float)m->x0, x1f = (float)m->x1, y1f = (float)m->y1;
-        if (pxf >= x1f) pxf = periodic ? x0f : nextafterf(x1f, -INFINITY);
-        if (pyf >= y1f) pyf = nextafterf(y1f, -INFINITY);
+        if (!m->edge_walls) {
+            if (pxf >= x1f) pxf = periodic ? x0f : nextafterf(x1f, -INFINITY);
+            if (pyf >= y1f) pyf = nextafterf(y1f, -INFINITY);
+        } else if (periodic && pxf >= x1f) {
+            pxf = x0f;
+        }
         /* point location */
         int hops = 0, ne;
-        if (locate_mode == 1) {
+        if (m->edge_walls) {
+            /* walls of any shape: mirrored across the wall edge through which the walk leaves */
+            ne = oracle_locate_walk_reflect(m, e, &pxf, &pyf, &Un, &Vn, &Wn, p->lid_u, &hops, &nref);
+            if (locate_mode == 2 && ne >= 0 && oracle_locate_brute(m, pxf, pyf) != ne) ne = -3;
+        } else if (locate_mode == 1) {
             ne = oracle_locate_brute(m, pxf, pyf);
         } else {
             ne = oracle_locate_walk(m, e, pxf, pyf, &hops);

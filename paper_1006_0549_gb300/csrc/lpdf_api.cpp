@@ -270,6 +270,7 @@ int build_mesh(const double* node_xy, int32_t n_nodes, const int32_t* tri, int32
                 return fail(LPDF_ERR_MESH, "directed edge %u->%u appears twice", a, b);
         }
     std::vector<std::pair<double, int64_t>> left_edges, right_edges;   // keyed by min y
+    bool edge_walls = false;
     for (int e = 0; e < n_tri; ++e)
         for (int k = 0; k < 3; ++k) {
             const uint32_t a = (uint32_t)tri[3 * e + k], b = (uint32_t)tri[3 * e + (k + 1) % 3];
@@ -284,6 +285,15 @@ int build_mesh(const double* node_xy, int32_t n_nodes, const int32_t* tri, int32
             }
             if (tag == LPDF_EDGE_INTERIOR)
                 return fail(LPDF_ERR_MESH, "element %d edge %d is a boundary edge tagged interior", e, k);
+            if (tag == LPDF_EDGE_WALL || tag == LPDF_EDGE_MOVING_WALL) {
+                if (tag == LPDF_EDGE_MOVING_WALL) en[4 * e + 3] |= (8 << k);   // bit 3 + k: moving wall
+                // a wall edge off the sides of its component's frame makes the mesh "edge walls"
+                const int c = ecomp[e];
+                const double ax = node_xy[2 * a], ay = node_xy[2 * a + 1], bx = node_xy[2 * b], by = node_xy[2 * b + 1];
+                const bool on_side = (ax == bx && (ax == fr[4 * c] || ax == fr[4 * c + 1])) ||
+                                     (ay == by && (ay == fr[4 * c + 2] || ay == fr[4 * c + 3]));
+                if (!on_side) edge_walls = true;
+            }
             if (tag == LPDF_EDGE_PERIODIC) {
                 if (!periodic) return fail(LPDF_ERR_MESH, "periodic edge without period_x");
                 const double ax = node_xy[2 * a], bx = node_xy[2 * b];
@@ -342,6 +352,7 @@ int build_mesh(const double* node_xy, int32_t n_nodes, const int32_t* tri, int32
     d.x0 = (float)x0; d.x1 = (float)x1; d.y0 = (float)y0; d.y1 = (float)y1;
     d.periodic = periodic ? 1 : 0;
     d.n_comp = n_comp;
+    d.edge_walls = edge_walls ? 1 : 0;
     std::vector<float> cf(4 * (size_t)n_comp);
     for (size_t q = 0; q < cf.size(); ++q) cf[q] = (float)fr[q];
     d.period = periodic ? (float)period_x : 0.0f;

@@ -146,7 +146,8 @@ __device__ __forceinline__ bool edge_owns(float ax, float ay, float bx, float by
 // One test of the barycentric neighbour walk at element e: true if e is the unique owner of
 // (px, py) (exact inside tests in the element's own frame; lam = its barycentrics, from the
 // orientation values); otherwise `next` = the neighbour across the exit edge (the edge with the
-// most negative orientation value, the lowest local index on ties), -1 for a wall. In a
+// most negative orientation value, the lowest local index on ties), -1 - k for a wall edge k
+// (with edge walls a point on a wall edge is inside: those walls are closed). In a
 // periodic image frame the test only navigates. Out of line: the step calls it only when the
 // certified fast test is undecided, and its registers stay out of the step's hot loop.
 static __device__ __noinline__ bool walk_test(const DevMesh& M, int e, float px, float py, float lam[3], int& next)
@@ -173,10 +174,15 @@ static __device__ __noinline__ bool walk_test(const DevMesh& M, int e, float px,
             const int a = k, b = (k + 1) % 3;
             int s;
             vv[k] = orient_sign(xs[a], ys[a], xs[b], ys[b], px, py, s);
-            const bool in = s > 0 || (s == 0 && edge_owns(xs[a], ys[a], xs[b], ys[b]));
+            // with edge walls a point on a wall edge belongs to the element (walls are closed);
+            // otherwise the domain is the half-open frame and the top-left rule decides
+            const bool in = s > 0 || (s == 0 && ((M.edge_walls && nb[k] < 0) || edge_owns(xs[a], ys[a], xs[b], ys[b])));
             if (!in) {
                 all_in = false;
-                if (best < 0 || vv[k] < bestv) { best = k; bestv = vv[k]; }
+                // the exit: the most negative across an interior edge, else across a wall
+                const bool better = best < 0 || (nb[k] >= 0 && nb[best] < 0) ||
+                                    ((nb[k] >= 0) == (nb[best] >= 0) && vv[k] < bestv);
+                if (better) { best = k; bestv = vv[k]; }
             }
         }
         if (all_in) {
@@ -198,17 +204,48 @@ static __device__ __noinline__ bool walk_test(const DevMesh& M, int e, float px,
         if (best < 0) best = (N.w & 1) ? 0 : (N.w & 2) ? 1 : (N.w & 4) ? 2 : 0;
     }
     next = best == 0 ? N.x : (best == 1 ? N.y : N.z);
+    if (next < 0) next = -1 - best;   // a wall: -1 - (the exit edge)
     return false;
+}
+
+// The most negative lambda (vertex a) of the fast walk test lies across a wall: leave through the
+// most negative interior edge that is certainly crossed instead; the wall (next = -1 - its edge)
+// only when no interior edge can be crossed; -1 (undecided) when an interior edge is within its
+// rounding bound. Out of line: the step reaches it only at walls.
+static __device__ __noinline__ int fast_wall_exit(float l0, float l1, float l2, float E0, float E1, float E2, int4 N,
+                                                  int a, int& next)
+{
+    const float lv[3] = {l0, l1, l2}, ev[3] = {E0, E1, E2};
+    const int nv[3] = {N.y, N.z, N.x};
+    int b = -1;
+    for (int q = 0; q < 3; ++q) {
+        if (nv[q] < 0) continue;
+        if (lv[q] < -ev[q]) {
+            if (b < 0 || lv[q] < lv[b]) b = q;
+        } else if (!(lv[q] > ev[q])) {
+            return -1;
+        }
+    }
+    if (b >= 0) {
+        next = nv[b];
+        return 0;
+    }
+    next = -1 - (a == 2 ? 0 : a + 1);
+    return 0;
 }
 
 // The walk test in the affine barycentric form relative to vertex 0, with a certified error
 // bound: 1 = (px, py) is strictly inside e; 0 = it is certainly outside, leave through `next`
-// (the edge opposite the most negative lambda; -1 for a wall); -1 = undecided (within the
-// rounding bound of an edge, or in a periodic image frame): the caller runs walk_test.
+// (the edge opposite the most negative certainly negative lambda across an interior edge; if
+// only walls are crossed, -1 - k for the wall edge k of the most negative one); -1 = undecided
+// (within the rounding bound of an edge, or in a periodic image frame): the caller runs
+// walk_test. Preferring interior exits keeps the walk inside a non-convex domain: a point of the
+// domain can lie beyond the line of some wall edge, never beyond every negative edge's line.
 // Bound: with u = 2^-24, dx = fl(px - x_v0) (x_v0 exact in FP32) and the coefficients rounded
 // from FP64, |lambda_a' - lambda_a| <= 4.01 u (|b_a dx| + |g_a dy|) for a = 1, 2, and for
 // lambda_0 = 1 - lambda_1 - lambda_2 that sum plus 2 u (1 + |lambda_1| + |lambda_2|); the
 // constants below carry a margin for the rounding of the bounds themselves.
+template <bool kWalls = false>
 __device__ __forceinline__ int walk_test_fast(const DevMesh& M, int e, float px, float py, int& next)
 {
     const float4 A = __ldg(&M.ea[e]);
@@ -223,16 +260,36 @@ __device__ __forceinline__ int walk_test_fast(const DevMesh& M, int e, float px,
     const float E2 = 3.0e-7f * (fabsf(t2) + fabsf(s2)) + 1e-30f;
     const float E0 = E1 + E2 + 1.5e-7f * (1.0f + fabsf(l1) + fabsf(l2));
     if (l0 > E0 && l1 > E1 && l2 > E2) return 1;
-    // the most negative lambda, lowest index on ties
+    // the most negative lambda, lowest index on ties; vertex a is opposite edge (a + 1) % 3
+    // (edge k runs from vertex k to vertex k + 1)
     int a = 0;
     float lm = l0;
     if (l1 < lm) { a = 1; lm = l1; }
     if (l2 < lm) { a = 2; lm = l2; }
     const float Ea = a == 0 ? E0 : (a == 1 ? E1 : E2);
     if (!(lm < -Ea)) return -1;
-    // vertex a is opposite edge (a + 1) % 3 (edge k runs from vertex k to vertex k + 1)
     next = a == 0 ? N.y : (a == 1 ? N.z : N.x);
+    if (next >= 0) return 0;
+    if (kWalls) return fast_wall_exit(l0, l1, l2, E0, E1, E2, N, a, next);
+    next = -1 - (a == 2 ? 0 : a + 1);   // a wall: -1 - (the exit edge)
     return 0;
+}
+
+// Mirror image of (px, py) across the line of edge k of element e (FP32, every operation rounded
+// once in this order): t = ((p - a).d) / (d.d), foot f = a + t d, p' = 2 f - p, d = b - a.
+static __device__ __noinline__ void mirror_across_edge(const DevMesh& M, int e, int k, float& px, float& py)
+{
+    const float4 X = __ldg(&M.ex[e]);
+    const float4 Y = __ldg(&M.ey[e]);
+    const float xs[3] = {X.x, X.y, X.z}, ys[3] = {Y.x, Y.y, Y.z};
+    const int b = k == 2 ? 0 : k + 1;
+    const float dx = __fsub_rn(xs[b], xs[k]), dy = __fsub_rn(ys[b], ys[k]);
+    const float qx = __fsub_rn(px, xs[k]), qy = __fsub_rn(py, ys[k]);
+    const float t = __fdiv_rn(__fadd_rn(__fmul_rn(qx, dx), __fmul_rn(qy, dy)),
+                              __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)));
+    const float fx = __fadd_rn(xs[k], __fmul_rn(t, dx)), fy = __fadd_rn(ys[k], __fmul_rn(t, dy));
+    px = __fsub_rn(__fmul_rn(2.0f, fx), px);
+    py = __fsub_rn(__fmul_rn(2.0f, fy), py);
 }
 
 // The whole walk from element e: the owner of (px, py) (and its barycentrics), -1 on a wall
@@ -243,7 +300,7 @@ __device__ __forceinline__ int locate_walk(const DevMesh& M, int e, float px, fl
     for (int h = 0; h <= kHopCap; ++h) {
         int next;
         if (walk_test(M, e, px, py, lam, next)) { hops = h; return e; }
-        if (next < 0) { hops = h; return -1; }
+        if (next < 0) { hops = h; return -1; }   // (the caller starts inside the domain)
         e = next;
     }
     hops = kHopCap + 1;
@@ -386,6 +443,28 @@ __device__ __forceinline__ bool in_source(float px, float py, float sx, float sy
     return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) < __fmul_rn(r, r);
 }
 
+// psi_alpha <- 1 inside the concentrated sources (discs) of `sp` (the step's parameters, or a
+// component's: both carry n_src, src_x, src_y, src_r, src_alpha), on the final FP32 position
+template <int NS, class SP>
+__device__ __forceinline__ void apply_sources(const SP& sp, float px, float py, float* psi)
+{
+    for (int q = 0; q < sp.n_src; ++q)
+        if (in_source(px, py, sp.src_x[q], sp.src_y[q], sp.src_r[q])) {
+#pragma unroll
+            for (int a = 0; a < NS; ++a)
+                if (a == sp.src_alpha[q]) psi[a] = 1.0f;
+        }
+}
+
+// the sources of the particle's component (a multi-component mesh), or the step's
+template <int NS, bool kGeneral>
+__device__ __forceinline__ void particle_sources(const DevMesh& M, const StepParams& P, int e, float px, float py,
+                                                 float* psi)
+{
+    if (kGeneral && M.n_comp > 1) apply_sources<NS>(P.comp[__ldg(&M.ecomp[e])], px, py, psi);
+    else apply_sources<NS>(P, px, py, psi);
+}
+
 // Interpolated node fields at the particle, two sources:
 //   kElementTable = false: F is the node table (n_nodes x nfp); the P1 shape functions of the
 //                          element weight its three node rows;
@@ -430,10 +509,11 @@ __device__ __forceinline__ void interpolate_fields(const DevMesh& M, const float
 }
 
 // On return p holds the new state except the element, which is the walk's start: the old
-// element, or 0 when the old one is outside the mesh (`bad`). kMulti: the mesh holds several
-// independent components; the particle's component (that of its element) gives the frame, the
-// Philox key and the sources.
-template <int NS, bool kElementTable = false, bool kMulti = false>
+// element, or 0 when the old one is outside the mesh (`bad`). kGeneral: the mesh may hold several
+// independent components (the particle's component, that of its element, gives the frame, the
+// Philox key and the sources) and walls off the frame (mirrored in the walk, not here); without
+// it, one component with walls on the frame's sides.
+template <int NS, bool kElementTable = false, bool kGeneral = false>
 __device__ __forceinline__ void advance_particle(const DevMesh& M, const float* __restrict__ F, const StepParams& P,
                                                  ParticleState<NS>& p, unsigned& err, bool& bad)
 {
@@ -443,24 +523,15 @@ __device__ __forceinline__ void advance_particle(const DevMesh& M, const float* 
     const int e = bad ? 0 : p.elem;
     float fx0 = M.x0, fx1 = M.x1, fy0 = M.y0, fy1 = M.y1;
     uint32_t key0 = P.key0, key1 = P.key1;
-    int n_src = P.n_src;
-    const float *src_x = P.src_x, *src_y = P.src_y, *src_r = P.src_r;
-    const int* src_alpha = P.src_alpha;
-    if (kMulti) {
+    if (kGeneral && M.n_comp > 1) {
         const int c = __ldg(&M.ecomp[e]);
         const float4 fr = __ldg(&M.cframe[c]);
         fx0 = fr.x;
         fx1 = fr.y;
         fy0 = fr.z;
         fy1 = fr.w;
-        const CompParams& cp = P.comp[c];
-        key0 = cp.key0;
-        key1 = cp.key1;
-        n_src = cp.n_src;
-        src_x = cp.src_x;
-        src_y = cp.src_y;
-        src_r = cp.src_r;
-        src_alpha = cp.src_alpha;
+        key0 = P.comp[c].key0;
+        key1 = P.comp[c].key1;
     }
     // Wiener increments: Philox blocks 0 and 1 of counter (pid, step, 0<<16 | block)
     uint32_t step_lo = P.step_lo, step_hi = P.step_hi;
@@ -507,24 +578,24 @@ __device__ __forceinline__ void advance_particle(const DevMesh& M, const float* 
         else if (qx >= fx1) qx -= M.period;
         if (qx < fx0 || qx >= fx1) qx -= floorf((qx - fx0) / M.period) * M.period;   // moves > one period
     }
+    if (!(kGeneral && M.edge_walls)) {
+        // walls on the frame's sides: mirror at the frame (edge walls are mirrored in the walk)
 #pragma unroll 1
-    for (int it = 0; it < 8; ++it) {
-        if (qy < fy0) { qy = 2.0f * fy0 - qy; un = -un; vn = -vn; wn = -wn; }
-        else if (qy > fy1) { qy = 2.0f * fy1 - qy; un = 2.0f * P.lid_u - un; vn = -vn; wn = -wn; }
-        else if (!M.periodic && qx < fx0) { qx = 2.0f * fx0 - qx; un = -un; vn = -vn; wn = -wn; }
-        else if (!M.periodic && qx > fx1) { qx = 2.0f * fx1 - qx; un = -un; vn = -vn; wn = -wn; }
-        else break;
-    }
-    // half-open domain [x0, x1) x [y0, y1)
-    if (qx >= fx1) qx = M.periodic ? fx0 : nextafterf(fx1, -CUDART_INF_F);
-    if (qy >= fy1) qy = nextafterf(fy1, -CUDART_INF_F);
-    // concentrated scalar sources
-    for (int q = 0; q < n_src; ++q)
-        if (in_source(qx, qy, src_x[q], src_y[q], src_r[q])) {
-#pragma unroll
-            for (int a = 0; a < NS; ++a)
-                if (a == src_alpha[q]) p.psi[a] = 1.0f;
+        for (int it = 0; it < 8; ++it) {
+            if (qy < fy0) { qy = 2.0f * fy0 - qy; un = -un; vn = -vn; wn = -wn; }
+            else if (qy > fy1) { qy = 2.0f * fy1 - qy; un = 2.0f * P.lid_u - un; vn = -vn; wn = -wn; }
+            else if (!M.periodic && qx < fx0) { qx = 2.0f * fx0 - qx; un = -un; vn = -vn; wn = -wn; }
+            else if (!M.periodic && qx > fx1) { qx = 2.0f * fx1 - qx; un = -un; vn = -vn; wn = -wn; }
+            else break;
         }
+        // half-open domain [x0, x1) x [y0, y1)
+        if (qx >= fx1) qx = M.periodic ? fx0 : nextafterf(fx1, -CUDART_INF_F);
+        if (qy >= fy1) qy = nextafterf(fy1, -CUDART_INF_F);
+    } else if (M.periodic && qx >= fx1) {
+        qx = fx0;
+    }
+    // concentrated scalar sources (with edge walls: after the walk, on the mirrored position)
+    if (!(kGeneral && M.edge_walls)) particle_sources<NS, kGeneral>(M, P, e, qx, qy, p.psi);
     if (!(isfinite(un) && isfinite(vn) && isfinite(wn) && isfinite(omn) && isfinite(qx) && isfinite(qy)))
         err |= kErrNonFinite;
     p.x = qx;

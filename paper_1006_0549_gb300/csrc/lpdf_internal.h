@@ -13,6 +13,7 @@
 namespace lpdf {
 
 constexpr int kHopCap = 64;
+constexpr int kReflCap = 8;    // wall mirrorings of one particle in one step (edge walls)
 constexpr int kMaxNS = LPDF_MAX_SCALARS;
 // Moment sums are accumulated as 64-bit fixed point with 32 fractional bits: integer addition
 // is associative, so the sums do not depend on the order in which CTAs and warps add them.
@@ -43,6 +44,9 @@ struct DevMesh {
     int n_comp = 1;
     int* ecomp = nullptr;
     float4* cframe = nullptr;
+    // 0: every wall edge lies on the frame's sides (walls are handled by mirroring at the frame);
+    // 1: walls of any shape, mirrored across the wall edge through which the walk leaves
+    int edge_walls = 0;
 };
 
 // per-component Philox key and scalar sources of a multi-component ensemble

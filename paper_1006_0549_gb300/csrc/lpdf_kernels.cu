@@ -44,8 +44,12 @@ __global__ void particles_init_kernel(const __grid_constant__ DevMesh M, const _
             fx1 = fr.y;
             fy1 = fr.w;
         }
-        if (px >= fx1) px = M.periodic ? fx0 : nextafterf(fx1, -CUDART_INF_F);
-        if (py >= fy1) py = nextafterf(fy1, -CUDART_INF_F);
+        if (!M.edge_walls) {
+            if (px >= fx1) px = M.periodic ? fx0 : nextafterf(fx1, -CUDART_INF_F);
+            if (py >= fy1) py = nextafterf(fy1, -CUDART_INF_F);
+        } else if (M.periodic && px >= fx1) {
+            px = fx0;
+        }
         int hops = 0;
         float lw[3];
         int ne = locate_walk(M, e, px, py, hops, lw);

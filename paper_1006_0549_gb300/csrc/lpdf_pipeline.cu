@@ -90,8 +90,39 @@ __device__ __forceinline__ uint32_t ld_stream(const uint32_t* p)
     return v;
 }
 
+// The rest of a walk that has met a wall edge (edge walls): mirror the position across the wall
+// edge (U <- 2 U_w - U, U_w = (lid_u, 0, 0) on a moving wall), go on walking from the same
+// element, at most kReflCap mirrorings and kHopCap hops in all. Returns the owner, or -1 (lost).
+// Out of line: particles reach it only at walls.
+static __device__ __noinline__ int walk_mirroring(const DevMesh& M, float lid_u, int e, int next, int& h, float& px,
+                                                  float& py, float& u, float& v, float& w)
+{
+    for (int nref = 0;;) {
+        if (next < 0) {
+            if (nref >= kReflCap) return -1;
+            const int k = -1 - next;
+            mirror_across_edge(M, e, k, px, py);
+            const bool moving = (__ldg(&M.en[e]).w >> (3 + k)) & 1;
+            u = (moving ? 2.0f * lid_u : 0.0f) - u;
+            v = -v;
+            w = -w;
+            ++nref;
+        } else {
+            if (h >= kHopCap) return -1;
+            e = next;
+            ++h;
+        }
+        int r = walk_test_fast<true>(M, e, px, py, next);
+        if (r < 0) {
+            float lam[3];
+            r = walk_test(M, e, px, py, lam, next) ? 1 : 0;
+        }
+        if (r == 1) return e;
+    }
+}
+
 // one particle: position i of the next buffer takes particle perm[i] of the current one
-template <int NS, bool kMulti>
+template <int NS, bool kGeneral>
 __device__ __forceinline__ void advance_one(const DevMesh& M, const DevState& cur, const DevState& nxt,
                                             const int* __restrict__ perm, const float* __restrict__ EF,
                                             const StepParams& P, unsigned long long* __restrict__ status, int64_t i,
@@ -110,21 +141,28 @@ __device__ __forceinline__ void advance_one(const DevMesh& M, const DevState& cu
     p.elem = ld_stream(cur.elem + src);
     p.pid = ld_stream(cur.pid + src);
     bool bad;
-    advance_particle<NS, true, kMulti>(M, EF, P, p, err, bad);
-    // barycentric neighbour walk from the old element
+    advance_particle<NS, true, kGeneral>(M, EF, P, p, err, bad);
+    // barycentric neighbour walk from the old element; with edge walls, a position found beyond
+    // a wall edge is mirrored across that edge (U <- 2 U_w - U) and the walk goes on
     const int e0 = p.elem;
     int e = e0, h = 0, ne = e0;
     bool lost = false;
 #pragma unroll 1
     for (;;) {
         int next = -1;
-        int r = walk_test_fast(M, e, p.x, p.y, next);
+        int r = walk_test_fast<kGeneral>(M, e, p.x, p.y, next);
         if (r < 0) {
             float lam[3];
             r = walk_test(M, e, p.x, p.y, lam, next) ? 1 : 0;
         }
         if (r == 1) {
             ne = e;
+            hops += h;
+            break;
+        }
+        if (kGeneral && next < 0 && M.edge_walls) {
+            ne = walk_mirroring(M, P.lid_u, e, next, h, p.x, p.y, p.u, p.v, p.w);
+            lost = ne < 0;
             hops += h;
             break;
         }
@@ -137,6 +175,7 @@ __device__ __forceinline__ void advance_one(const DevMesh& M, const DevState& cu
         ++h;
     }
     if (lost) ne = e0;
+    if (kGeneral && M.edge_walls) particle_sources<NS, kGeneral>(M, P, e0, p.x, p.y, p.psi);
     if (lost || bad) {
         err |= kErrLost;
         atomicAdd(&status[1], 1ull);
@@ -157,7 +196,7 @@ __device__ __forceinline__ void advance_one(const DevMesh& M, const DevState& cu
 // K1 variants (the autotuner picks one per context; all give bit-identical results): ABLK
 // threads per CTA, at least MINB CTAs per SM (the register cap), and either one particle per
 // thread over the whole grid or a persistent grid striding over ABLK-particle tiles.
-template <int NS, bool kMulti, int ABLK, int MINB, bool kPersist>
+template <int NS, bool kGeneral, int ABLK, int MINB, bool kPersist>
 __global__ void __launch_bounds__(ABLK, MINB)
 advance_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevState cur,
                const __grid_constant__ DevState nxt, const int* __restrict__ perm, const float* __restrict__ EF,
@@ -170,7 +209,7 @@ advance_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevSta
 #pragma unroll 1
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += kPersist ? gridDim.x : ntiles) {
         const int64_t i = tile * ABLK + threadIdx.x;
-        if (i < cur.n) advance_one<NS, kMulti>(M, cur, nxt, perm, EF, P, status, i, err, hops);
+        if (i < cur.n) advance_one<NS, kGeneral>(M, cur, nxt, perm, EF, P, status, i, err, hops);
     }
     const unsigned e_or = __reduce_or_sync(kFull, err);
     const int h_sum = __reduce_add_sync(kFull, hops);
@@ -616,25 +655,25 @@ int sm_count_cached()
     return n;
 }
 
-template <int NS, bool kMulti, int ABLK, int MINB, bool kPersist>
+template <int NS, bool kGeneral, int ABLK, int MINB, bool kPersist>
 void launch_advance_v(const DevMesh& m, const DevState& cur, const DevState& nxt, const int* perm, const float* ef,
                       const StepParams& p, unsigned long long* status, cudaStream_t st)
 {
     const int64_t ntiles = (cur.n + ABLK - 1) / ABLK;
     const int64_t grid = kPersist ? std::min<int64_t>(ntiles, (int64_t)sm_count_cached() * MINB) : ntiles;
-    advance_kernel<NS, kMulti, ABLK, MINB, kPersist><<<(unsigned)grid, ABLK, 0, st>>>(m, cur, nxt, perm, ef, p, status);
+    advance_kernel<NS, kGeneral, ABLK, MINB, kPersist><<<(unsigned)grid, ABLK, 0, st>>>(m, cur, nxt, perm, ef, p, status);
 }
 
-template <int NS, bool kMulti>
+template <int NS, bool kGeneral>
 void launch_advance(int v, const DevMesh& m, const DevState& cur, const DevState& nxt, const int* perm,
                     const float* ef, const StepParams& p, unsigned long long* status, cudaStream_t st)
 {
     switch (v) {
-        case 1: launch_advance_v<NS, kMulti, 256, 6, false>(m, cur, nxt, perm, ef, p, status, st); break;
-        case 2: launch_advance_v<NS, kMulti, 128, 8, false>(m, cur, nxt, perm, ef, p, status, st); break;
-        case 3: launch_advance_v<NS, kMulti, 256, 4, true>(m, cur, nxt, perm, ef, p, status, st); break;
-        case 4: launch_advance_v<NS, kMulti, 256, 6, true>(m, cur, nxt, perm, ef, p, status, st); break;
-        default: launch_advance_v<NS, kMulti, 256, 4, false>(m, cur, nxt, perm, ef, p, status, st); break;
+        case 1: launch_advance_v<NS, kGeneral, 256, 6, false>(m, cur, nxt, perm, ef, p, status, st); break;
+        case 2: launch_advance_v<NS, kGeneral, 128, 8, false>(m, cur, nxt, perm, ef, p, status, st); break;
+        case 3: launch_advance_v<NS, kGeneral, 256, 4, true>(m, cur, nxt, perm, ef, p, status, st); break;
+        case 4: launch_advance_v<NS, kGeneral, 256, 6, true>(m, cur, nxt, perm, ef, p, status, st); break;
+        default: launch_advance_v<NS, kGeneral, 256, 4, false>(m, cur, nxt, perm, ef, p, status, st); break;
     }
 }
 
@@ -668,7 +707,8 @@ cudaError_t run_pipeline(const DevMesh& m, const DevState& cur, const DevState& 
     if (ev) cudaEventRecord(ev[0], st);
     constexpr int NQ4 = (22 + NS + 3) / 4;
     element_fields_kernel<NS><<<nblocks((int64_t)E * NQ4, 256), 256, 0, st>>>(m, fields, w.efields);
-    if (m.n_comp > 1) launch_advance<NS, true>(tune.adv, m, cur, nxt, w.perm, w.efields, p, status, st);
+    // the general kernel for several components or walls off the frame, the plain one otherwise
+    if (m.n_comp > 1 || m.edge_walls) launch_advance<NS, true>(tune.adv, m, cur, nxt, w.perm, w.efields, p, status, st);
     else launch_advance<NS, false>(tune.adv, m, cur, nxt, w.perm, w.efields, p, status, st);
     if (ev) cudaEventRecord(ev[1], st);
     histogram_kernel<<<(unsigned)((nblk + kHWarps - 1) / kHWarps), 32 * kHWarps, 0, st>>>(

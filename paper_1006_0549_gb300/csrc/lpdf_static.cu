@@ -66,8 +66,8 @@ extern "C" int lpdf_pdf_step_static(const lpdf_mesh* mesh, const lpdf_params* pa
         lpdf_set_error(LPDF_ERR_ARG, "pdf_step_static: NULL argument");
         return LPDF_ERR_ARG;
     }
-    if (mesh->d.n_comp > 1) {
-        lpdf_set_error(LPDF_ERR_UNSUPPORTED, "pdf_step_static: multi-component meshes need a context");
+    if (mesh->d.n_comp > 1 || mesh->d.edge_walls) {
+        lpdf_set_error(LPDF_ERR_UNSUPPORTED, "pdf_step_static: multi-component meshes and walls off the frame need a context");
         return LPDF_ERR_UNSUPPORTED;
     }
     if (params->ns < 1 || params->ns > LPDF_MAX_SCALARS) {

@@ -520,3 +520,30 @@ def batched_channels(n: int = 64, tri_range=(2000, 40000), ppe_range=(50, 400), 
         seeds.append(seed + k)
         srcs.append([(0.25, float(np.float32(rng.uniform(*source_y))), 0.02, 0)])
     return BatchedWorkload(f"channels-x{n}", union_mesh(meshes), ppe, seeds, srcs, 1, 1.0 / 180.0, 1e-3)
+
+
+def bump_channel_mesh(nx: int, ny: int, seed: int, amp: float = 0.15, jitter: float = 0.2) -> Mesh:
+    """The periodic channel of channel_mesh with a smooth bump on the bottom wall: every node moves
+    up by h(s) (1 - y / 2), h(s) = amp (1 - cos 2 pi s) / 2, s = the node column's position along
+    the channel (0 and 1 at the periodic columns, which therefore keep their y values and their
+    pairing). The bottom wall is curved and the fluid side of it is non-convex; the top wall stays
+    flat. Coordinates are rounded to FP32."""
+    m = channel_mesh(nx, ny, seed, jitter=jitter)
+    x, y = m.node_xy[:, 0], m.node_xy[:, 1]
+    s = x / m.period_x
+    h = amp * 0.5 * (1.0 - np.cos(2.0 * np.pi * s))
+    h[(x == 0.0) | (x == m.period_x)] = 0.0
+    xy = np.stack([x, _f32(y + h * (1.0 - 0.5 * y))], axis=1)
+    box = (0.0, m.period_x, float(xy[:, 1].min()), float(xy[:, 1].max()))
+    return Mesh(xy, m.tri, m.edge_tag, m.period_x, box, "channel", nx, ny)
+
+
+def trapezoid_mesh(nx: int, ny: int, seed: int, jitter: float = 0.2) -> Mesh:
+    """The cavity mesh mapped to the convex quadrilateral with corners (0, 0), (1, 0), (1.3, 1.2)
+    and (0.3, 0.8) by x' = x + 0.3 y, y' = y (0.8 + 0.4 x): three slanted walls (the top one
+    keeps the lid tag) and a flat bottom. Coordinates are rounded to FP32."""
+    m = cavity_mesh(nx, ny, seed, jitter=jitter)
+    x, y = m.node_xy[:, 0], m.node_xy[:, 1]
+    xy = np.stack([_f32(x + 0.3 * y), _f32(y * (0.8 + 0.4 * x))], axis=1)
+    box = (float(xy[:, 0].min()), float(xy[:, 0].max()), float(xy[:, 1].min()), float(xy[:, 1].max()))
+    return Mesh(xy, m.tri, m.edge_tag, 0.0, box, "cavity", nx, ny)

@@ -62,6 +62,23 @@ def reorder(st: wl.State, idx) -> wl.State:
                     np.ascontiguousarray(st.elem[idx]), np.ascontiguousarray(st.pid[idx]))
 
 
+def wall_distance_points(mesh: wl.Mesh, px, py):
+    """Distance of points to the nearest wall edge (tags 1, 2; periodic images in x)."""
+    xy = mesh.node_xy
+    segs = [(xy[mesh.tri[e, k]], xy[mesh.tri[e, (k + 1) % 3]]) for e in range(mesh.n_tri) for k in range(3)
+            if mesh.edge_tag[e, k] in (1, 2)]
+    q = np.stack([np.asarray(px, dtype=np.float64), np.asarray(py, dtype=np.float64)], axis=1)
+    best = np.full(q.shape[0], np.inf)
+    shifts = [0.0] if not mesh.period_x > 0 else [-mesh.period_x, 0.0, mesh.period_x]
+    for a, b in segs:
+        t = b - a
+        for sx in shifts:
+            r = q - a - np.array([sx, 0.0])
+            s = np.clip(r @ t / (t @ t), 0.0, 1.0)
+            best = np.minimum(best, np.hypot(r[:, 0] - s * t[0], r[:, 1] - s * t[1]))
+    return best
+
+
 def compare_step(mesh: wl.Mesh, om: oracle.OracleMesh, params: lpdf.Params, F, st_in: wl.State, step: int,
                  g: wl.State, check_locate: bool = True):
     """Per-stage parity of one step from the same input state.
@@ -83,9 +100,12 @@ def compare_step(mesh: wl.Mesh, om: oracle.OracleMesh, params: lpdf.Params, F, s
     x0, x1, y0, y1 = mesh.box
     pre_x, pre_y = aux[:, 0], aux[:, 1]
     # straddling a wall or the periodic seam within rounding distance
-    near_wall = (np.abs(pre_y - y0) < 1e-5) | (np.abs(pre_y - y1) < 1e-5)
-    if mesh.period_x == 0.0:
-        near_wall |= (np.abs(pre_x - x0) < 1e-5) | (np.abs(pre_x - x1) < 1e-5)
+    if om.edge_walls:
+        near_wall = wall_distance_points(mesh, pre_x, pre_y) < 1e-5
+    else:
+        near_wall = (np.abs(pre_y - y0) < 1e-5) | (np.abs(pre_y - y1) < 1e-5)
+        if mesh.period_x == 0.0:
+            near_wall |= (np.abs(pre_x - x0) < 1e-5) | (np.abs(pre_x - x1) < 1e-5)
     ok_any = np.zeros(st_in.n, dtype=bool)
     for k in FIELDS:
         o = res[k]

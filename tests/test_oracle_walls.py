@@ -1,0 +1,99 @@
+"""Pins of the oracle's walls of any shape: the walk in a non-convex domain, and the mirroring of
+a particle across a slanted or curved wall edge (reading 8 applied to each wall edge)."""
+import numpy as np
+
+import oracle
+from paper_1006_0549_gb300 import workloads as wl
+
+
+def _inside_points(mesh, rng, n):
+    """Random points strictly inside random elements (owner known by construction)."""
+    e = rng.integers(0, mesh.n_tri, n)
+    r = rng.uniform(0.02, 1.0, size=(n, 3))
+    r /= r.sum(axis=1, keepdims=True)
+    xy = np.einsum("pk,pkd->pd", r, mesh.node_xy[mesh.tri[e]]).astype(np.float32).astype(np.float64)
+    return e, xy
+
+
+def test_mesh_kinds():
+    assert oracle.OracleMesh(wl.bump_channel_mesh(12, 8, 1)).edge_walls
+    assert oracle.OracleMesh(wl.trapezoid_mesh(8, 8, 2)).edge_walls
+    assert not oracle.OracleMesh(wl.channel_mesh(8, 6, 3)).edge_walls
+    assert not oracle.OracleMesh(wl.cavity_mesh(6, 6, 4)).edge_walls
+
+
+def test_walk_in_a_non_convex_domain_finds_the_owner_without_crossing_the_wall():
+    """Points of the bump channel reached from elements a few hops away: the walk (interior exits
+    first) ends at the brute-force owner, never at a wall."""
+    mesh = wl.bump_channel_mesh(24, 10, 5, amp=0.3)
+    om = oracle.OracleMesh(mesh)
+    nbr = om.neighbors()
+    rng = np.random.default_rng(1)
+    e_true, xy = _inside_points(mesh, rng, 3000)
+    for k in range(len(e_true)):
+        start = int(e_true[k])
+        for _ in range(int(rng.integers(0, 4))):          # a random nearby start
+            cand = [n for n in nbr[start] if n >= 0]
+            start = int(cand[rng.integers(0, len(cand))])
+        e, _ = om.locate_walk(start, xy[k, 0], xy[k, 1])
+        assert e == om.locate_brute(xy[k, 0], xy[k, 1]), (k, start, xy[k])
+
+
+def _still_fields(mesh, ns):
+    """Node fields that leave U unchanged (no pressure gradient, no drift, no diffusion)."""
+    F = np.zeros((mesh.n_nodes, wl.n_fields_padded(ns)), dtype=np.float32)
+    F[:, wl.F_OMEGA] = 1.0
+    return F
+
+
+def test_mirror_across_a_slanted_wall():
+    """Particles near the trapezoid's left wall (the line from (0, 0) to (0.3, 0.8)) moving out
+    through it: the final position is the mirror image of the moved position (checked with the
+    unit-normal form p' = q - 2 ((q - a).n) n), the velocity is reversed, and the owner exists."""
+    mesh = wl.trapezoid_mesh(12, 12, 7)
+    om = oracle.OracleMesh(mesh)
+    rng = np.random.default_rng(3)
+    a = np.array([0.0, 0.0])
+    d = np.array([0.3, 0.8]) / np.hypot(0.3, 0.8)
+    n_in = np.array([d[1], -d[0]])                         # inward unit normal (the domain is to the right)
+    # start points inside, 0.002 .. 0.01 from the wall, away from its ends
+    P = 400
+    t = rng.uniform(0.25, 0.75, P) * np.hypot(0.3, 0.8)
+    dist = rng.uniform(0.002, 0.01, P)
+    pts = (a + t[:, None] * d + dist[:, None] * n_in).astype(np.float32)
+    elem = np.array([om.locate_brute(float(x), float(y)) for x, y in pts], dtype=np.int32)
+    assert np.all(elem >= 0)
+    speed = rng.uniform(15.0, 30.0, P)                     # dt = 1e-3: moves of 0.015 .. 0.03 outward
+    U = (-speed[:, None] * n_in).astype(np.float32)
+    st = wl.State(pts[:, 0].copy(), pts[:, 1].copy(), U[:, 0].copy(), U[:, 1].copy(),
+                  np.zeros(P, np.float32), np.ones(P, np.float32), np.zeros((1, P), np.float32), elem,
+                  np.arange(P, dtype=np.uint32))
+    p = oracle.make_params(nu=1e-30, dt=1e-3, seed=9, ns=1)
+    res, oelem, aux, lost = oracle.pdf_step(om, p, _still_fields(mesh, 1), st, 1, locate_mode=2)
+    assert lost == 0
+    q = aux[:, 0:2]                                        # moved position before the wall treatment
+    beyond = (q - a) @ n_in < 0.0
+    assert beyond.all()
+    want = q - 2.0 * ((q - a) @ n_in)[:, None] * n_in[None, :]
+    got = np.stack([res["x"], res["y"]], axis=1)
+    assert np.allclose(got, want, atol=2e-7)
+    assert np.all(aux[:, 2] == 1)                          # one mirroring each
+    assert np.array_equal(res["u"], -st.u.astype(np.float64)) and np.array_equal(res["v"], -st.v.astype(np.float64))
+    for i in range(P):
+        assert om.locate_brute(res["x"][i], res["y"][i]) == oelem[i] >= 0
+
+
+def test_particles_stay_in_the_bump_channel():
+    """A step with fast random velocities: every particle ends owned, walk and brute force agree,
+    and the ones that met the curved wall were mirrored back into the fluid."""
+    mesh = wl.bump_channel_mesh(20, 8, 11, amp=0.3)
+    om = oracle.OracleMesh(mesh)
+    st = wl.synthetic_state(mesh, 6, 1, seed=12)
+    st.u *= 4.0
+    st.v = (st.v * 20.0).astype(np.float32)
+    p = oracle.make_params(nu=1.0 / 180.0, dt=1e-3, seed=13, ns=1)
+    F = wl.synthetic_node_fields(mesh, 1, seed=14)
+    res, oelem, aux, lost = oracle.pdf_step(om, p, F, st, 1, locate_mode=2)
+    assert lost == 0
+    assert np.all(oelem >= 0)
+    assert (aux[:, 2] > 0).sum() > 10                      # some particles met a wall
