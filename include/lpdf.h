@@ -83,6 +83,13 @@ typedef struct {
     int32_t cg_warm_start;  /* lpdf_elliptic_relax_solve: 1 starts the CGs from the previous solution
                                on this mesh (a time loop), 0 from zero */
     double dpdx0, dpdy0;    /* fixed mean pressure gradient added to the solved one (channel: -1, 0) */
+    /* Eq. 9 micromixing: 0 IEM (<phi|V> -> <phi>), 1 IECM with the conditional mean estimated
+     * linearly in the velocity, <phi_a|V> = <phi_a> + beta_a . (V - <U>) (lpdf_ctx_set_iecm) */
+    int32_t mixing;
+    /* reactive source of Eq. 9 (none when react_k <= 0): the second-order reaction
+     * psi_a + psi_b -> psi_p at rate react_k, S_a = S_b = -react_k psi_a psi_b, S_p = +react_k psi_a psi_b */
+    int32_t react_a, react_b, react_p;
+    double react_k;
 } lpdf_params;
 
 typedef struct lpdf_mesh lpdf_mesh;
@@ -90,7 +97,8 @@ typedef struct lpdf_ctx lpdf_ctx;
 
 /* Fills *p with C3 = 5, C4 = 0.25, Cphi = 2, C0 = 2.1, Comega1 = 0.5, Comega2 = 0.73,
  * CL = 0.134, Ceta = 72, nu = 1/180, dt = 1e-3, ns = 1, no sources, seed = 1, lid_u = 0,
- * gmodel = 0, pressure_solve = 0, cg_warm_start = 0, dpdx0 = dpdy0 = 0. */
+ * gmodel = 0, pressure_solve = 0, cg_warm_start = 0, dpdx0 = dpdy0 = 0, mixing = 0 (IEM),
+ * react_k = 0 (no reaction), react_a = react_b = react_p = 0. */
 void lpdf_params_default(lpdf_params* p);
 
 /* Message of the calling thread's last error ("" if none). Owned by the library. */
@@ -202,7 +210,8 @@ int lpdf_get_state(const lpdf_ctx* ctx, float* x, float* y, float* u, float* v, 
  *               the linear shape functions of its element.
  *   step        the step index (part of the Philox counter: (pid, step, 0<<16 | block)).
  * Per particle, with the state at t_n: Eq. 4 for U, Eq. 5 for omega (sqrt(max(omega,0)),
- * then omega <- |omega|), Eq. 9 in IEM form for psi, Eq. 2 for X with the same dW_1, dW_2;
+ * then omega <- |omega|), Eq. 9 for psi (IEM, or IECM with params->mixing = 1, plus the reactive
+ * source when params->react_k > 0, both from the state at t_n), Eq. 2 for X with the same dW_1, dW_2;
  * periodic wrap; wall reflection (X mirrored, U <- 2 U_w - U); exact point location by a
  * barycentric neighbour walk (hop cap 64); psi_alpha <- 1 inside scalar source discs; then
  * S_k(n) += lambda_n(X') q_k, q = 1, u, v, w, uu, uv, uw, vv, vw, ww, omega, psi_a, psi_a^2.
@@ -210,6 +219,29 @@ int lpdf_get_state(const lpdf_ctx* ctx, float* x, float* y, float* u, float* v, 
  * call itself only reports argument and launch errors.
  * ------------------------------------------------------------------------------------- */
 int lpdf_pdf_step(lpdf_ctx* ctx, const float* node_fields, uint64_t step, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * IECM (Eq. 9): the scalar mean conditional on the particle velocity. Reading: the conditional
+ * mean is estimated linearly in the velocity (exact for jointly Gaussian velocity and scalar),
+ * <phi_a|V> = <phi_a> + beta_a . (V - <U>), beta_a = R^-1 c_a with R = <u_i u_j> (the Reynolds
+ * stresses, 3 x 3) and c_a = <u_i psi_a'> (the scalar fluxes), both at the gridpoints; beta is
+ * a node field interpolated to the particle by the linear shape functions.
+ *
+ * lpdf_grid_flux_statistics -- the scalar fluxes of the state left by the last pdf_step of a
+ *   context created with params->mixing = 1 (the step then also sums lambda_n u_i psi_a). async.
+ *   out device, n_nodes x 3 ns FP64, per node (u psi_0, v psi_0, w psi_0, u psi_1, ...):
+ *   raw = 1 the sums S(n) = sum_p lambda_n(X_p) u_i psi_a; raw = 0 the covariances
+ *   S/S_0 - <u_i><psi_a> (zeros where S_0 = 0). Errors: LPDF_ERR_ARG (mixing = 0 at creation).
+ * lpdf_iecm_coefficients -- beta from gridpoint statistics (lpdf_grid_statistics raw = 0) and
+ *   fluxes (lpdf_grid_flux_statistics raw = 0), both device FP64. async. beta device out,
+ *   n_nodes x 3 ns FP32 (beta_0 = (bx, by, bz), beta_1, ...): beta_a = R^-1 c_a in FP64 by
+ *   Cramer's rule; beta_a = 0 where det R <= 1e-12 (trace R / 3)^3.
+ * lpdf_ctx_set_iecm -- the beta table (device, n_nodes x 3 ns FP32, owned by the caller, read by
+ *   every later pdf_step while params->mixing = 1; NULL clears it: IECM then falls back to IEM). */
+int lpdf_grid_flux_statistics(lpdf_ctx* ctx, double* out, int raw, void* stream);
+int lpdf_iecm_coefficients(const lpdf_mesh* mesh, int32_t ns, const double* stats, const double* flux, float* beta,
+                           void* stream);
+int lpdf_ctx_set_iecm(lpdf_ctx* ctx, const float* beta);
 
 /* ---------------------------------------------------------------------------------------
  * lpdf_pdf_steps -- nsteps consecutive steps step0, step0 + 1, ... with the same node fields,

@@ -61,7 +61,8 @@ def lib():
         L.oracle_locate_walk.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, vp]
         L.oracle_barycentric.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, vp]
         L.oracle_pdf_step.restype = ctypes.c_long
-        L.oracle_pdf_step.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_long] + [vp] * 9 + \
+        L.oracle_flux_moments.argtypes = [vp, ctypes.c_int, ctypes.c_long] + [vp] * 8
+        L.oracle_pdf_step.argtypes = [vp, vp, vp, ctypes.c_int, vp, ctypes.c_long] + [vp] * 9 + \
             [ctypes.c_uint64, ctypes.c_int] + [vp] * 9
         L.oracle_moments.argtypes = [vp, ctypes.c_int, ctypes.c_long] + [vp] * 10
         L.oracle_grid_statistics.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp]
@@ -80,14 +81,19 @@ class OParams(ctypes.Structure):
                 ("C4", ctypes.c_double), ("Cphi", ctypes.c_double), ("lid_u", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("ns", ctypes.c_int32), ("n_sources", ctypes.c_int32),
                 ("src_x", ctypes.c_double * MAX_SOURCES), ("src_y", ctypes.c_double * MAX_SOURCES),
-                ("src_r", ctypes.c_double * MAX_SOURCES), ("src_alpha", ctypes.c_int32 * MAX_SOURCES)]
+                ("src_r", ctypes.c_double * MAX_SOURCES), ("src_alpha", ctypes.c_int32 * MAX_SOURCES),
+                ("react_k", ctypes.c_double), ("react_a", ctypes.c_int32), ("react_b", ctypes.c_int32),
+                ("react_p", ctypes.c_int32)]
 
 
-def make_params(nu, dt, seed, ns, sources=(), C3=5.0, C4=0.25, Cphi=2.0, lid_u=0.0) -> OParams:
+def make_params(nu, dt, seed, ns, sources=(), C3=5.0, C4=0.25, Cphi=2.0, lid_u=0.0, react=None) -> OParams:
     """Model constants: C_3, C_4 (Eq. 5), C_phi (IEM time scale); the paper prints no values,
-    so the defaults are the literature values recalled for the cited models."""
+    so the defaults are the literature values recalled for the cited models. react = (k, a, b, p):
+    the reactive source of Eq. 9 for psi_a + psi_b -> psi_p at rate k."""
     p = OParams()
     p.nu, p.dt, p.C3, p.C4, p.Cphi, p.lid_u = nu, dt, C3, C4, Cphi, lid_u
+    if react is not None:
+        p.react_k, p.react_a, p.react_b, p.react_p = react
     p.seed, p.ns, p.n_sources = seed, ns, len(sources)
     for i, (sx, sy, sr, sa) in enumerate(sources):
         p.src_x[i], p.src_y[i], p.src_r[i], p.src_alpha[i] = sx, sy, sr, sa
@@ -173,13 +179,15 @@ def _f64c(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def pdf_step(om: OracleMesh, params: OParams, fields, state, step: int, locate_mode: int = 0):
+def pdf_step(om: OracleMesh, params: OParams, fields, state, step: int, locate_mode: int = 0, beta=None):
     """One forward-Euler step of every particle (Eq. 2, 4, 5, 9; tracking; reflection; sources).
 
-    `state` is a workloads.State (FP32). Returns (dict of FP64 arrays, elem, aux, lost)."""
+    `state` is a workloads.State (FP32); beta (n_nodes x 3 ns) switches Eq. 9 to IECM. Returns
+    (dict of FP64 arrays, elem, aux, lost)."""
     P, ns = state.n, params.ns
     fields = _f32c(fields)
     nfp = fields.shape[1]
+    beta = None if beta is None else _f32c(beta)
     ins = [_f32c(a) for a in (state.x, state.y, state.u, state.v, state.w, state.omega)]
     psi = _f32c(state.psi.reshape(ns, P))
     elem = np.ascontiguousarray(state.elem, dtype=np.int32)
@@ -188,7 +196,7 @@ def pdf_step(om: OracleMesh, params: OParams, fields, state, step: int, locate_m
     opsi = np.empty((ns, P))
     oelem = np.empty(P, dtype=np.int32)
     aux = np.empty((P, 4))
-    lost = lib().oracle_pdf_step(om.ptr, ctypes.byref(params), _p(fields), nfp, P,
+    lost = lib().oracle_pdf_step(om.ptr, ctypes.byref(params), _p(fields), nfp, _p(beta), P,
                                  *[_p(a) for a in ins], _p(psi), _p(elem), _p(pid), step, locate_mode,
                                  *[_p(a) for a in outs], _p(opsi), _p(oelem), _p(aux))
     names = ("x", "y", "u", "v", "w", "omega")
@@ -208,6 +216,16 @@ def moments(om: OracleMesh, ns: int, x, y, u, v, w, omega, psi, elem, with_abs: 
     Sabs = np.empty((om.n_nodes, nq)) if with_abs else None
     lib().oracle_moments(om.ptr, ns, P, *[_p(a) for a in arrs], _p(psi), _p(elem), _p(S), _p(Sabs))
     return S, Sabs
+
+
+def flux_moments(om: OracleMesh, ns: int, x, y, u, v, w, psi, elem):
+    """Raw scalar-flux sums per node: sum_p lambda_n (u psi_a, v psi_a, w psi_a), FP64."""
+    P = len(x)
+    F = np.empty((om.n_nodes, 3 * ns))
+    lib().oracle_flux_moments(om.ptr, ns, P, *[_p(_f64c(a)) for a in (x, y, u, v, w)],
+                              _p(_f64c(np.asarray(psi).reshape(ns, P))), _p(np.ascontiguousarray(elem, dtype=np.int32)),
+                              _p(F))
+    return F
 
 
 def grid_statistics(S, ns: int):

@@ -236,3 +236,47 @@ def node_fields(mesh, stats, ns, C0=2.1, Comega1=0.5, Comega2=0.73, CL=0.134, Ce
     if return_parts:
         return out, dict(geo=geo, k=k, eps=eps, p=p, **parts)
     return out
+
+
+# ---------------------------------------------------------------------------------- IECM (Eq. 9)
+
+def flux_covariances(stats_raw, flux_raw, ns):
+    """<u_i psi_a> - <u_i><psi_a> per node from raw sums (S_0, S_u, S_v, S_w, ..., S_psi) and the
+    raw flux sums (u psi_a, v psi_a, w psi_a per scalar); zeros where S_0 = 0."""
+    S = np.asarray(stats_raw, dtype=np.float64)
+    Fx = np.asarray(flux_raw, dtype=np.float64)
+    out = np.zeros_like(Fx)
+    s0 = S[:, 0]
+    ok = s0 != 0.0
+    for a in range(ns):
+        mpsi = np.where(ok, S[:, 11 + a] / np.where(ok, s0, 1.0), 0.0)
+        for c in range(3):
+            mu = np.where(ok, S[:, 1 + c] / np.where(ok, s0, 1.0), 0.0)
+            out[:, 3 * a + c] = np.where(ok, Fx[:, 3 * a + c] / np.where(ok, s0, 1.0) - mu * mpsi, 0.0)
+    return out
+
+
+def iecm_coefficients(stats, flux, ns):
+    """beta_a = R^-1 c_a per node: R the Reynolds-stress tensor (statistics columns uu, uv, uw, vv,
+    vw, ww), c_a the scalar flux <u_i psi_a'>; beta = 0 where det R <= 1e-12 (trace R / 3)^3. The
+    conditional mean of Eq. 9 is then read as <phi_a|V> = <phi_a> + beta_a . (V - <U>), the
+    conditional expectation of jointly Gaussian velocity and scalar."""
+    st = np.asarray(stats, dtype=np.float64)
+    c = np.asarray(flux, dtype=np.float64)
+    N = st.shape[0]
+    R = np.empty((N, 3, 3))
+    R[:, 0, 0], R[:, 0, 1], R[:, 0, 2] = st[:, RUU], st[:, RUV], st[:, RUW]
+    R[:, 1, 0], R[:, 1, 1], R[:, 1, 2] = st[:, RUV], st[:, RVV], st[:, RVW]
+    R[:, 2, 0], R[:, 2, 1], R[:, 2, 2] = st[:, RUW], st[:, RVW], st[:, RWW]
+    det = np.linalg.det(R)
+    tr = np.trace(R, axis1=1, axis2=2) / 3.0
+    ok = det > 1e-12 * np.maximum(tr, 0.0) ** 3
+    beta = np.zeros((N, 3 * ns))
+    for a in range(ns):
+        rhs = c[:, 3 * a:3 * a + 3]
+        sol = np.zeros((N, 3))
+        if ok.any():
+            sol[ok] = np.linalg.solve(R[ok], rhs[ok][:, :, None])[:, :, 0]
+        beta[:, 3 * a:3 * a + 3] = sol
+    return beta
+

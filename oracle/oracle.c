@@ -475,6 +475,9 @@ typedef struct {
     int32_t n_sources;
     double src_x[ORACLE_MAX_SOURCES], src_y[ORACLE_MAX_SOURCES], src_r[ORACLE_MAX_SOURCES];
     int32_t src_alpha[ORACLE_MAX_SOURCES];
+    /* reactive source of Eq. 9: psi_a + psi_b -> psi_p at rate react_k (none when react_k <= 0) */
+    double react_k;
+    int32_t react_a, react_b, react_p;
 } OParams;
 
 /* node-field columns */
@@ -511,7 +514,7 @@ static int in_source_f32(float px, float py, float sx, float sy, float r)
 /* locate_mode: 0 walk, 1 brute force, 2 both (a disagreement counts as lost).            */
 /* Returns the number of particles that could not be located.                            */
 /* ------------------------------------------------------------------------------------ */
-long oracle_pdf_step(const OMesh* m, const OParams* p, const float* fields, int nfp, long P,
+long oracle_pdf_step(const OMesh* m, const OParams* p, const float* fields, int nfp, const float* beta, long P,
                      const float* x, const float* y, const float* u, const float* v, const float* w,
                      const float* om, const float* psi, const int* elem, const uint32_t* pid,
                      uint64_t step, int locate_mode,
@@ -548,11 +551,26 @@ long oracle_pdf_step(const OMesh* m, const OParams* p, const float* fields, int 
         double OMn = OM - p->C3 * Om * (OM - Om) * dt - F[F_SOMEGA] * Om * OM * dt
                         + sqrt(2.0 * p->C3 * p->C4 * Om * Om * fmax(OM, 0.0)) * dWw;
         OMn = fabs(OMn);
-        /* Eq. 9, IEM: 1/t_m = C_phi <omega> / 2 */
-        double PSIn[ORACLE_MAX_NS];
+        /* Eq. 9: relaxation to the conditional mean with 1/t_m = C_phi <omega> / 2; IEM takes
+         * <phi|V> = <phi>, IECM (beta given) <phi_a|V> = <phi_a> + beta_a . (U - <U>) with beta
+         * interpolated like the other node fields; plus the reactive source, from the state at t_n */
+        double PSIn[ORACLE_MAX_NS], PS[ORACLE_MAX_NS], S[ORACLE_MAX_NS];
         for (int a = 0; a < ns; ++a) {
-            double ps = psi[(size_t)a * (size_t)P + (size_t)i];
-            PSIn[a] = ps - (ps - F[F_PHI0 + a]) * (0.5 * p->Cphi * Om) * dt;
+            PS[a] = psi[(size_t)a * (size_t)P + (size_t)i];
+            S[a] = 0.0;
+        }
+        if (p->react_k > 0.0) {
+            const double r = p->react_k * PS[p->react_a] * PS[p->react_b];
+            S[p->react_a] -= r;
+            S[p->react_b] -= r;
+            S[p->react_p] += r;
+        }
+        double B[3 * ORACLE_MAX_NS];
+        if (beta) interpolate(m, beta, 3 * ns, 3 * ns, e, lam, B);
+        for (int a = 0; a < ns; ++a) {
+            double cond = F[F_PHI0 + a];
+            if (beta) cond += B[3 * a] * Ur + B[3 * a + 1] * Vr + B[3 * a + 2] * Wr;
+            PSIn[a] = PS[a] - (PS[a] - cond) * (0.5 * p->Cphi * Om) * dt + S[a] * dt;
         }
         /* Eq. 2, with the state at t_n */
         double qx = X + U * dt + s2nu * dW1;
@@ -662,6 +680,32 @@ void oracle_moments(const OMesh* m, int ns, long P, const double* x, const doubl
 
 /* means and central moments: [S0, <u>, <v>, <w>, <u'u'>, <u'v'>, <u'w'>, <v'v'>, <v'w'>, <w'w'>,
  * <omega>, <psi_a>, <psi_a'^2>]; a node with S0 == 0 gets zeros. */
+/* Scalar-flux sums for IECM: F(n) = sum_p lambda_n(X_p) (u psi_a, v psi_a, w psi_a), a = 0..ns-1,
+ * per node (3 ns columns); periodic duplicates folded as in oracle_moments. */
+void oracle_flux_moments(const OMesh* m, int ns, long P, const double* x, const double* y, const double* u,
+                         const double* v, const double* w, const double* psi, const int* elem, double* F)
+{
+    const int nq = 3 * ns;
+    memset(F, 0, sizeof(double) * (size_t)m->n_nodes * (size_t)nq);
+    for (long i = 0; i < P; ++i) {
+        const int e = elem[i];
+        double lam[3];
+        barycentric(m, e, x[i], y[i], lam);
+        for (int k = 0; k < 3; ++k) {
+            const int n = m->master[m->tri[3 * e + k]];
+            for (int a = 0; a < ns; ++a) {
+                const double ps = psi[(size_t)a * (size_t)P + (size_t)i];
+                F[(size_t)n * nq + 3 * a + 0] += lam[k] * u[i] * ps;
+                F[(size_t)n * nq + 3 * a + 1] += lam[k] * v[i] * ps;
+                F[(size_t)n * nq + 3 * a + 2] += lam[k] * w[i] * ps;
+            }
+        }
+    }
+    for (int n = 0; n < m->n_nodes; ++n)
+        if (m->master[n] != n)
+            memcpy(F + (size_t)n * nq, F + (size_t)m->master[n] * nq, sizeof(double) * (size_t)nq);
+}
+
 void oracle_grid_statistics(int n_nodes, int ns, const double* S, double* out)
 {
     const int nq = 11 + 2 * ns;
