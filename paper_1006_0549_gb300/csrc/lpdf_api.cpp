@@ -121,6 +121,10 @@ StepParams lpdf::make_step_params(const lpdf_params& p, const lpdf_mesh* m, uint
     s.key1 = (uint32_t)(p.seed >> 32);
     s.step_lo = (uint32_t)step;
     s.step_hi = (uint32_t)(step >> 32);
+    s.react_k = p.react_k > 0.0 ? (float)p.react_k : 0.0f;
+    s.react_a = p.react_a;
+    s.react_b = p.react_b;
+    s.react_p = p.react_p;
     s.n_src = p.n_sources;
     for (int i = 0; i < p.n_sources; ++i) {
         s.src_x[i] = p.src_x[i];
@@ -145,6 +149,11 @@ int check_params(const lpdf_params* p)
         if (p->src_alpha[i] < 0 || p->src_alpha[i] >= p->ns)
             return fail(LPDF_ERR_ARG, "source %d sets scalar %d, but ns = %d", i, p->src_alpha[i], p->ns);
     if (!(p->dt > 0.0) || !(p->nu >= 0.0)) return fail(LPDF_ERR_ARG, "need dt > 0 and nu >= 0");
+    if (p->mixing < 0 || p->mixing > 1) return fail(LPDF_ERR_ARG, "mixing = %d (0 IEM, 1 IECM)", p->mixing);
+    if (p->react_k > 0.0 && (p->react_a < 0 || p->react_a >= p->ns || p->react_b < 0 || p->react_b >= p->ns ||
+                             p->react_p < 0 || p->react_p >= p->ns))
+        return fail(LPDF_ERR_ARG, "reaction scalars %d + %d -> %d outside 0..%d", p->react_a, p->react_b, p->react_p,
+                    p->ns - 1);
     return LPDF_OK;
 }
 
@@ -474,7 +483,8 @@ int lpdf_ctx_create(const lpdf_mesh* mesh, const lpdf_params* params, int64_t ca
         (ce = alloc_pipe(c->pipe, cap, E, c->ns)) || (ce = dalloc(&c->comp, mesh->d.n_comp)) ||
         (ce = dalloc(&c->init_pbase, mesh->d.n_comp + 1)) || (ce = dalloc(&c->init_ppe, mesh->d.n_comp)) ||
         (ce = dalloc(&c->init_toff, mesh->d.n_comp + 1)) || (ce = dalloc(&c->init_key, 2 * mesh->d.n_comp)) ||
-        (ce = dalloc(&c->step_dev, 1))) {
+        (ce = dalloc(&c->step_dev, 1)) ||
+        (params->mixing == 1 && (ce = dalloc(&c->flux_acc, (size_t)mesh->d.n_nodes * 3 * c->ns)))) {
         lpdf_ctx_free(c);
         return fail(LPDF_ERR_CUDA, "ctx_create: %s", cudaGetErrorString(ce));
     }
@@ -513,6 +523,7 @@ void lpdf_ctx_free(lpdf_ctx* c)
     cudaFree(c->node_acc); cudaFree(c->status);
     cudaFree(c->comp); cudaFree(c->init_pbase); cudaFree(c->init_ppe); cudaFree(c->init_toff); cudaFree(c->init_key);
     cudaFree(c->step_dev);
+    cudaFree(c->flux_acc);
     drop_graphs(c);
     if (c->graph_stream) cudaStreamDestroy(c->graph_stream);
     delete c;
@@ -524,6 +535,8 @@ int lpdf_ctx_set_params(lpdf_ctx* c, const lpdf_params* p)
     int rc = check_params(p);
     if (rc) return rc;
     if (p->ns != c->ns) return fail(LPDF_ERR_ARG, "ns cannot change (%d -> %d)", c->ns, p->ns);
+    if (p->mixing == 1 && !c->flux_acc)
+        return fail(LPDF_ERR_ARG, "IECM needs a context created with mixing = 1 (its flux sums)");
     c->params = *p;
     drop_graphs(c);
     if (!c->comp_set) {
@@ -682,6 +695,9 @@ int lpdf_pdf_step(lpdf_ctx* c, const float* node_fields, uint64_t step, void* st
     CUDA_TRY(cudaMemsetAsync(c->node_acc, 0, sizeof(unsigned long long) * (size_t)c->mesh->d.n_nodes * nq, st));
     StepParams p = make_step_params(c->params, c->mesh, step);
     p.comp = c->mesh->d.n_comp > 1 ? c->comp : nullptr;
+    p.beta = c->params.mixing == 1 ? c->iecm_beta : nullptr;
+    if (c->flux_acc)
+        CUDA_TRY(cudaMemsetAsync(c->flux_acc, 0, sizeof(unsigned long long) * (size_t)c->mesh->d.n_nodes * 3 * c->ns, st));
     c->s2.n = c->s.n;
     std::array<cudaEvent_t, 4> ev{};
     if (c->timing) {
@@ -696,7 +712,7 @@ int lpdf_pdf_step(lpdf_ctx* c, const float* node_fields, uint64_t step, void* st
         c->ev_pending.push_back(ev);
     }
     CUDA_TRY(launch_pdf_step_pipeline(c->mesh->d, c->s, c->s2, c->ns, node_fields, p, c->pipe, c->node_acc,
-                                      c->status, st, c->timing ? ev.data() : nullptr, c->tune));
+                                      c->status, st, c->timing ? ev.data() : nullptr, c->tune, c->flux_acc));
     // the new state is in the second buffer, listed in element order by perm_new
     std::swap(c->s, c->s2);
     std::swap(c->pipe.perm, c->pipe.perm_new);
@@ -717,14 +733,17 @@ static int capture_steps(lpdf_ctx* c, const float* fields, int slot)
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
         e = cudaMemsetAsync(c->node_acc, 0, sizeof(unsigned long long) * (size_t)c->mesh->d.n_nodes * nq, cs);
+        if (e == cudaSuccess && c->flux_acc)
+            e = cudaMemsetAsync(c->flux_acc, 0, sizeof(unsigned long long) * (size_t)c->mesh->d.n_nodes * 3 * c->ns, cs);
         StepParams p = make_step_params(c->params, c->mesh, 0);
         p.comp = c->mesh->d.n_comp > 1 ? c->comp : nullptr;
+        p.beta = c->params.mixing == 1 ? c->iecm_beta : nullptr;
         p.step_dev = c->step_dev;
         p.step_add = (unsigned)k;
         b.n = a.n;
         if (e == cudaSuccess)
             e = launch_pdf_step_pipeline(c->mesh->d, a, b, c->ns, fields, p, w, c->node_acc, c->status, cs, nullptr,
-                                         c->tune);
+                                         c->tune, c->flux_acc);
         std::swap(a, b);
         std::swap(w.perm, w.perm_new);
     }
@@ -848,6 +867,32 @@ int lpdf_ctx_autotune(lpdf_ctx* c, const float* node_fields, uint64_t step0, int
     }
     if (steps_used) *steps_used = (int32_t)(step - step0);
     return rc;
+}
+
+int lpdf_ctx_set_iecm(lpdf_ctx* c, const float* beta)
+{
+    if (!c) return fail(LPDF_ERR_ARG, "ctx is NULL");
+    c->iecm_beta = beta;
+    drop_graphs(c);
+    return LPDF_OK;
+}
+
+int lpdf_grid_flux_statistics(lpdf_ctx* c, double* out, int raw, void* stream)
+{
+    if (!c || !out) return fail(LPDF_ERR_ARG, "grid_flux_statistics: NULL argument");
+    if (!c->flux_acc) return fail(LPDF_ERR_ARG, "grid_flux_statistics: the context was created with mixing = 0");
+    CUDA_TRY(launch_flux_statistics(c->mesh->d.master, c->mesh->d.n_nodes, c->ns, c->node_acc, c->flux_acc, out, raw,
+                                    (cudaStream_t)stream));
+    return LPDF_OK;
+}
+
+int lpdf_iecm_coefficients(const lpdf_mesh* mesh, int32_t ns, const double* stats, const double* flux, float* beta,
+                           void* stream)
+{
+    if (!mesh || !stats || !flux || !beta) return fail(LPDF_ERR_ARG, "iecm_coefficients: NULL argument");
+    if (ns < 1 || ns > LPDF_MAX_SCALARS) return fail(LPDF_ERR_UNSUPPORTED, "iecm_coefficients: ns = %d", ns);
+    CUDA_TRY(launch_iecm_coefficients(mesh->d.n_nodes, ns, stats, flux, beta, (cudaStream_t)stream));
+    return LPDF_OK;
 }
 
 int lpdf_ctx_set_timing(lpdf_ctx* c, int enable)

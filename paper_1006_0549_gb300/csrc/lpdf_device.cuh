@@ -566,10 +566,56 @@ __device__ __forceinline__ void advance_particle(const DevMesh& M, const float* 
     float omn = om - P.C3 * Om * (om - Om) * P.dt - Fi[LPDF_F_SOMEGA] * Om * om * P.dt
               + sqrtf(2.0f * P.C3 * P.C4 * Om * Om * fmaxf(om, 0.0f)) * (P.sdt * z5);
     omn = fabsf(omn);
-    // Eq. 9, IEM form: 1/t_m = C_phi <omega> / 2
+    // Eq. 9: relaxation to the conditional mean, 1/t_m = C_phi <omega> / 2
     const float mix = P.half_cphi * Om * P.dt;
+    if (kGeneral && (P.beta || P.react_k > 0.0f)) {
+        // IECM: <phi_a|V> = <phi_a> + beta_a . (U - <U>), beta interpolated by the shape functions of
+        // the element's nodes; the reactive source psi_ra + psi_rb -> psi_rp; all from the state at t_n
+        float cond[NS], src[NS];
 #pragma unroll
-    for (int a = 0; a < NS; ++a) p.psi[a] = p.psi[a] - (p.psi[a] - Fi[LPDF_F_PHI0 + a]) * mix;
+        for (int a = 0; a < NS; ++a) {
+            cond[a] = Fi[LPDF_F_PHI0 + a];
+            src[a] = 0.0f;
+        }
+        if (P.beta) {
+            const float4 X = __ldg(&M.ex[e]), Y = __ldg(&M.ey[e]);
+            const int4 V = __ldg(&M.ev[e]);
+            float l0, l1, l2;
+            barycentric(X, Y, x, y, l0, l1, l2);
+            const float* b0 = P.beta + (size_t)V.x * 3 * NS;
+            const float* b1 = P.beta + (size_t)V.y * 3 * NS;
+            const float* b2 = P.beta + (size_t)V.z * 3 * NS;
+#pragma unroll
+            for (int a = 0; a < NS; ++a) {
+                float bc[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    bc[c] = fmaf(l0, __ldg(b0 + 3 * a + c), fmaf(l1, __ldg(b1 + 3 * a + c), l2 * __ldg(b2 + 3 * a + c)));
+                cond[a] += bc[0] * Ur + bc[1] * Vr + bc[2] * Wr;
+            }
+        }
+        if (P.react_k > 0.0f) {
+            float pa = 0.0f, pb = 0.0f;
+#pragma unroll
+            for (int a = 0; a < NS; ++a) {
+                if (a == P.react_a) pa = p.psi[a];
+                if (a == P.react_b) pb = p.psi[a];
+            }
+            const float r = P.react_k * pa * pb;
+#pragma unroll
+            for (int a = 0; a < NS; ++a) {
+                if (a == P.react_a) src[a] -= r;
+                if (a == P.react_b) src[a] -= r;
+                if (a == P.react_p) src[a] += r;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < NS; ++a) p.psi[a] = p.psi[a] - (p.psi[a] - cond[a]) * mix + src[a] * P.dt;
+    } else {
+        // IEM: <phi|V> = <phi>
+#pragma unroll
+        for (int a = 0; a < NS; ++a) p.psi[a] = p.psi[a] - (p.psi[a] - Fi[LPDF_F_PHI0 + a]) * mix;
+    }
     // Eq. 2 with the velocity at t_n and the same dW_1, dW_2
     float qx = x + u * P.dt + P.s2nu * dW1;
     float qy = y + v * P.dt + P.s2nu * dW2;

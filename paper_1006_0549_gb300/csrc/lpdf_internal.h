@@ -67,6 +67,9 @@ struct StepParams {
     const CompParams* comp;   // per component (multi-component meshes), else NULL
     const unsigned long long* step_dev;   // if set, the step number is *step_dev + step_add
     unsigned step_add;
+    const float* beta;        // IECM: n_nodes x 3 ns conditional-mean slopes, else NULL (IEM)
+    float react_k;            // reactive source psi_a + psi_b -> psi_p (none when <= 0)
+    int react_a, react_b, react_p;
 };
 
 struct DevState {
@@ -137,8 +140,15 @@ constexpr int kAdvVariants = 5, kMomVariants = 4;
 cudaError_t launch_pdf_step_pipeline(const DevMesh& m, const DevState& cur, const DevState& nxt, int ns,
                                      const float* fields, const StepParams& p, PipeScratch& w,
                                      unsigned long long* node_acc, unsigned long long* status, cudaStream_t st,
-                                     const cudaEvent_t* ev, const StepTune& tune);
+                                     const cudaEvent_t* ev, const StepTune& tune,
+                                     unsigned long long* flux_acc = nullptr);
 cudaError_t launch_iota(int* p, int64_t n, cudaStream_t st);
+// scalar fluxes per node (raw sums or covariances; n_nodes x 3 ns FP64) from the fixed-point sums
+cudaError_t launch_flux_statistics(const int* master, int n_nodes, int ns, const unsigned long long* node_acc,
+                                   const unsigned long long* flux_acc, double* out, int raw, cudaStream_t st);
+// beta_a = R^-1 c_a per node (n_nodes x 3 ns FP32)
+cudaError_t launch_iecm_coefficients(int n_nodes, int ns, const double* stats, const double* flux, float* beta,
+                                     cudaStream_t st);
 // SMs of the current device (queried once; call it before a stream capture)
 int sm_count();
 // *c = set (add = 0) or *c += add, one thread
@@ -272,6 +282,8 @@ struct lpdf_ctx {
     lpdf::SortScratch sort;
     lpdf::PipeScratch pipe;
     unsigned long long* node_acc = nullptr;   // n_nodes x nq fixed-point sums
+    unsigned long long* flux_acc = nullptr;   // n_nodes x 3 ns fixed-point scalar-flux sums (IECM)
+    const float* iecm_beta = nullptr;         // lpdf_ctx_set_iecm
     unsigned long long* status = nullptr;     // 4 words
     int ns;
     int64_t nsteps = 0;                       // pdf_step calls so far

@@ -141,4 +141,76 @@ cudaError_t launch_grid_statistics(const DevMesh& m, int ns, const unsigned long
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------------
+// IECM (Eq. 9): scalar fluxes at the gridpoints, and the slopes of the conditional mean
+// ------------------------------------------------------------------------------------------
+__global__ void flux_statistics_kernel(const int* __restrict__ master, int n_nodes, int ns,
+                                       const unsigned long long* __restrict__ acc,
+                                       const unsigned long long* __restrict__ facc, double* __restrict__ out, int raw)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= n_nodes) return;
+    const int m = master[n];
+    const int nq = 11 + 2 * ns, nf = 3 * ns;
+    double* o = out + (size_t)n * nf;
+    const double s0 = (double)(long long)acc[(size_t)m * nq] * (1.0 / kFixScale);
+    for (int a = 0; a < ns; ++a)
+        for (int c = 0; c < 3; ++c) {
+            const double f = (double)(long long)facc[(size_t)m * nf + 3 * a + c] * (1.0 / kFixScale);
+            if (raw) {
+                o[3 * a + c] = f;
+            } else if (s0 == 0.0) {
+                o[3 * a + c] = 0.0;
+            } else {
+                const double su = (double)(long long)acc[(size_t)m * nq + 1 + c] * (1.0 / kFixScale);
+                const double sp = (double)(long long)acc[(size_t)m * nq + 11 + a] * (1.0 / kFixScale);
+                o[3 * a + c] = f / s0 - (su / s0) * (sp / s0);
+            }
+        }
+}
+
+// beta_a = R^-1 c_a by Cramer's rule (R symmetric, from the statistics columns uu, uv, uw, vv, vw,
+// ww); beta_a = 0 where det R <= 1e-12 (trace R / 3)^3
+__global__ void iecm_coefficients_kernel(int n_nodes, int ns, const double* __restrict__ stats,
+                                         const double* __restrict__ flux, float* __restrict__ beta)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= n_nodes) return;
+    const double* st = stats + (size_t)n * (11 + 2 * ns);
+    const double a11 = st[4], a12 = st[5], a13 = st[6], a22 = st[7], a23 = st[8], a33 = st[9];
+    // cofactors of the symmetric matrix
+    const double c11 = a22 * a33 - a23 * a23, c12 = a13 * a23 - a12 * a33, c13 = a12 * a23 - a13 * a22;
+    const double c22 = a11 * a33 - a13 * a13, c23 = a12 * a13 - a11 * a23, c33 = a11 * a22 - a12 * a12;
+    const double det = a11 * c11 + a12 * c12 + a13 * c13;
+    const double tr = fmax((a11 + a22 + a33) / 3.0, 0.0);
+    const bool ok = det > 1e-12 * tr * tr * tr;
+    for (int a = 0; a < ns; ++a) {
+        const double* f = flux + (size_t)n * 3 * ns + 3 * a;
+        float* b = beta + (size_t)n * 3 * ns + 3 * a;
+        if (!ok) {
+            b[0] = b[1] = b[2] = 0.0f;
+            continue;
+        }
+        b[0] = (float)((c11 * f[0] + c12 * f[1] + c13 * f[2]) / det);
+        b[1] = (float)((c12 * f[0] + c22 * f[1] + c23 * f[2]) / det);
+        b[2] = (float)((c13 * f[0] + c23 * f[1] + c33 * f[2]) / det);
+    }
+}
+
+cudaError_t launch_flux_statistics(const int* master, int n_nodes, int ns, const unsigned long long* node_acc,
+                                   const unsigned long long* flux_acc, double* out, int raw, cudaStream_t st)
+{
+    if (n_nodes <= 0) return cudaSuccess;
+    flux_statistics_kernel<<<(n_nodes + 255) / 256, 256, 0, st>>>(master, n_nodes, ns, node_acc, flux_acc, out, raw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iecm_coefficients(int n_nodes, int ns, const double* stats, const double* flux, float* beta,
+                                     cudaStream_t st)
+{
+    if (n_nodes <= 0) return cudaSuccess;
+    iecm_coefficients_kernel<<<(n_nodes + 255) / 256, 256, 0, st>>>(n_nodes, ns, stats, flux, beta);
+    return cudaGetLastError();
+}
+
 }  // namespace lpdf

@@ -520,14 +520,15 @@ __global__ void particle_scatter_kernel(int64_t n, const uint16_t* __restrict__ 
 // ------------------------------------------------------------------------------------------
 // K2
 // ------------------------------------------------------------------------------------------
-template <int NS, int MBLK, int MMINB>
+// kFlux: the same reduction of the scalar fluxes u_i psi_a (IECM) into their own accumulators
+template <int NS, int MBLK, int MMINB, bool kFlux = false>
 __global__ void __launch_bounds__(MBLK, MMINB) moments_kernel(const __grid_constant__ DevMesh M,
                                                       const __grid_constant__ DevState S,
                                                       const int* __restrict__ perm, const int* __restrict__ kstart,
                                                       unsigned long long* __restrict__ node_acc,
                                                       unsigned long long* __restrict__ status)
 {
-    constexpr int NQ = 11 + 2 * NS, NK = 3 * NQ;
+    constexpr int NQ = kFlux ? 3 * NS : 11 + 2 * NS, NK = 3 * NQ;
     const int e = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (e >= M.n_tri) return;
@@ -565,7 +566,7 @@ __global__ void __launch_bounds__(MBLK, MMINB) moments_kernel(const __grid_const
                 su[k] = S.u[j];
                 sv[k] = S.v[j];
                 sw[k] = S.w[j];
-                so[k] = S.om[j];
+                if (!kFlux) so[k] = S.om[j];
 #pragma unroll
                 for (int a = 0; a < NS; ++a) sp[k][a] = S.psi[(size_t)a * S.cap + j];
             }
@@ -574,13 +575,22 @@ __global__ void __launch_bounds__(MBLK, MMINB) moments_kernel(const __grid_const
                 if (idx[k0 + k] < 0) break;
                 float q[NQ];
                 const float u = su[k], v = sv[k], w = sw[k];
-                q[0] = 1.0f; q[1] = u; q[2] = v; q[3] = w;
-                q[4] = u * u; q[5] = u * v; q[6] = u * w; q[7] = v * v; q[8] = v * w; q[9] = w * w;
-                q[10] = so[k];
+                if (kFlux) {
 #pragma unroll
-                for (int a = 0; a < NS; ++a) {
-                    q[11 + a] = sp[k][a];
-                    q[11 + NS + a] = sp[k][a] * sp[k][a];
+                    for (int a = 0; a < NS; ++a) {
+                        q[3 * a] = u * sp[k][a];
+                        q[3 * a + 1] = v * sp[k][a];
+                        q[3 * a + 2] = w * sp[k][a];
+                    }
+                } else {
+                    q[0] = 1.0f; q[1] = u; q[2] = v; q[3] = w;
+                    q[4] = u * u; q[5] = u * v; q[6] = u * w; q[7] = v * v; q[8] = v * w; q[9] = w * w;
+                    q[10] = so[k];
+#pragma unroll
+                    for (int a = 0; a < NS; ++a) {
+                        q[11 + a] = sp[k][a];
+                        q[11 + NS + a] = sp[k][a] * sp[k][a];
+                    }
                 }
                 float l0, l1, l2;
                 barycentric(X, Y, sx[k], sy[k], l0, l1, l2);
@@ -693,7 +703,7 @@ void launch_moments(int v, const DevMesh& m, const DevState& s, const int* perm,
 template <int NS>
 cudaError_t run_pipeline(const DevMesh& m, const DevState& cur, const DevState& nxt, const float* fields,
                          const StepParams& p, PipeScratch& w, unsigned long long* node_acc, unsigned long long* status,
-                         cudaStream_t st, const cudaEvent_t* ev, const StepTune& tune)
+                         cudaStream_t st, const cudaEvent_t* ev, const StepTune& tune, unsigned long long* flux_acc)
 {
     const int64_t n = cur.n;
     if (n == 0) return cudaSuccess;
@@ -707,8 +717,10 @@ cudaError_t run_pipeline(const DevMesh& m, const DevState& cur, const DevState& 
     if (ev) cudaEventRecord(ev[0], st);
     constexpr int NQ4 = (22 + NS + 3) / 4;
     element_fields_kernel<NS><<<nblocks((int64_t)E * NQ4, 256), 256, 0, st>>>(m, fields, w.efields);
-    // the general kernel for several components or walls off the frame, the plain one otherwise
-    if (m.n_comp > 1 || m.edge_walls) launch_advance<NS, true>(tune.adv, m, cur, nxt, w.perm, w.efields, p, status, st);
+    // the general kernel for several components, walls off the frame, IECM or reactions; the plain
+    // one otherwise
+    if (m.n_comp > 1 || m.edge_walls || p.beta || p.react_k > 0.0f)
+        launch_advance<NS, true>(tune.adv, m, cur, nxt, w.perm, w.efields, p, status, st);
     else launch_advance<NS, false>(tune.adv, m, cur, nxt, w.perm, w.efields, p, status, st);
     if (ev) cudaEventRecord(ev[1], st);
     histogram_kernel<<<(unsigned)((nblk + kHWarps - 1) / kHWarps), 32 * kHWarps, 0, st>>>(
@@ -721,6 +733,9 @@ cudaError_t run_pipeline(const DevMesh& m, const DevState& cur, const DevState& 
     particle_scatter_kernel<<<nblocks(n, 256 * kScatterPer), 256, 0, st>>>(n, w.rrank, w.rec_off, w.perm_new);
     if (ev) cudaEventRecord(ev[2], st);
     launch_moments<NS>(tune.mom, m, nxt, w.perm_new, w.kstart, node_acc, status, st);
+    if (flux_acc)
+        moments_kernel<NS, 256, 2, true><<<nblocks((int64_t)E * 32, 256), 256, 0, st>>>(m, nxt, w.perm_new, w.kstart,
+                                                                                      flux_acc, status);
     if (ev) cudaEventRecord(ev[3], st);
     return cudaGetLastError();
 }
@@ -730,13 +745,13 @@ cudaError_t run_pipeline(const DevMesh& m, const DevState& cur, const DevState& 
 cudaError_t launch_pdf_step_pipeline(const DevMesh& m, const DevState& cur, const DevState& nxt, int ns,
                                      const float* fields, const StepParams& p, PipeScratch& w,
                                      unsigned long long* node_acc, unsigned long long* status, cudaStream_t st,
-                                     const cudaEvent_t* ev, const StepTune& tune)
+                                     const cudaEvent_t* ev, const StepTune& tune, unsigned long long* flux_acc)
 {
     switch (ns) {
-        case 1: return run_pipeline<1>(m, cur, nxt, fields, p, w, node_acc, status, st, ev, tune);
-        case 2: return run_pipeline<2>(m, cur, nxt, fields, p, w, node_acc, status, st, ev, tune);
-        case 3: return run_pipeline<3>(m, cur, nxt, fields, p, w, node_acc, status, st, ev, tune);
-        case 4: return run_pipeline<4>(m, cur, nxt, fields, p, w, node_acc, status, st, ev, tune);
+        case 1: return run_pipeline<1>(m, cur, nxt, fields, p, w, node_acc, status, st, ev, tune, flux_acc);
+        case 2: return run_pipeline<2>(m, cur, nxt, fields, p, w, node_acc, status, st, ev, tune, flux_acc);
+        case 3: return run_pipeline<3>(m, cur, nxt, fields, p, w, node_acc, status, st, ev, tune, flux_acc);
+        case 4: return run_pipeline<4>(m, cur, nxt, fields, p, w, node_acc, status, st, ev, tune, flux_acc);
         default: return cudaErrorInvalidValue;
     }
 }

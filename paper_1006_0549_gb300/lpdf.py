@@ -39,7 +39,8 @@ EXPORTS = ("lpdf_params_default", "lpdf_last_error", "lpdf_version", "lpdf_mesh_
            "lpdf_mlp_create", "lpdf_mlp_free", "lpdf_mlp_set_params", "lpdf_mlp_get_params", "lpdf_mlp_fit_norm",
            "lpdf_mlp_forward", "lpdf_mlp_gradient", "lpdf_mlp_train", "lpdf_surrogate_features",
            "lpdf_mlp_set_policy", "lpdf_surrogate_relax_solve", "lpdf_mesh_load_multi", "lpdf_ctx_set_components",
-           "lpdf_particles_init_multi", "lpdf_pdf_steps", "lpdf_ctx_set_tune", "lpdf_ctx_autotune")
+           "lpdf_particles_init_multi", "lpdf_pdf_steps", "lpdf_ctx_set_tune", "lpdf_ctx_autotune",
+           "lpdf_grid_flux_statistics", "lpdf_iecm_coefficients", "lpdf_ctx_set_iecm")
 
 N_ADV_VARIANTS, N_MOM_VARIANTS = 5, 4
 
@@ -70,7 +71,9 @@ class Params(ctypes.Structure):
                 ("src_y", ctypes.c_float * MAX_SOURCES), ("src_r", ctypes.c_float * MAX_SOURCES),
                 ("src_alpha", ctypes.c_int32 * MAX_SOURCES),
                 ("gmodel", ctypes.c_int32), ("pressure_solve", ctypes.c_int32), ("cg_warm_start", ctypes.c_int32),
-                ("dpdx0", ctypes.c_double), ("dpdy0", ctypes.c_double)]
+                ("dpdx0", ctypes.c_double), ("dpdy0", ctypes.c_double),
+                ("mixing", ctypes.c_int32), ("react_a", ctypes.c_int32), ("react_b", ctypes.c_int32),
+                ("react_p", ctypes.c_int32), ("react_k", ctypes.c_double)]
 
 
 _lib = None
@@ -131,6 +134,9 @@ def lib():
     L.lpdf_particles_init_multi.argtypes = [vp, vp, vp, i32, vp]
     L.lpdf_pdf_steps.argtypes = [vp, vp, u64, i32, vp]
     L.lpdf_ctx_set_tune.argtypes = [vp, i32, i32]
+    L.lpdf_grid_flux_statistics.argtypes = [vp, vp, ctypes.c_int, vp]
+    L.lpdf_iecm_coefficients.argtypes = [vp, i32, vp, vp, vp, vp]
+    L.lpdf_ctx_set_iecm.argtypes = [vp, vp]
     L.lpdf_ctx_autotune.argtypes = [vp, vp, u64, i32, i32, vp, vp, vp, vp]
     for name in EXPORTS:
         f = getattr(L, name)
@@ -229,6 +235,11 @@ class Mesh:
                                                int(maxit), _ptr(it), _stream(stream)))
         return int(it[0]), int(it[1])
 
+    def iecm_coefficients(self, ns: int, stats, flux, beta, stream=None):
+        """lpdf_iecm_coefficients: beta (n_nodes x 3 ns FP32) from statistics and flux covariances."""
+        _check(lib().lpdf_iecm_coefficients(self.h, int(ns), _ptr(stats), _ptr(flux), _ptr(beta), _stream(stream)))
+        return beta
+
     def surrogate_features(self, params: Params, stats, feat, fields=None, tgt=None, stream=None):
         """lpdf_surrogate_features: per-node network inputs (feat, n_nodes x 8 float32, CUDA) and,
         with fields given, the targets taken from them (tgt, n_nodes x 7 float32, CUDA)."""
@@ -302,6 +313,16 @@ class Context:
     def pdf_steps(self, node_fields, step0: int, nsteps: int, stream=None):
         """lpdf_pdf_steps: nsteps steps from step0, pairs of steps replayed from a CUDA graph."""
         _check(lib().lpdf_pdf_steps(self.h, _ptr(node_fields), int(step0), int(nsteps), _stream(stream)))
+
+    def grid_flux_statistics(self, out, raw: bool = False, stream=None):
+        """lpdf_grid_flux_statistics: per node (u psi_a, v psi_a, w psi_a) sums or covariances (FP64)."""
+        _check(lib().lpdf_grid_flux_statistics(self.h, _ptr(out), int(raw), _stream(stream)))
+        return out
+
+    def set_iecm(self, beta):
+        """lpdf_ctx_set_iecm: the conditional-mean slopes (n_nodes x 3 ns FP32, CUDA) or None."""
+        self._iecm_beta = beta            # the context reads it at every step: keep it alive
+        _check(lib().lpdf_ctx_set_iecm(self.h, _ptr(beta)))
 
     def set_tune(self, adv: int, mom: int):
         _check(lib().lpdf_ctx_set_tune(self.h, int(adv), int(mom)))

@@ -28,10 +28,11 @@ def host_state(d, ns) -> wl.State:
 
 
 def oracle_params(p: lpdf.Params):
+    react = (p.react_k, p.react_a, p.react_b, p.react_p) if p.react_k > 0 else None
     return oracle.make_params(nu=p.nu, dt=p.dt, seed=p.seed, ns=p.ns,
                               sources=[(float(p.src_x[i]), float(p.src_y[i]), float(p.src_r[i]), int(p.src_alpha[i]))
                                        for i in range(p.n_sources)],
-                              C3=p.C3, C4=p.C4, Cphi=p.Cphi, lid_u=p.lid_u)
+                              C3=p.C3, C4=p.C4, Cphi=p.Cphi, lid_u=p.lid_u, react=react)
 
 
 def gpu_step(ctx: lpdf.Context, fields_dev, st: wl.State, step: int):
@@ -80,7 +81,7 @@ def wall_distance_points(mesh: wl.Mesh, px, py):
 
 
 def compare_step(mesh: wl.Mesh, om: oracle.OracleMesh, params: lpdf.Params, F, st_in: wl.State, step: int,
-                 g: wl.State, check_locate: bool = True):
+                 g: wl.State, check_locate: bool = True, beta=None):
     """Per-stage parity of one step from the same input state.
 
     1. FP32 state within RTOL of the oracle's FP64 step, except for particles whose discrete
@@ -94,7 +95,7 @@ def compare_step(mesh: wl.Mesh, om: oracle.OracleMesh, params: lpdf.Params, F, s
     # match the particles by pid
     g = reorder(g, match_pids(st_in.pid, g.pid))
     op = oracle_params(params)
-    res, oelem, aux, lost = oracle.pdf_step(om, op, F, st_in, step)
+    res, oelem, aux, lost = oracle.pdf_step(om, op, F, st_in, step, beta=beta)
     assert lost == 0
     diag = {}
     x0, x1, y0, y1 = mesh.box
