@@ -457,11 +457,11 @@ __device__ __forceinline__ void apply_sources(const SP& sp, float px, float py, 
 }
 
 // the sources of the particle's component (a multi-component mesh), or the step's
-template <int NS, bool kGeneral>
+template <int NS, int kKind>
 __device__ __forceinline__ void particle_sources(const DevMesh& M, const StepParams& P, int e, float px, float py,
                                                  float* psi)
 {
-    if (kGeneral && M.n_comp > 1) apply_sources<NS>(P.comp[__ldg(&M.ecomp[e])], px, py, psi);
+    if (kKind >= 1 && M.n_comp > 1) apply_sources<NS>(P.comp[__ldg(&M.ecomp[e])], px, py, psi);
     else apply_sources<NS>(P, px, py, psi);
 }
 
@@ -509,11 +509,11 @@ __device__ __forceinline__ void interpolate_fields(const DevMesh& M, const float
 }
 
 // On return p holds the new state except the element, which is the walk's start: the old
-// element, or 0 when the old one is outside the mesh (`bad`). kGeneral: the mesh may hold several
-// independent components (the particle's component, that of its element, gives the frame, the
-// Philox key and the sources) and walls off the frame (mirrored in the walk, not here); without
-// it, one component with walls on the frame's sides.
-template <int NS, bool kElementTable = false, bool kGeneral = false>
+// element, or 0 when the old one is outside the mesh (`bad`). kKind selects the code compiled in:
+// 0 one component, walls on the frame's sides, IEM; 1 also several independent components (the
+// particle's component, that of its element, gives the frame, the Philox key and the sources);
+// 2 also walls off the frame (mirrored in the walk, not here), IECM and reactive sources.
+template <int NS, bool kElementTable = false, int kKind = 0>
 __device__ __forceinline__ void advance_particle(const DevMesh& M, const float* __restrict__ F, const StepParams& P,
                                                  ParticleState<NS>& p, unsigned& err, bool& bad)
 {
@@ -523,7 +523,7 @@ __device__ __forceinline__ void advance_particle(const DevMesh& M, const float* 
     const int e = bad ? 0 : p.elem;
     float fx0 = M.x0, fx1 = M.x1, fy0 = M.y0, fy1 = M.y1;
     uint32_t key0 = P.key0, key1 = P.key1;
-    if (kGeneral && M.n_comp > 1) {
+    if (kKind >= 1 && M.n_comp > 1) {
         const int c = __ldg(&M.ecomp[e]);
         const float4 fr = __ldg(&M.cframe[c]);
         fx0 = fr.x;
@@ -568,7 +568,7 @@ __device__ __forceinline__ void advance_particle(const DevMesh& M, const float* 
     omn = fabsf(omn);
     // Eq. 9: relaxation to the conditional mean, 1/t_m = C_phi <omega> / 2
     const float mix = P.half_cphi * Om * P.dt;
-    if (kGeneral && (P.beta || P.react_k > 0.0f)) {
+    if (kKind == 2 && (P.beta || P.react_k > 0.0f)) {
         // IECM: <phi_a|V> = <phi_a> + beta_a . (U - <U>), beta interpolated by the shape functions of
         // the element's nodes; the reactive source psi_ra + psi_rb -> psi_rp; all from the state at t_n
         float cond[NS], src[NS];
@@ -624,7 +624,7 @@ __device__ __forceinline__ void advance_particle(const DevMesh& M, const float* 
         else if (qx >= fx1) qx -= M.period;
         if (qx < fx0 || qx >= fx1) qx -= floorf((qx - fx0) / M.period) * M.period;   // moves > one period
     }
-    if (!(kGeneral && M.edge_walls)) {
+    if (!(kKind == 2 && M.edge_walls)) {
         // walls on the frame's sides: mirror at the frame (edge walls are mirrored in the walk)
 #pragma unroll 1
         for (int it = 0; it < 8; ++it) {
@@ -641,7 +641,7 @@ __device__ __forceinline__ void advance_particle(const DevMesh& M, const float* 
         qx = fx0;
     }
     // concentrated scalar sources (with edge walls: after the walk, on the mirrored position)
-    if (!(kGeneral && M.edge_walls)) particle_sources<NS, kGeneral>(M, P, e, qx, qy, p.psi);
+    if (!(kKind == 2 && M.edge_walls)) particle_sources<NS, kKind>(M, P, e, qx, qy, p.psi);
     if (!(isfinite(un) && isfinite(vn) && isfinite(wn) && isfinite(omn) && isfinite(qx) && isfinite(qy)))
         err |= kErrNonFinite;
     p.x = qx;

@@ -122,7 +122,7 @@ static __device__ __noinline__ int walk_mirroring(const DevMesh& M, float lid_u,
 }
 
 // one particle: position i of the next buffer takes particle perm[i] of the current one
-template <int NS, bool kGeneral>
+template <int NS, int kKind>
 __device__ __forceinline__ void advance_one(const DevMesh& M, const DevState& cur, const DevState& nxt,
                                             const int* __restrict__ perm, const float* __restrict__ EF,
                                             const StepParams& P, unsigned long long* __restrict__ status, int64_t i,
@@ -141,7 +141,7 @@ __device__ __forceinline__ void advance_one(const DevMesh& M, const DevState& cu
     p.elem = ld_stream(cur.elem + src);
     p.pid = ld_stream(cur.pid + src);
     bool bad;
-    advance_particle<NS, true, kGeneral>(M, EF, P, p, err, bad);
+    advance_particle<NS, true, kKind>(M, EF, P, p, err, bad);
     // barycentric neighbour walk from the old element; with edge walls, a position found beyond
     // a wall edge is mirrored across that edge (U <- 2 U_w - U) and the walk goes on
     const int e0 = p.elem;
@@ -150,7 +150,7 @@ __device__ __forceinline__ void advance_one(const DevMesh& M, const DevState& cu
 #pragma unroll 1
     for (;;) {
         int next = -1;
-        int r = walk_test_fast<kGeneral>(M, e, p.x, p.y, next);
+        int r = walk_test_fast<kKind == 2>(M, e, p.x, p.y, next);
         if (r < 0) {
             float lam[3];
             r = walk_test(M, e, p.x, p.y, lam, next) ? 1 : 0;
@@ -160,7 +160,7 @@ __device__ __forceinline__ void advance_one(const DevMesh& M, const DevState& cu
             hops += h;
             break;
         }
-        if (kGeneral && next < 0 && M.edge_walls) {
+        if (kKind == 2 && next < 0 && M.edge_walls) {
             ne = walk_mirroring(M, P.lid_u, e, next, h, p.x, p.y, p.u, p.v, p.w);
             lost = ne < 0;
             hops += h;
@@ -175,7 +175,7 @@ __device__ __forceinline__ void advance_one(const DevMesh& M, const DevState& cu
         ++h;
     }
     if (lost) ne = e0;
-    if (kGeneral && M.edge_walls) particle_sources<NS, kGeneral>(M, P, e0, p.x, p.y, p.psi);
+    if (kKind == 2 && M.edge_walls) particle_sources<NS, kKind>(M, P, e0, p.x, p.y, p.psi);
     if (lost || bad) {
         err |= kErrLost;
         atomicAdd(&status[1], 1ull);
@@ -196,7 +196,7 @@ __device__ __forceinline__ void advance_one(const DevMesh& M, const DevState& cu
 // K1 variants (the autotuner picks one per context; all give bit-identical results): ABLK
 // threads per CTA, at least MINB CTAs per SM (the register cap), and either one particle per
 // thread over the whole grid or a persistent grid striding over ABLK-particle tiles.
-template <int NS, bool kGeneral, int ABLK, int MINB, bool kPersist>
+template <int NS, int kKind, int ABLK, int MINB, bool kPersist>
 __global__ void __launch_bounds__(ABLK, MINB)
 advance_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevState cur,
                const __grid_constant__ DevState nxt, const int* __restrict__ perm, const float* __restrict__ EF,
@@ -209,7 +209,7 @@ advance_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevSta
 #pragma unroll 1
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += kPersist ? gridDim.x : ntiles) {
         const int64_t i = tile * ABLK + threadIdx.x;
-        if (i < cur.n) advance_one<NS, kGeneral>(M, cur, nxt, perm, EF, P, status, i, err, hops);
+        if (i < cur.n) advance_one<NS, kKind>(M, cur, nxt, perm, EF, P, status, i, err, hops);
     }
     const unsigned e_or = __reduce_or_sync(kFull, err);
     const int h_sum = __reduce_add_sync(kFull, hops);
@@ -665,25 +665,25 @@ int sm_count_cached()
     return n;
 }
 
-template <int NS, bool kGeneral, int ABLK, int MINB, bool kPersist>
+template <int NS, int kKind, int ABLK, int MINB, bool kPersist>
 void launch_advance_v(const DevMesh& m, const DevState& cur, const DevState& nxt, const int* perm, const float* ef,
                       const StepParams& p, unsigned long long* status, cudaStream_t st)
 {
     const int64_t ntiles = (cur.n + ABLK - 1) / ABLK;
     const int64_t grid = kPersist ? std::min<int64_t>(ntiles, (int64_t)sm_count_cached() * MINB) : ntiles;
-    advance_kernel<NS, kGeneral, ABLK, MINB, kPersist><<<(unsigned)grid, ABLK, 0, st>>>(m, cur, nxt, perm, ef, p, status);
+    advance_kernel<NS, kKind, ABLK, MINB, kPersist><<<(unsigned)grid, ABLK, 0, st>>>(m, cur, nxt, perm, ef, p, status);
 }
 
-template <int NS, bool kGeneral>
+template <int NS, int kKind>
 void launch_advance(int v, const DevMesh& m, const DevState& cur, const DevState& nxt, const int* perm,
                     const float* ef, const StepParams& p, unsigned long long* status, cudaStream_t st)
 {
     switch (v) {
-        case 1: launch_advance_v<NS, kGeneral, 256, 6, false>(m, cur, nxt, perm, ef, p, status, st); break;
-        case 2: launch_advance_v<NS, kGeneral, 128, 8, false>(m, cur, nxt, perm, ef, p, status, st); break;
-        case 3: launch_advance_v<NS, kGeneral, 256, 4, true>(m, cur, nxt, perm, ef, p, status, st); break;
-        case 4: launch_advance_v<NS, kGeneral, 256, 6, true>(m, cur, nxt, perm, ef, p, status, st); break;
-        default: launch_advance_v<NS, kGeneral, 256, 4, false>(m, cur, nxt, perm, ef, p, status, st); break;
+        case 1: launch_advance_v<NS, kKind, 256, 6, false>(m, cur, nxt, perm, ef, p, status, st); break;
+        case 2: launch_advance_v<NS, kKind, 128, 8, false>(m, cur, nxt, perm, ef, p, status, st); break;
+        case 3: launch_advance_v<NS, kKind, 256, 4, true>(m, cur, nxt, perm, ef, p, status, st); break;
+        case 4: launch_advance_v<NS, kKind, 256, 6, true>(m, cur, nxt, perm, ef, p, status, st); break;
+        default: launch_advance_v<NS, kKind, 256, 4, false>(m, cur, nxt, perm, ef, p, status, st); break;
     }
 }
 
@@ -717,11 +717,12 @@ cudaError_t run_pipeline(const DevMesh& m, const DevState& cur, const DevState& 
     if (ev) cudaEventRecord(ev[0], st);
     constexpr int NQ4 = (22 + NS + 3) / 4;
     element_fields_kernel<NS><<<nblocks((int64_t)E * NQ4, 256), 256, 0, st>>>(m, fields, w.efields);
-    // the general kernel for several components, walls off the frame, IECM or reactions; the plain
-    // one otherwise
-    if (m.n_comp > 1 || m.edge_walls || p.beta || p.react_k > 0.0f)
-        launch_advance<NS, true>(tune.adv, m, cur, nxt, w.perm, w.efields, p, status, st);
-    else launch_advance<NS, false>(tune.adv, m, cur, nxt, w.perm, w.efields, p, status, st);
+    // the kernel with the least code that covers the mesh and the model: walls off the frame,
+    // IECM or reactions (kind 2); several components (kind 1); the plain step (kind 0)
+    if (m.edge_walls || p.beta || p.react_k > 0.0f)
+        launch_advance<NS, 2>(tune.adv, m, cur, nxt, w.perm, w.efields, p, status, st);
+    else if (m.n_comp > 1) launch_advance<NS, 1>(tune.adv, m, cur, nxt, w.perm, w.efields, p, status, st);
+    else launch_advance<NS, 0>(tune.adv, m, cur, nxt, w.perm, w.efields, p, status, st);
     if (ev) cudaEventRecord(ev[1], st);
     histogram_kernel<<<(unsigned)((nblk + kHWarps - 1) / kHWarps), 32 * kHWarps, 0, st>>>(
         nxt.elem, n, w.rrank, w.rec_key, w.rec_cnt, w.nrec, kcnt, krc, status);
