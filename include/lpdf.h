@@ -449,6 +449,9 @@ int lpdf_surrogate_features(const lpdf_mesh* mesh, const lpdf_params* params, co
 /* lpdf_mlp_set_policy -- the fallback policy of lpdf_surrogate_relax_solve: every check_every-th
  * call (the first call included; 0: never) also runs the plain solve and compares. */
 int lpdf_mlp_set_policy(lpdf_mlp* m, int32_t check_every, double threshold);
+/* lpdf_mlp_request_check -- the next lpdf_surrogate_relax_solve call checks (for example after
+ * the network was trained further on the fields of a failed check), whatever the cadence. */
+int lpdf_mlp_request_check(lpdf_mlp* m);
 
 /* lpdf_surrogate_relax_solve -- lpdf_elliptic_relax_solve (gmodel 0) with G_ij and C0 eps from
  * the network. sync. Everything else (gradients, Laplacians, pressure, S_omega) is computed as

@@ -37,6 +37,7 @@ struct lpdf_mlp {
     double threshold = 0.02;
     int64_t calls = 0;
     bool net_ok = false;
+    bool check_next = false;   // lpdf_mlp_request_check
 };
 
 namespace {
@@ -266,6 +267,13 @@ int lpdf_mlp_set_policy(lpdf_mlp* m, int32_t check_every, double threshold)
     return LPDF_OK;
 }
 
+int lpdf_mlp_request_check(lpdf_mlp* m)
+{
+    if (!m) return lpdf_set_error(LPDF_ERR_ARG, "mlp_request_check: NULL argument");
+    m->check_next = true;
+    return LPDF_OK;
+}
+
 int lpdf_surrogate_relax_solve(const lpdf_mesh* mesh, lpdf_mlp* m, const lpdf_params* params, const double* stats,
                                float* fields, double tol, int32_t maxit, double* info, void* stream)
 {
@@ -281,7 +289,8 @@ int lpdf_surrogate_relax_solve(const lpdf_mesh* mesh, lpdf_mlp* m, const lpdf_pa
     const int nfp = nfields_padded(params->ns);
     if (const int rc = grow(&m->s_feat, m->s_feat_cap, N * kIn)) return rc;
     if (const int rc = grow(&m->s_out, m->s_out_cap, N * kOutP)) return rc;
-    const bool check = m->check_every > 0 && m->calls % m->check_every == 0;
+    const bool check = m->check_next || (m->check_every > 0 && m->calls % m->check_every == 0);
+    m->check_next = false;
     ++m->calls;
     const bool use_net = check || m->net_ok;
     const bool use_plain = check || !m->net_ok;

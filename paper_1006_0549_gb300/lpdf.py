@@ -40,7 +40,7 @@ EXPORTS = ("lpdf_params_default", "lpdf_last_error", "lpdf_version", "lpdf_mesh_
            "lpdf_mlp_forward", "lpdf_mlp_gradient", "lpdf_mlp_train", "lpdf_surrogate_features",
            "lpdf_mlp_set_policy", "lpdf_surrogate_relax_solve", "lpdf_mesh_load_multi", "lpdf_ctx_set_components",
            "lpdf_particles_init_multi", "lpdf_pdf_steps", "lpdf_ctx_set_tune", "lpdf_ctx_autotune",
-           "lpdf_grid_flux_statistics", "lpdf_iecm_coefficients", "lpdf_ctx_set_iecm")
+           "lpdf_grid_flux_statistics", "lpdf_iecm_coefficients", "lpdf_ctx_set_iecm", "lpdf_mlp_request_check")
 
 N_ADV_VARIANTS, N_MOM_VARIANTS = 5, 4
 
@@ -128,6 +128,7 @@ def lib():
     L.lpdf_mlp_train.argtypes = [vp, vp, vp, i64, i64, i32, ctypes.c_float, vp, vp]
     L.lpdf_surrogate_features.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.lpdf_mlp_set_policy.argtypes = [vp, i32, ctypes.c_double]
+    L.lpdf_mlp_request_check.argtypes = [vp]
     L.lpdf_surrogate_relax_solve.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, i32, vp, vp]
     L.lpdf_mesh_load_multi.argtypes = [vp, i32, vp, i32, vp, i32, vp, vp, ctypes.c_double, vp]
     L.lpdf_ctx_set_components.argtypes = [vp, vp, i32]
@@ -433,6 +434,7 @@ class MLP:
         _check(lib().lpdf_mlp_create(int(max_batch), ctypes.byref(h)))
         self.h = h
         self.max_batch = int(max_batch)
+        self.check_every, self.threshold = 50, 0.02
 
     def __del__(self):
         try:
@@ -481,6 +483,11 @@ class MLP:
 
     def set_policy(self, check_every: int = 50, threshold: float = 0.02):
         _check(lib().lpdf_mlp_set_policy(self.h, int(check_every), float(threshold)))
+        self.check_every, self.threshold = int(check_every), float(threshold)
+
+    def request_check(self):
+        """lpdf_mlp_request_check: the next surrogate solve checks against the plain solve."""
+        _check(lib().lpdf_mlp_request_check(self.h))
 
 
 def version() -> str:

@@ -104,3 +104,44 @@ def relative_difference(a, b, cols):
     a = np.asarray(a)[:, cols]
     b = np.asarray(b)[:, cols]
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def run_surrogate(loop: TimeLoop, net: lpdf.MLP, steps: int, train_feat=None, train_tgt=None, retrain_steps: int = 0,
+                  retrain_lr: float = 3e-4, batch: int = 1024, seed: int = 17):
+    """`steps` steps with the surrogate solve. With retrain_steps > 0 the network keeps learning:
+    a failed check (its plain fields are the step's fields) adds that step's inputs and targets to
+    a set of new rows, the network takes retrain_steps more Adam steps on the new rows mixed with
+    as many rows drawn from the earlier training data (train_feat, train_tgt), and the next solve
+    checks again. Returns a dict of what happened (per-step solve times, whether the plain solve
+    ran, check errors, calls on the network, retrainings)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    new_f, new_t = [], []
+    times, errs, used, retrains = [], [], 0, 0
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        checked, err, used_plain, _ = loop.solve_surrogate(net)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append((e0.elapsed_time(e1), used_plain))
+        if checked:
+            errs.append(err)
+        used += 0 if used_plain else 1
+        if checked and retrain_steps > 0 and err > net.threshold:
+            f, t = loop.features(True)
+            new_f.append(f)
+            new_t.append(t)
+            Fn, Tn = torch.cat(new_f), torch.cat(new_t)
+            if train_feat is not None:
+                pick = torch.from_numpy(rng.integers(0, train_feat.shape[0], Fn.shape[0])).to(Fn.device)
+                Fn, Tn = torch.cat([Fn, train_feat[pick]]), torch.cat([Tn, train_tgt[pick]])
+            perm = torch.from_numpy(rng.permutation(Fn.shape[0])).to(Fn.device)
+            n = max(batch, Fn.shape[0] // batch * batch)
+            b = min(batch, Fn.shape[0])
+            net.train(Fn[perm][:n].contiguous(), Tn[perm][:n].contiguous(), batch=b, steps=retrain_steps,
+                      lr=retrain_lr)
+            net.request_check()
+            retrains += 1
+        loop.advance()
+    return {"times": times, "check_errors": errs, "network_used_on": used, "retrains": retrains}

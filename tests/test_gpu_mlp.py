@@ -214,3 +214,10 @@ def test_surrogate_solve_checks_falls_back_and_uses_the_network(torch_cuda):
     # every other column is the plain solve's
     other = [c for c in range(22 + 1) if not 14 <= c <= 19]
     assert np.allclose(got[:, other], plain[:, other], rtol=1e-6, atol=1e-6)
+    # a requested check runs on the next call whatever the cadence, once
+    net.set_policy(check_every=1000, threshold=1e30)
+    net.request_check()
+    checked, err, used_plain, _ = gm.surrogate_relax_solve(net, params, S, out, 1e-10)
+    assert checked and used_plain and err > 0.0
+    checked, _, _, _ = gm.surrogate_relax_solve(net, params, S, out, 1e-10)
+    assert not checked
