@@ -195,6 +195,15 @@ struct Fem {
     int* ncomp = nullptr;        // component of every geometric node
     int nseg = 0, n_comp = 1;
     double period = 0.0;         // x period (0: none)
+    // CUDA graphs of kCheckEvery CG iterations, one per call site (its matrix, diagonal, solution
+    // and scratch pointers, component count and wall mask)
+    struct CgGraph {
+        const void* key[4];
+        int nv, mask;
+        cudaGraphExec_t exec;
+    };
+    std::vector<CgGraph> cg_graphs;
+    cudaStream_t capture_stream = nullptr;
     double* wdist = nullptr;     // per geometric node, filled on first use: distance to the wall,
     int* wseg = nullptr;         //   the wall edge of the nearest wall point
     double* wt = nullptr;        //   and its position on that edge (0 at a, 1 at b)

@@ -743,6 +743,8 @@ void fem_free(Fem* F)
                   F->xy, F->seg, F->segn, F->seg_off, F->ncomp, F->wdist, F->wseg, F->wt};
     for (void* p : ps) cudaFree(p);
     cudaFreeHost(F->scal_host);
+    for (auto& g : F->cg_graphs) cudaGraphExecDestroy(g.exec);
+    if (F->capture_stream) cudaStreamDestroy(F->capture_stream);
     delete F;
 }
 
@@ -783,6 +785,37 @@ cudaError_t pcg(const Fem& F, const double* A, const double* diag, const double*
     if (!xref) launch_dot(F, r, r, nv, kR0, 0, st);
     launch_dot(F, r, r, nv, kRR, 0, st);
     launch_dot(F, r, z, nv, kRZ, 0, st);
+    // one CG iteration: five launches (SpMV with the p.q dot, alpha, update with the r.z and r.r
+    // dots, beta, new direction)
+    auto iteration = [&](cudaStream_t s) {
+        spmv_dot_kernel<<<nb, kDotThreads, 0, s>>>(F, A, p, q, mask, nv, F.part);
+        scalar_kernel<<<1, 32, 0, s>>>(F.part, nb, nv, kDot, 1, F.scal);          // alpha = rz / pq
+        update_dot_kernel<<<nb, kDotThreads, 0, s>>>((int)n, nv, F.scal, diag, p, q, x, r, z, part_rz, part_rr);
+        scalar_beta_kernel<<<1, 32, 0, s>>>(part_rz, part_rr, nb, nv, F.scal);    // beta, rz, rr
+        cg_direction_kernel<<<g, 256, 0, s>>>((int)n, nv, F.scal, z, p);
+    };
+    // kCheckEvery iterations between two convergence tests replay one CUDA graph, captured once per
+    // call site (the scalars live on the device, so a replay needs no host work)
+    cudaGraphExec_t exec = nullptr;
+    for (const auto& cg : F.cg_graphs)
+        if (cg.key[0] == A && cg.key[1] == diag && cg.key[2] == x && cg.key[3] == scratch && cg.nv == nv &&
+            cg.mask == mask)
+            exec = cg.exec;
+    if (!exec) {
+        Fem& Fm = const_cast<Fem&>(F);
+        cudaError_t e = cudaSuccess;
+        if (!Fm.capture_stream) e = cudaStreamCreateWithFlags(&Fm.capture_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(Fm.capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            for (int k = 0; k < kCheckEvery; ++k) iteration(Fm.capture_stream);
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamEndCapture(Fm.capture_stream, &graph);
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+        }
+        if (e != cudaSuccess) return e;
+        Fm.cg_graphs.push_back({{A, diag, x, scratch}, nv, mask, exec});
+    }
     double r0[4] = {0, 0, 0, 0};
     int it = 0;
     bool done = false;
@@ -798,12 +831,14 @@ cudaError_t pcg(const Fem& F, const double* A, const double* diag, const double*
                 if (std::sqrt(F.scal_host[kRR + c]) > tol * r0[c]) done = false;
             if (done || it >= maxit) break;
         }
-        spmv_dot_kernel<<<nb, kDotThreads, 0, st>>>(F, A, p, q, mask, nv, F.part);
-        scalar_kernel<<<1, 32, 0, st>>>(F.part, nb, nv, kDot, 1, F.scal);          // alpha = rz / pq
-        update_dot_kernel<<<nb, kDotThreads, 0, st>>>((int)n, nv, F.scal, diag, p, q, x, r, z, part_rz, part_rr);
-        scalar_beta_kernel<<<1, 32, 0, st>>>(part_rz, part_rr, nb, nv, F.scal);    // beta, rz, rr
-        cg_direction_kernel<<<g, 256, 0, st>>>((int)n, nv, F.scal, z, p);
-        ++it;
+        if (it % kCheckEvery == 0 && it + kCheckEvery <= maxit) {
+            const cudaError_t e = cudaGraphLaunch(exec, st);
+            if (e != cudaSuccess) return e;
+            it += kCheckEvery;
+        } else {
+            iteration(st);
+            ++it;
+        }
     }
     *iters = it;
     cudaError_t e = cudaGetLastError();
