@@ -155,10 +155,29 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(load)}
 
 
+def replica_seed(rank: int) -> int:
+    """Each rank runs an independent replica of the ensemble (replicas only: the path has no
+    exchange between ensembles), drawn from its own seed."""
+    return 1006054902 + 7919 * rank
+
+
+def combine_ranks(dist, maxed, summed, device):
+    """The job-wide figures of a replicated run: the maximum over ranks of the times (`maxed`)
+    and the sum of the work (`summed`); no collective on the data path, only this one at the end."""
+    if dist is None:
+        return list(maxed), list(summed)
+    import torch
+    t = torch.tensor(list(maxed), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor(list(summed), dtype=torch.float64, device=device)
+    dist.all_reduce(n)
+    return [float(v) for v in t], [float(v) for v in n]
+
+
 def build_workload(rank: int, ppe: int):
     import torch
     from paper_1006_0549_gb300 import lpdf, workloads as wl
-    wk = wl.channel_25m(seed=1006054902 + 7919 * rank)
+    wk = wl.channel_25m(seed=replica_seed(rank))
     wk.n_per_elem = ppe
     mesh = lpdf.Mesh(wk.mesh)
     params = lpdf.params_for(wk)
@@ -516,16 +535,7 @@ def main():
     r = run_gpu(args, rank, world, dist)
     total_ms = r["total_ms"]
     P = r["P"]
-    if dist is not None:
-        t = torch.tensor([total_ms, r["e2e_s"]], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, e2e_s = float(t[0]), float(t[1])
-        n_all = torch.tensor([P], dtype=torch.float64, device="cuda")
-        dist.all_reduce(n_all)
-        P_all = float(n_all[0])
-    else:
-        e2e_s = r["e2e_s"]
-        P_all = float(P)
+    (total_ms, e2e_s), (P_all,) = combine_ranks(dist, [total_ms, r["e2e_s"]], [float(P)], "cuda")
     if rank != 0:
         dist.destroy_process_group()
         return
