@@ -379,7 +379,8 @@ def run_batched(steps: int, warmup: int):
             "setup_s": setup_s}
 
 
-def run_surrogate(wk, train_steps: int, run_steps: int, check_every: int, threshold: float):
+def run_surrogate(wk, train_steps: int, run_steps: int, check_every: int, threshold: float, pressure_solve: int = 0,
+                  dpdx0: float = -1.0, tol: float = 1e-8, maxit: int = 20000):
     """The learned surrogate of the gridpoint solve beside the plain solve, in the coupled time loop
     of the same workload: train on the fields of `train_steps` plain steps (on the GPU, with the
     library's forward and backward kernels), then continue from one state for `run_steps` steps with
@@ -388,8 +389,8 @@ def run_surrogate(wk, train_steps: int, run_steps: int, check_every: int, thresh
     stresses and the scalar variance."""
     import torch
     from paper_1006_0549_gb300 import lpdf, timeloop as tl
-    params = lpdf.params_for(wk, gmodel=0, pressure_solve=0, dpdx0=-1.0)
-    loop = tl.TimeLoop(wk, params)
+    params = lpdf.params_for(wk, gmodel=0, pressure_solve=pressure_solve, dpdx0=dpdx0)
+    loop = tl.TimeLoop(wk, params, tol=tol, maxit=maxit)
     t = time.perf_counter()
     feat, tgt = tl.collect_training_data(loop, train_steps)
     torch.cuda.synchronize()
@@ -426,14 +427,16 @@ def run_surrogate(wk, train_steps: int, run_steps: int, check_every: int, thresh
 
     p0, n0 = net.get_params()
     plain, t_plain = run_plain(params)
-    other = lpdf.params_for(wk, gmodel=0, pressure_solve=0, dpdx0=-1.0)
+    other = lpdf.params_for(wk, gmodel=0, pressure_solve=pressure_solve, dpdx0=dpdx0)
     other.seed = params.seed + 12345
     spread, _ = run_plain(other)
     surr, t_surr, r_fixed = run_net(0)
     surr_rt, t_surr_rt, r_rt = run_net(400)
     errs, used = r_fixed["check_errors"], r_fixed["network_used_on"]
     R, PHI = [4, 5, 6, 7, 8, 9], [11 + wk.ns + a for a in range(wk.ns)]
-    return {"workload": f"{wk.name}, coupled loop (elliptic relaxation, fixed mean pressure gradient)",
+    solve = "elliptic relaxation and mean-pressure CGs" if pressure_solve else \
+        "elliptic relaxation, fixed mean pressure gradient"
+    return {"workload": f"{wk.name}, coupled loop ({solve})",
             "train_steps": train_steps, "train_rows": int(feat.shape[0]), "adam_steps": int(len(losses)),
             "final_loss": float(np.mean(losses[-200:])), "collect_s": collect_s, "train_s": train_s,
             "run_steps": run_steps, "check_every": check_every, "threshold": threshold,
@@ -486,6 +489,8 @@ def main():
     ap.add_argument("--surrogate-run-steps", type=int, default=40)
     ap.add_argument("--batched", type=int, default=1, help="1: also report the 64-ensemble batched step")
     ap.add_argument("--cavity", type=int, default=1, help="1: also report the 20M-particle cavity step")
+    ap.add_argument("--surrogate-cavity", type=int, default=0,
+                    help="steps of the cavity surrogate report (training and run; 0: none)")
     ap.add_argument("--tune", default="auto",
                     help="launch configuration of the step: 'auto' (the library's autotuner) or 'adv,mom'")
     ap.add_argument("--ppe", type=int, default=500,
@@ -551,9 +556,13 @@ def main():
     cpu_n, cpu_dt = cpu_baseline_sample(r["wk"], args.cpu_sample)
     batched = run_batched(args.steps, args.warmup) if args.batched else None
     cavity = run_cavity(args.steps, args.warmup, peak) if args.cavity else None
-    surrogate = None
+    surrogate = surrogate_cavity = None
     if args.surrogate_train_steps > 0:
         surrogate = run_surrogate(r["wk"], args.surrogate_train_steps, args.surrogate_run_steps, 10, 0.02)
+    if args.surrogate_cavity:
+        from paper_1006_0549_gb300 import workloads as wl
+        surrogate_cavity = run_surrogate(wl.cavity_20m(), args.surrogate_cavity, args.surrogate_cavity, 5, 0.02,
+                                         pressure_solve=0, dpdx0=0.0, tol=1e-8, maxit=20000)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -577,6 +586,7 @@ def main():
         "gpu_launches": K * LAUNCHES_PER_STEP,
         "gridpoint_solve": r["solve"],
         "surrogate": surrogate,
+        "surrogate_cavity": surrogate_cavity,
         "batched": batched,
         "cavity": cavity,
         "tune": r["tune"],
