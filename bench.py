@@ -456,18 +456,20 @@ def run_surrogate(wk, train_steps: int, run_steps: int, check_every: int, thresh
                     "over the calls that ran the plain solve alone / the network alone"}
 
 
-def cpu_baseline_sample(wk, n_sample: int):
-    """FP64 oracle (single-threaded C) on the first n_sample particles of a fresh initialisation
-    of the same workload: one step plus the gridpoint moments."""
+def cpu_baseline_sample(wk, n_sample: int, first_elem: int = 0):
+    """FP64 oracle (single-threaded C) on n_sample particles of the same workload (the particles of
+    the elements from first_elem on, at the workload's particles per element): one step plus the
+    gridpoint moments."""
     import oracle
     from paper_1006_0549_gb300 import workloads as wl
     om = oracle.OracleMesh(wk.mesh)
     p = oracle.make_params(nu=wk.nu, dt=wk.dt, seed=wk.seed, ns=wk.ns, sources=wk.sources, lid_u=wk.lid_u)
-    # initial state of the sample: the oracle's own initialisation of those elements' particles
     n_el = max(1, n_sample // wk.n_per_elem)
-    sub = wl.Mesh(wk.mesh.node_xy, wk.mesh.tri[:n_el], wk.mesh.edge_tag[:n_el], wk.mesh.period_x, wk.mesh.box,
-                  wk.mesh.kind, wk.mesh.nx, wk.mesh.ny)
+    e0 = min(first_elem, wk.mesh.n_tri - n_el)
+    sub = wl.Mesh(wk.mesh.node_xy, wk.mesh.tri[e0:e0 + n_el], wk.mesh.edge_tag[e0:e0 + n_el], wk.mesh.period_x,
+                  wk.mesh.box, wk.mesh.kind, wk.mesh.nx, wk.mesh.ny)
     st = wl.synthetic_state(sub, wk.n_per_elem, wk.ns, seed=3)
+    st.elem = (st.elem + e0).astype(np.int32)
     F = wl.synthetic_node_fields(wk.mesh, wk.ns, seed=5)
     t = time.perf_counter()
     res, elem, aux, lost = oracle.pdf_step(om, p, F, st, 0)
@@ -475,6 +477,39 @@ def cpu_baseline_sample(wk, n_sample: int):
                           elem, with_abs=False)
     dt = time.perf_counter() - t
     return st.n, dt
+
+
+def _cpu_worker(args):
+    """One host core's share of the parallel oracle baseline (a process of its own)."""
+    sys.path.insert(0, ROOT)
+    from paper_1006_0549_gb300 import workloads as wl
+    n_sample, first_elem = args
+    wk = wl.channel_25m()
+    return cpu_baseline_sample(wk, n_sample, first_elem)
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def cpu_baseline_parallel(n_per_core: int, cores: int):
+    """The oracle on every host core at once: `cores` processes (started with spawn), each on its
+    own elements of the 25M channel; particles per second = all particles / the slowest process."""
+    import multiprocessing as mpr
+    per_elem = 500
+    chunks = [(n_per_core, k * (n_per_core // per_elem)) for k in range(cores)]
+    with mpr.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_cpu_worker, chunks)
+    n = sum(r[0] for r in res)
+    return n, max(r[1] for r in res)
 
 
 def main():
@@ -554,6 +589,8 @@ def main():
     step_gbs = BYTES_PER_UPDATE * P / (ms_step * 1e-3) / 1e9
     traffic = ncu_traffic(P, r["tune"]["advance_variant"])
     cpu_n, cpu_dt = cpu_baseline_sample(r["wk"], args.cpu_sample)
+    ncores = os.cpu_count() or 1
+    par_n, par_dt = cpu_baseline_parallel(max(500, args.cpu_sample // ncores), ncores)
     batched = run_batched(args.steps, args.warmup) if args.batched else None
     cavity = run_cavity(args.steps, args.warmup, peak) if args.cavity else None
     surrogate = surrogate_cavity = None
@@ -577,8 +614,10 @@ def main():
                      "kernel": "advance_kernel", "bytes_per_update": BYTES_PER_UPDATE,
                      "kernel_ms": kms["advance"], "kernels_ms_per_step": kms,
                      "step_achieved_gbs": step_gbs, "step_frac": step_gbs / peak},
-        "cpu_baseline": {"value": cpu_n / cpu_dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{cpu_n} particles of the same workload, one FP64 step + gridpoint moments"},
+        "cpu_baseline": {"value": par_n / par_dt, "unit": UNIT, "cores": ncores, "kind": "oracle",
+                         "sample": f"{par_n} particles of the same workload ({ncores} processes on the host cores, "
+                                   f"{cpu_model()}, each on its own elements), one FP64 step + gridpoint moments; "
+                                   f"single core: {cpu_n / cpu_dt:.4g} particle-updates/s on {cpu_n} particles"},
         "clocks": r["clocks"],
         "e2e": {"value": P_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"],
                 "note": "per step: node fields host->device, pdf_step, grid_statistics, statistics device->host; "
