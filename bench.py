@@ -492,8 +492,11 @@ def cpu_model() -> str:
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
-                if line.lower().startswith(("model name", "cpu part")):
+                if line.lower().startswith("model name"):
                     return line.split(":", 1)[1].strip()
+                if line.lower().startswith("cpu part"):
+                    part = line.split(":", 1)[1].strip()
+                    return {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1"}.get(part, "Arm part " + part)
     except OSError:
         pass
     import platform

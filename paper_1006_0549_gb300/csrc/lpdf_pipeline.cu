@@ -441,15 +441,20 @@ __global__ void scan_add_kernel(ScanPair sp, int n)
 // ------------------------------------------------------------------------------------------
 // S2, S3, S4
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlk) record_scatter_kernel(const int* __restrict__ nrec, const int* __restrict__ rec_key,
-                                                              const int* __restrict__ krstart, int* __restrict__ kcur,
-                                                              int* __restrict__ klist)
+// a warp per record block (a block holds a few records: one per distinct element)
+__global__ void __launch_bounds__(256) record_scatter_kernel(const int* __restrict__ nrec, const int* __restrict__ rec_key,
+                                                            const int* __restrict__ krstart, int* __restrict__ kcur,
+                                                            int* __restrict__ klist, int64_t nblk)
 {
-    const int t = threadIdx.x;
-    if (t >= nrec[blockIdx.x]) return;
-    const int rid = blockIdx.x * kBlk + t;
-    const int key = rec_key[rid];
-    klist[krstart[key] + atomicAdd(&kcur[key], 1)] = rid;
+    const int64_t blk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (blk >= nblk) return;
+    const int lane = threadIdx.x & 31;
+    const int nr = nrec[blk];
+    for (int t = lane; t < nr; t += 32) {
+        const int rid = (int)blk * kBlk + t;
+        const int key = rec_key[rid];
+        klist[krstart[key] + atomicAdd(&kcur[key], 1)] = rid;
+    }
 }
 
 // a warp per element: its records in block order (a record id is block * kBlk + slot, and an
@@ -728,7 +733,7 @@ cudaError_t run_pipeline(const DevMesh& m, const DevState& cur, const DevState& 
         nxt.elem, n, w.rrank, w.rec_key, w.rec_cnt, w.nrec, kcnt, krc, status);
     e = scan_pair(kcnt, w.kstart, krc, w.krstart, E + 1, w.scan_part, st);
     if (e != cudaSuccess) return e;
-    record_scatter_kernel<<<(unsigned)nblk, kBlk, 0, st>>>(w.nrec, w.rec_key, w.krstart, kcur, w.klist);
+    record_scatter_kernel<<<nblocks(nblk * 32, 256), 256, 0, st>>>(w.nrec, w.rec_key, w.krstart, kcur, w.klist, nblk);
     key_offsets_kernel<<<nblocks((int64_t)E * 32, 256), 256, 0, st>>>(E, w.kstart, w.krstart, w.klist, w.klist2,
                                                                        w.rec_cnt, w.rec_off);
     particle_scatter_kernel<<<nblocks(n, 256 * kScatterPer), 256, 0, st>>>(n, w.rrank, w.rec_off, w.perm_new);
