@@ -2,6 +2,7 @@
 // device memory management, argument checking, launches).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -46,6 +47,27 @@ cudaError_t dalloc(T** p, size_t n)
 
 bool is_f32(double v) { return (double)(float)v == v; }
 
+// the box x0, x1, y0, y1 around the discs (x - r .. x + r, y - r .. y + r), each bound rounded
+// outward to FP32; empty (+inf, -inf, +inf, -inf) without discs
+void source_box(int n, const float* sx, const float* sy, const float* sr, float box[4])
+{
+    double lo[2] = {HUGE_VAL, HUGE_VAL}, hi[2] = {-HUGE_VAL, -HUGE_VAL};
+    for (int i = 0; i < n; ++i) {
+        const double c[2] = {sx[i], sy[i]};
+        for (int d = 0; d < 2; ++d) {
+            lo[d] = std::min(lo[d], c[d] - (double)sr[i]);
+            hi[d] = std::max(hi[d], c[d] + (double)sr[i]);
+        }
+    }
+    for (int d = 0; d < 2; ++d) {
+        float l = (float)lo[d], h = (float)hi[d];
+        if ((double)l > lo[d]) l = std::nextafter(l, -HUGE_VALF);
+        if ((double)h < hi[d]) h = std::nextafter(h, HUGE_VALF);
+        box[2 * d] = l;
+        box[2 * d + 1] = h;
+    }
+}
+
 CompParams comp_params(uint64_t seed, int n_src, const float* sx, const float* sy, const float* sr, const int32_t* sa)
 {
     CompParams c{};
@@ -58,6 +80,7 @@ CompParams comp_params(uint64_t seed, int n_src, const float* sx, const float* s
         c.src_r[i] = sr[i];
         c.src_alpha[i] = sa[i];
     }
+    source_box(n_src, sx, sy, sr, c.src_box);
     return c;
 }
 
@@ -132,6 +155,7 @@ StepParams lpdf::make_step_params(const lpdf_params& p, const lpdf_mesh* m, uint
         s.src_r[i] = p.src_r[i];
         s.src_alpha[i] = p.src_alpha[i];
     }
+    source_box(p.n_sources, p.src_x, p.src_y, p.src_r, s.src_box);
     (void)m;
     return s;
 }

@@ -448,6 +448,9 @@ __device__ __forceinline__ bool in_source(float px, float py, float sx, float sy
 template <int NS, class SP>
 __device__ __forceinline__ void apply_sources(const SP& sp, float px, float py, float* psi)
 {
+    // outside the discs' box: px < x - r (or another side) for every disc, so the rounded
+    // difference is at least r in magnitude and the rounded squared distance is not below r^2
+    if (!(px >= sp.src_box[0] && px <= sp.src_box[1] && py >= sp.src_box[2] && py <= sp.src_box[3])) return;
     for (int q = 0; q < sp.n_src; ++q)
         if (in_source(px, py, sp.src_x[q], sp.src_y[q], sp.src_r[q])) {
 #pragma unroll
@@ -624,8 +627,9 @@ __device__ __forceinline__ void advance_particle(const DevMesh& M, const float* 
         else if (qx >= fx1) qx -= M.period;
         if (qx < fx0 || qx >= fx1) qx -= floorf((qx - fx0) / M.period) * M.period;   // moves > one period
     }
-    if (!(kKind == 2 && M.edge_walls)) {
-        // walls on the frame's sides: mirror at the frame (edge walls are mirrored in the walk)
+    if (!(kKind == 2 && M.edge_walls) && !(qy >= fy0 && qy < fy1 && qx >= fx0 && qx < fx1)) {
+        // walls on the frame's sides: mirror at the frame (edge walls are mirrored in the walk);
+        // a position inside the half-open frame needs neither this nor the clamp below
 #pragma unroll 1
         for (int it = 0; it < 8; ++it) {
             if (qy < fy0) { qy = 2.0f * fy0 - qy; un = -un; vn = -vn; wn = -wn; }

@@ -50,9 +50,12 @@ struct DevMesh {
 };
 
 // per-component Philox key and scalar sources of a multi-component ensemble
+// src_box: x0, x1, y0, y1 bounding every source disc, rounded outward to FP32 (empty without
+// sources); a position outside it is outside every disc in the FP32 test as well
 struct CompParams {
     uint32_t key0, key1;
     int n_src, pad;
+    float src_box[4];
     float src_x[LPDF_MAX_SOURCES], src_y[LPDF_MAX_SOURCES], src_r[LPDF_MAX_SOURCES];
     int src_alpha[LPDF_MAX_SOURCES];
 };
@@ -62,6 +65,7 @@ struct StepParams {
     uint32_t key0, key1;
     uint32_t step_lo, step_hi;
     int n_src;
+    float src_box[4];
     float src_x[LPDF_MAX_SOURCES], src_y[LPDF_MAX_SOURCES], src_r[LPDF_MAX_SOURCES];
     int src_alpha[LPDF_MAX_SOURCES];
     const CompParams* comp;   // per component (multi-component meshes), else NULL
