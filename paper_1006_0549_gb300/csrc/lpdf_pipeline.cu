@@ -549,43 +549,56 @@ __global__ void __launch_bounds__(MBLK, MMINB) moments_kernel(const __grid_const
 #pragma unroll
         for (int k = 0; k < NK; ++k) acc[k] = 0.0f;
         const int end = min(p1, base + 32 * kLaneChunk);
-        // the lane's gather indices for the whole chunk first, then MB particles per lane in
-        // flight: their state loads are issued before any of them is used; the accumulation order
-        // per lane stays position order
+        // the lane's gather indices for the whole chunk first, then batches of MB particles per
+        // lane, double-buffered: the next batch's state loads are issued before the current
+        // batch is accumulated; the accumulation order per lane stays position order
         constexpr int MB = NS <= 2 ? 4 : 2;
+        static_assert(kLaneChunk % MB == 0, "whole batches per chunk");
         int idx[kLaneChunk];
 #pragma unroll
         for (int k = 0; k < kLaneChunk; ++k) {
             const int pos = base + lane + 32 * k;
             idx[k] = pos < end ? perm[pos] : -1;
         }
-#pragma unroll
-        for (int k0 = 0; k0 < kLaneChunk; k0 += MB) {
-            if (base + 32 * k0 >= end) break;
-            float sx[MB], sy[MB], su[MB], sv[MB], sw[MB], so[MB], sp[MB][NS];
+        float bx[2][MB], by[2][MB], bu[2][MB], bv[2][MB], bw[2][MB], bo[2][MB], bp[2][MB][NS];
+        auto gather = [&](int buf, int k0) {
 #pragma unroll
             for (int k = 0; k < MB; ++k) {
                 const int j = idx[k0 + k] >= 0 ? idx[k0 + k] : 0;
-                sx[k] = S.x[j];
-                sy[k] = S.y[j];
-                su[k] = S.u[j];
-                sv[k] = S.v[j];
-                sw[k] = S.w[j];
-                if (!kFlux) so[k] = S.om[j];
+                bx[buf][k] = S.x[j];
+                by[buf][k] = S.y[j];
+                bu[buf][k] = S.u[j];
+                bv[buf][k] = S.v[j];
+                bw[buf][k] = S.w[j];
+                if (!kFlux) bo[buf][k] = S.om[j];
 #pragma unroll
-                for (int a = 0; a < NS; ++a) sp[k][a] = S.psi[(size_t)a * S.cap + j];
+                for (int a = 0; a < NS; ++a) bp[buf][k][a] = S.psi[(size_t)a * S.cap + j];
             }
+        };
+        gather(0, 0);
+#pragma unroll
+        for (int k0 = 0; k0 < kLaneChunk; k0 += MB) {
+            if (base + 32 * k0 >= end) break;
+            const int cb = (k0 / MB) & 1;
+            if (k0 + MB < kLaneChunk && base + 32 * (k0 + MB) < end) gather(cb ^ 1, k0 + MB);
+            float* const sx = bx[cb];
+            float* const sy = by[cb];
+            float* const su = bu[cb];
+            float* const sv = bv[cb];
+            float* const sw = bw[cb];
+            float* const so = bo[cb];
 #pragma unroll
             for (int k = 0; k < MB; ++k) {
                 if (idx[k0 + k] < 0) break;
                 float q[NQ];
+                float* const spk = bp[cb][k];
                 const float u = su[k], v = sv[k], w = sw[k];
                 if (kFlux) {
 #pragma unroll
                     for (int a = 0; a < NS; ++a) {
-                        q[3 * a] = u * sp[k][a];
-                        q[3 * a + 1] = v * sp[k][a];
-                        q[3 * a + 2] = w * sp[k][a];
+                        q[3 * a] = u * spk[a];
+                        q[3 * a + 1] = v * spk[a];
+                        q[3 * a + 2] = w * spk[a];
                     }
                 } else {
                     q[0] = 1.0f; q[1] = u; q[2] = v; q[3] = w;
@@ -593,8 +606,8 @@ __global__ void __launch_bounds__(MBLK, MMINB) moments_kernel(const __grid_const
                     q[10] = so[k];
 #pragma unroll
                     for (int a = 0; a < NS; ++a) {
-                        q[11 + a] = sp[k][a];
-                        q[11 + NS + a] = sp[k][a] * sp[k][a];
+                        q[11 + a] = spk[a];
+                        q[11 + NS + a] = spk[a] * spk[a];
                     }
                 }
                 float l0, l1, l2;
