@@ -550,9 +550,10 @@ __global__ void __launch_bounds__(MBLK, MMINB) moments_kernel(const __grid_const
         for (int k = 0; k < NK; ++k) acc[k] = 0.0f;
         const int end = min(p1, base + 32 * kLaneChunk);
         // the lane's gather indices for the whole chunk first, then batches of MB particles per
-        // lane, double-buffered: the next batch's state loads are issued before the current
-        // batch is accumulated; the accumulation order per lane stays position order
-        constexpr int MB = NS <= 2 ? 4 : 2;
+        // lane; with one scalar the batches are double-buffered (the next batch's state loads
+        // are issued before the current batch is accumulated), with more the registers go to one
+        // batch at a time. The accumulation order per lane stays position order either way.
+        constexpr int MB = NS <= 2 ? 4 : 2, NB = NS == 1 ? 2 : 1;
         static_assert(kLaneChunk % MB == 0, "whole batches per chunk");
         int idx[kLaneChunk];
 #pragma unroll
@@ -560,7 +561,7 @@ __global__ void __launch_bounds__(MBLK, MMINB) moments_kernel(const __grid_const
             const int pos = base + lane + 32 * k;
             idx[k] = pos < end ? perm[pos] : -1;
         }
-        float bx[2][MB], by[2][MB], bu[2][MB], bv[2][MB], bw[2][MB], bo[2][MB], bp[2][MB][NS];
+        float bx[NB][MB], by[NB][MB], bu[NB][MB], bv[NB][MB], bw[NB][MB], bo[NB][MB], bp[NB][MB][NS];
         auto gather = [&](int buf, int k0) {
 #pragma unroll
             for (int k = 0; k < MB; ++k) {
@@ -575,12 +576,16 @@ __global__ void __launch_bounds__(MBLK, MMINB) moments_kernel(const __grid_const
                 for (int a = 0; a < NS; ++a) bp[buf][k][a] = S.psi[(size_t)a * S.cap + j];
             }
         };
-        gather(0, 0);
+        if constexpr (NB == 2) gather(0, 0);
 #pragma unroll
         for (int k0 = 0; k0 < kLaneChunk; k0 += MB) {
             if (base + 32 * k0 >= end) break;
-            const int cb = (k0 / MB) & 1;
-            if (k0 + MB < kLaneChunk && base + 32 * (k0 + MB) < end) gather(cb ^ 1, k0 + MB);
+            const int cb = NB == 2 ? (k0 / MB) & 1 : 0;
+            if constexpr (NB == 2) {
+                if (k0 + MB < kLaneChunk && base + 32 * (k0 + MB) < end) gather(cb ^ 1, k0 + MB);
+            } else {
+                gather(0, k0);
+            }
             float* const sx = bx[cb];
             float* const sy = by[cb];
             float* const su = bu[cb];
