@@ -18,6 +18,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -61,10 +62,15 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "advance_kernel_channel25M_traffic
 
 
 def kernel_source_hash():
+    """Hash of the advance kernel's code: its sources without comments and blank lines, so that
+    an edit of a comment keeps a traffic figure while any change of code drops it."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1006_0549_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1006_0549_gb300", "csrc", f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("\n".join(ln.strip() for ln in text.splitlines() if ln.strip()).encode())
     return h.hexdigest()[:16]
 
 

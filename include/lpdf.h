@@ -5,7 +5,7 @@
  * The method (Section "Governing equations"): a large number of Lagrangian particles carry
  * position X, velocity U, turbulent frequency omega and scalar compositions psi_alpha, governed
  * by Eq. 2 (position), Eq. 4 (generalized Langevin model), Eq. 5/6 (frequency) and Eq. 9
- * (micromixing, used here in its IEM form <phi|V> -> <phi>); they are advanced by forward Euler,
+ * (micromixing: IEM, <phi|V> -> <phi>, or IECM with a reactive source); they are advanced by forward Euler,
  * Eulerian statistics are evaluated at particle positions, and an unstructured grid is used to
  * extract statistics, to solve for Eulerian quantities, and to track particles (Introduction,
  * items i-iii).
@@ -474,7 +474,9 @@ int lpdf_surrogate_relax_solve(const lpdf_mesh* mesh, lpdf_mlp* m, const lpdf_pa
  * accumulators and four status words) is a static device array of at most 2^21 accumulators,
  * i.e. n_nodes * (11 + 2 ns) <= 2,097,152 (16 MiB, held by every GPU that loads the library
  * until the process exits); larger meshes are rejected with LPDF_ERR_ARG.
- *   mesh, params    as for lpdf_ctx_create (the mesh itself was built by lpdf_mesh_load)
+ *   mesh, params    as for lpdf_ctx_create (the mesh itself was built by lpdf_mesh_load); IEM
+ *                   only (mixing = 0, react_k <= 0), one component, walls on the frame's sides:
+ *                   other settings are rejected with LPDF_ERR_UNSUPPORTED
  *   x..pid          device, n particles (psi: ns rows of n), advanced in place
  *   node_fields     device, n_nodes x nfp FP32 (see lpdf_pdf_step)
  *   moments         device out, n_nodes x (11 + 2 ns) FP64 raw sums S_k(n) of the new state

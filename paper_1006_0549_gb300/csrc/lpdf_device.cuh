@@ -427,8 +427,9 @@ __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy
 
 // ------------------------------------------------------------------------------------------
 // One particle's state in registers, and its forward-Euler step (Section "Governing
-// equations"): Eq. 4 for U, Eq. 5 for omega, Eq. 9 in IEM form for psi, Eq. 2 for X with the
-// same dW_1, dW_2; periodic wrap, wall reflection, the half-open domain and the scalar sources.
+// equations"): Eq. 4 for U, Eq. 5 for omega, Eq. 9 for psi (IEM, or IECM with a reactive
+// source), Eq. 2 for X with the same dW_1, dW_2; periodic wrap, wall reflection, the half-open
+// domain and the scalar sources.
 // ------------------------------------------------------------------------------------------
 template <int NS>
 struct ParticleState {

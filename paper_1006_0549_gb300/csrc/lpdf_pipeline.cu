@@ -1,26 +1,28 @@
 // The particle time step as a pipeline that keeps the ensemble in element order (sm_103a).
 //
-// Per step (Section "Governing equations": Eq. 2, 4, 5, 6, 9 in IEM form, forward Euler,
+// Per step (Section "Governing equations": Eq. 2, 4, 5, 6, 9, forward Euler,
 // statistics at the gridpoints, tracking through the unstructured grid):
 //   T   element_fields_kernel: the node fields in element form (per element: the fields at vertex
 //       0 and their x and y gradients), so a particle interpolates without the node indirection.
 //   K1  advance_kernel: thread i takes the particle perm[i] of the current buffer (perm lists the
-//       buffer in element order), advances it (Eq. 4, 5, 9, 2, wrap, reflection, sources),
-//       locates it with the barycentric neighbour walk and writes it to position i of the next
-//       buffer. No barriers: a thread's walk never waits for another's.
+//       buffer in element order), advances it (Eq. 4, 5, 9 (IEM, or IECM with a reactive source),
+//       2, wrap, reflection, sources), locates it with the barycentric neighbour walk and writes it
+//       to position i of the next buffer. No barriers: a thread's walk never waits for another's.
 //   H   histogram_kernel: each 256-particle block of the next buffer counts its particles per new
 //       element (a sparse histogram: one record per distinct element) and gives every particle
 //       its rank among the block's particles of the same element, in position order.
 //   S1  exclusive scans: particles per element -> bucket starts; records per element -> list starts.
-//   S2  record_scatter_kernel: every record joins its element's record list.
+//   S2  record_scatter_kernel (a warp per record block): every record joins its element's record
+//       list.
 //   S3  key_offsets_kernel (a warp per element): the element's records in block order, and each
 //       record's offset = bucket start + the counts of the element's records in earlier blocks.
 //   S4  particle_scatter_kernel: perm_new[offset(record) + rank] = i. perm_new lists the next
 //       buffer in (new element, position) order: a stable counting sort, fully deterministic.
 //   K2  moments_kernel (a warp per element): the element's particles, gathered through perm_new
-//       in canonical order; lambda_a' q_k accumulated in FP32 per lane over at most kLaneChunk
-//       particles, a fixed butterfly across the lanes, one 64-bit fixed-point atomic add per
-//       node and quantity.
+//       in canonical order (with one scalar the gathers of the next batch are in flight while
+//       a batch is accumulated); lambda_a' q_k accumulated in FP32 per lane over at most
+//       kLaneChunk particles, a fixed butterfly across the lanes, one 64-bit fixed-point atomic
+//       add per node and quantity.
 // Every step leaves perm_new as the next step's perm, so the ensemble is re-bucketed by element
 // every step without a separate sort, and the reduction never needs a hash or a binning pass.
 #include <algorithm>
@@ -31,39 +33,13 @@ namespace lpdf {
 
 namespace {
 
-constexpr int kBlk = 256;          // K1 block: particles (= threads) per histogram block
-constexpr int kRecHash = 512;      // hash slots for the distinct elements of a block
+constexpr int kBlk = 256;          // H: positions per record block
 constexpr int kLaneChunk = 16;     // K2: particles a lane sums in FP32 before the warp reduction
 constexpr int kScanItems = 4;      // scan: items per thread
 constexpr int kScanThreads = 1024;
 constexpr int kScanTile = kScanItems * kScanThreads;
 
 __device__ __forceinline__ unsigned rec_hash(int key) { return ((unsigned)key * 2654435761u) >> 23; }   // 9 bits
-static_assert(kRecHash == 512, "rec_hash gives 9 bits");
-
-// exclusive scan over the kBlk threads of a block; `total` gets the sum (two barriers)
-__device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int& total)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) wsum[wid] = incl;
-    __syncthreads();
-    int off = 0, tot = 0;
-#pragma unroll
-    for (int w = 0; w < kBlk / 32; ++w) {
-        const int s = wsum[w];
-        off += w < wid ? s : 0;
-        tot += s;
-    }
-    __syncthreads();
-    total = tot;
-    return off + incl - v;
-}
 
 // ------------------------------------------------------------------------------------------
 // K1
@@ -251,6 +227,7 @@ __global__ void element_fields_kernel(const __grid_constant__ DevMesh M, const f
 constexpr int kHWarps = 8;             // warps (record blocks) per CTA
 constexpr int kRows = kBlk / 32;       // rows of 32 positions in a record block
 constexpr int kWHash = 512;            // per-warp hash slots (a block has at most kBlk elements)
+static_assert(kWHash == 512 && kWHash >= kBlk, "rec_hash gives 9 bits; a block has at most kBlk elements");
 
 __global__ void __launch_bounds__(32 * kHWarps) histogram_kernel(const int* __restrict__ elem, int64_t n,
                                                                uint16_t* __restrict__ rrank,

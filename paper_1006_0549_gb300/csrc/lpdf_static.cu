@@ -74,6 +74,10 @@ extern "C" int lpdf_pdf_step_static(const lpdf_mesh* mesh, const lpdf_params* pa
         lpdf_set_error(LPDF_ERR_UNSUPPORTED, "pdf_step_static: ns outside 1..4");
         return LPDF_ERR_UNSUPPORTED;
     }
+    if (params->mixing != 0 || params->react_k > 0.0) {
+        lpdf_set_error(LPDF_ERR_UNSUPPORTED, "pdf_step_static: IECM and reactive sources need a context");
+        return LPDF_ERR_UNSUPPORTED;
+    }
     if (n < 0 || (n > 0 && (!x || !y || !u || !v || !w || !omega || !psi || !elem || !pid))) {
         lpdf_set_error(LPDF_ERR_ARG, "pdf_step_static: bad particle arrays");
         return LPDF_ERR_ARG;

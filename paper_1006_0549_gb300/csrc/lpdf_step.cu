@@ -1,6 +1,7 @@
 // The particle time step (sm_103a): one forward-Euler step of every particle of the joint
 // velocity-frequency-scalar PDF method (arXiv:1006.0549, Section "Governing equations": Eq. 2,
-// 4, 5, 6, 9 in IEM form; statistics at particle positions; tracking through the unstructured
+// 4, 5, 6, 9 in IEM form (the static entry point's kernel; IECM and reactive sources run in the
+// pipeline); statistics at particle positions; tracking through the unstructured
 // grid), fused with the reduction of the new state's moments to the gridpoints.
 //
 // A persistent CTA (128 threads, four per SM) walks a contiguous range of 512-particle

@@ -1,0 +1,39 @@
+"""Host logic of bench.py that needs no GPU: the source hash that keeps or drops the committed
+ncu traffic figure, and the lookup of that figure."""
+import os
+import shutil
+
+import bench
+
+
+def _copy_sources(tmp_path):
+    root = tmp_path / "repo"
+    csrc = root / "paper_1006_0549_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in bench.KERNEL_SOURCES:
+        shutil.copy(os.path.join(bench.ROOT, "paper_1006_0549_gb300", "csrc", f), csrc / f)
+    return root, csrc
+
+
+def test_source_hash_ignores_comments_but_not_code(tmp_path, monkeypatch):
+    root, csrc = _copy_sources(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    h0 = bench.kernel_source_hash()
+    f = csrc / "lpdf_pipeline.cu"
+    text = f.read_text()
+    f.write_text("// an added line comment\n/* and a\n block comment */\n\n" + text.replace("\n", "\n\n", 3))
+    assert bench.kernel_source_hash() == h0
+    f.write_text(text.replace("constexpr int kLaneChunk = 16;", "constexpr int kLaneChunk = 8;"))
+    assert bench.kernel_source_hash() != h0
+
+
+def test_traffic_figure_follows_the_hash(tmp_path, monkeypatch):
+    root, csrc = _copy_sources(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    prof = tmp_path / "traffic.txt"
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(prof))
+    prof.write_text("variant 2 bytes per particle: 77.5\nkernel_source_hash: %s\n" % bench.kernel_source_hash())
+    assert bench.ncu_traffic(1000, 2) == 77500.0
+    assert bench.ncu_traffic(1000, 3) is None          # no figure for that variant
+    (csrc / "lpdf_device.cuh").write_text((csrc / "lpdf_device.cuh").read_text() + "\nnamespace lpdf {}\n")
+    assert bench.ncu_traffic(1000, 2) is None          # taken on other code
