@@ -204,7 +204,7 @@ def run_gpu(args, rank, world, dist):
     # launch configuration of the step's kernels, chosen by the library's autotuner on this
     # ensemble (every configuration gives bit-identical results)
     if args.tune == "auto":
-        tune, tune_ms, step = ctx.autotune(fields, 0, steps_per_trial=4, rounds=2)
+        tune, tune_ms, step = ctx.autotune(fields, 0, steps_per_trial=4, rounds=3)
     else:
         tune, tune_ms, step = tuple(int(v) for v in args.tune.split(",")), [], 0
         ctx.set_tune(*tune)
@@ -304,7 +304,7 @@ def run_cavity(steps: int, warmup: int, peak: float):
     ctx.particles_init(wk.n_per_elem, torch.from_numpy(wl.node_init_fields(wk.mesh)).cuda(), m_erlang=4)
     F = torch.from_numpy(wl.synthetic_node_fields(wk.mesh, wk.ns, seed=5)).cuda()
     ctx.status()
-    tune, tune_ms, step = ctx.autotune(F, 0, steps_per_trial=4, rounds=2)
+    tune, tune_ms, step = ctx.autotune(F, 0, steps_per_trial=4, rounds=3)
     for _ in range(warmup):
         ctx.pdf_step(F, step)
         step += 1
@@ -359,7 +359,7 @@ def run_batched(steps: int, warmup: int):
                                                for k, m in enumerate(parts)])).cuda()
     ctx.status()
     setup_s = time.perf_counter() - t
-    tune, tune_ms, step = ctx.autotune(F, 0, steps_per_trial=3, rounds=2)
+    tune, tune_ms, step = ctx.autotune(F, 0, steps_per_trial=3, rounds=3)
     ctx.pdf_steps(F, step, warmup)
     step += warmup
     torch.cuda.synchronize()
