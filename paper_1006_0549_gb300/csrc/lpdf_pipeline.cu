@@ -21,8 +21,8 @@
 //   K2  moments_kernel (a warp per element): the element's particles, gathered through perm_new
 //       in canonical order (with one scalar the gathers of the next batch are in flight while
 //       a batch is accumulated); lambda_a' q_k accumulated in FP32 per lane over at most
-//       kLaneChunk particles, a fixed butterfly across the lanes, one 64-bit fixed-point atomic
-//       add per node and quantity.
+//       kLaneChunk particles, a fixed reduce-scatter across the lanes (recursive halving), one
+//       64-bit fixed-point atomic add per node and quantity.
 // Every step leaves perm_new as the next step's perm, so the ensemble is re-bucketed by element
 // every step without a separate sort, and the reduction never needs a hash or a binning pass.
 #include <algorithm>
@@ -503,6 +503,50 @@ __global__ void particle_scatter_kernel(int64_t n, const uint16_t* __restrict__ 
 // K2
 // ------------------------------------------------------------------------------------------
 // kFlux: the same reduction of the scalar fluxes u_i psi_a (IECM) into their own accumulators
+// One step of the warp reduce-scatter below: with offset O, a lane keeps the half of its live
+// columns that its lane bit O selects, in its low entries, and adds the partner's copy of them.
+// LA, LB: live entries of a (columns base + i) and b (columns base + i + 32) before the step.
+template <int O, int LA, int LB>
+__device__ __forceinline__ void halve(float (&a)[32], float (&b)[32], bool up)
+{
+#pragma unroll
+    for (int i = 0; i < (LA < O ? LA : O); ++i) {
+        const float lo = a[i], hi = O + i < LA ? a[O + i] : 0.0f;
+        a[i] = (up ? hi : lo) + __shfl_xor_sync(kFull, up ? lo : hi, O);
+    }
+#pragma unroll
+    for (int i = 0; i < (LB < O ? LB : O); ++i) {
+        const float lo = b[i], hi = O + i < LB ? b[O + i] : 0.0f;
+        b[i] = (up ? hi : lo) + __shfl_xor_sync(kFull, up ? lo : hi, O);
+    }
+}
+
+__host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
+
+// Column sums of NK <= 64 per-lane values over the warp, by recursive halving: after the steps
+// with offsets 16, 8, 4, 2, 1 lane j holds the sums of columns j (lo) and j + 32 (hi, zero when
+// j + 32 >= NK). About NK shuffles instead of a butterfly's 5 NK; the order of the additions is
+// fixed, so every launch gives the same bits.
+template <int NK>
+__device__ __forceinline__ void warp_reduce_scatter(const float (&acc)[NK], int lane, float& lo, float& hi)
+{
+    static_assert(NK >= 1 && NK <= 64, "at most two columns per lane");
+    constexpr int A0 = cmin(NK, 32), B0 = NK > 32 ? NK - 32 : 0;
+    float a[32], b[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        a[i] = i < NK ? acc[i] : 0.0f;
+        b[i] = 32 + i < NK ? acc[32 + i] : 0.0f;
+    }
+    halve<16, A0, B0>(a, b, (lane & 16) != 0);
+    halve<8, cmin(A0, 16), cmin(B0, 16)>(a, b, (lane & 8) != 0);
+    halve<4, cmin(A0, 8), cmin(B0, 8)>(a, b, (lane & 4) != 0);
+    halve<2, cmin(A0, 4), cmin(B0, 4)>(a, b, (lane & 2) != 0);
+    halve<1, cmin(A0, 2), cmin(B0, 2)>(a, b, (lane & 1) != 0);
+    lo = a[0];
+    hi = B0 > 0 ? b[0] : 0.0f;
+}
+
 template <int NS, int MBLK, int MMINB, bool kFlux = false>
 __global__ void __launch_bounds__(MBLK, MMINB) moments_kernel(const __grid_constant__ DevMesh M,
                                                       const __grid_constant__ DevState S,
@@ -602,20 +646,14 @@ __global__ void __launch_bounds__(MBLK, MMINB) moments_kernel(const __grid_const
                 }
             }
         }
-        // the same butterfly in every lane: every lane ends with every column's sum
-#pragma unroll
-        for (int k = 0; k < NK; ++k) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(kFull, acc[k], o);
-        }
+        // the warp's column sums, scattered: lane j ends with columns j and j + 32
+        float colsum[2];
+        warp_reduce_scatter<NK>(acc, lane, colsum[0], colsum[1]);
         // lane j adds columns j and j + 32
 #pragma unroll
         for (int kk = 0; kk < 2; ++kk) {
             const int col = lane + 32 * kk;
-            float mine = 0.0f;
-#pragma unroll
-            for (int k = 0; k < NK; ++k)
-                if (k == col) mine = acc[k];
+            const float mine = colsum[kk];
             if (col < NK) {
                 const int c = col / NQ, qq = col - c * NQ;
                 const int node = c == 0 ? mv.x : (c == 1 ? mv.y : mv.z);
