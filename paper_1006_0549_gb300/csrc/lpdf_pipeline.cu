@@ -564,21 +564,22 @@ __global__ void __launch_bounds__(MBLK, MMINB) moments_kernel(const __grid_const
     const float4 Y = __ldg(&M.ey[e]);
     const int4 mv = __ldg(&M.em[e]);
     unsigned err = 0;
+    constexpr int LC = kLaneChunk;   // particles per lane and chunk
 #pragma unroll 1
-    for (int base = p0; base < p1; base += 32 * kLaneChunk) {
+    for (int base = p0; base < p1; base += 32 * LC) {
         float acc[NK];
 #pragma unroll
         for (int k = 0; k < NK; ++k) acc[k] = 0.0f;
-        const int end = min(p1, base + 32 * kLaneChunk);
+        const int end = min(p1, base + 32 * LC);
         // the lane's gather indices for the whole chunk first, then batches of MB particles per
         // lane; with one scalar the batches are double-buffered (the next batch's state loads
         // are issued before the current batch is accumulated), with more the registers go to one
         // batch at a time. The accumulation order per lane stays position order either way.
         constexpr int MB = NS <= 2 ? 4 : 2, NB = NS == 1 ? 2 : 1;
-        static_assert(kLaneChunk % MB == 0, "whole batches per chunk");
-        int idx[kLaneChunk];
+        static_assert(LC % MB == 0, "whole batches per chunk");
+        int idx[LC];
 #pragma unroll
-        for (int k = 0; k < kLaneChunk; ++k) {
+        for (int k = 0; k < LC; ++k) {
             const int pos = base + lane + 32 * k;
             idx[k] = pos < end ? perm[pos] : -1;
         }
@@ -599,11 +600,11 @@ __global__ void __launch_bounds__(MBLK, MMINB) moments_kernel(const __grid_const
         };
         if constexpr (NB == 2) gather(0, 0);
 #pragma unroll
-        for (int k0 = 0; k0 < kLaneChunk; k0 += MB) {
+        for (int k0 = 0; k0 < LC; k0 += MB) {
             if (base + 32 * k0 >= end) break;
             const int cb = NB == 2 ? (k0 / MB) & 1 : 0;
             if constexpr (NB == 2) {
-                if (k0 + MB < kLaneChunk && base + 32 * (k0 + MB) < end) gather(cb ^ 1, k0 + MB);
+                if (k0 + MB < LC && base + 32 * (k0 + MB) < end) gather(cb ^ 1, k0 + MB);
             } else {
                 gather(0, k0);
             }
