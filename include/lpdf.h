@@ -263,7 +263,8 @@ int lpdf_pdf_steps(lpdf_ctx* ctx, const float* node_fields, uint64_t step0, int3
  * lpdf_ctx_set_tune sets it (LPDF_ERR_ARG outside those ranges). lpdf_ctx_autotune times every
  * advance variant, then every moments variant with the best advance variant. A trial is one
  * warm-up step and steps_per_trial timed steps (CUDA events on `stream`) of this context's own
- * ensemble and fields; every variant is tried once per round, `rounds` rounds interleaved, and
+ * ensemble and fields; every variant is tried once per round, `rounds` rounds interleaved (odd
+ * rounds in reverse order, so that no variant is always timed right after the same one), and
  * a variant's time is its fastest trial (the ensemble keeps changing while it is timed). The
  * fastest variants are kept. The trial steps are real steps, numbered from step0: *steps_used
  * (host, may be NULL) tells how many were taken. choice (host, 2 ints, may be NULL) = (adv,

@@ -856,12 +856,14 @@ int lpdf_ctx_autotune(lpdf_ctx* c, const float* node_fields, uint64_t step0, int
     const bool timing = c->timing;
     c->timing = false;
     StepTune best = c->tune;
-    // every variant once per round, the rounds interleaved; a variant's time is its fastest trial
+    // every variant once per round, the rounds interleaved and run in alternating order (a variant
+    // is not always timed right after the same one); a variant's time is its fastest trial
     double t_adv[kAdvVariants], t_mom[kMomVariants];
     for (double& t : t_adv) t = 1e300;
     for (double& t : t_mom) t = 1e300;
     for (int r = 0; r < rounds && rc == LPDF_OK; ++r)
-        for (int v = 0; v < kAdvVariants && rc == LPDF_OK; ++v) {
+        for (int j = 0; j < kAdvVariants && rc == LPDF_OK; ++j) {
+            const int v = r % 2 ? kAdvVariants - 1 - j : j;
             double ms = 0.0;
             rc = trial(v, best.mom, ms);
             t_adv[v] = std::min(t_adv[v], ms);
@@ -869,7 +871,8 @@ int lpdf_ctx_autotune(lpdf_ctx* c, const float* node_fields, uint64_t step0, int
     for (int v = 0; v < kAdvVariants; ++v)
         if (t_adv[v] < t_adv[best.adv]) best.adv = v;
     for (int r = 0; r < rounds && rc == LPDF_OK; ++r)
-        for (int v = 0; v < kMomVariants && rc == LPDF_OK; ++v) {
+        for (int j = 0; j < kMomVariants && rc == LPDF_OK; ++j) {
+            const int v = r % 2 ? kMomVariants - 1 - j : j;
             double ms = 0.0;
             rc = trial(best.adv, v, ms);
             t_mom[v] = std::min(t_mom[v], ms);
