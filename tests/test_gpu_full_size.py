@@ -1,14 +1,17 @@
 """Parity at the full workload sizes, in the launch configuration the bench times.
 
 The 50,000-triangle channel with 25M particles (one scalar) and the 199,712-triangle cavity with
-~20M particles (four scalars, moving lid): the ensemble is initialised on the device and stepped
-once, so it is in the pipeline's element order; the next step is checked on samples the FP64
-oracle can compute one by one:
+~20M particles (four scalars, moving lid): the ensemble is initialised on the device, the launch
+configuration is chosen by the autotuner on it (as bench.py does), and it is stepped once more,
+so it is in the pipeline's element order; the next step is checked on samples the FP64 oracle
+can compute one by one:
   * 20,000 sampled particles re-run by the oracle from the GPU's input state (matched by pid):
     FP32 state within the per-step tolerance;
   * 300 of them located by the oracle's brute force: element ids bit-exact;
   * the moment sums at 300 sampled gridpoints against the oracle's reduction of every particle
-    whose new element touches them."""
+    whose new element touches them.
+Then the same step, from the same input state, in the autotuner's configuration and in another
+one: bit-identical state and moment sums at full size."""
 import numpy as np
 import pytest
 
@@ -41,11 +44,13 @@ def test_full_size_sampled_parity(torch_cuda, name):
     ctx.particles_init(wk.n_per_elem, torch.from_numpy(wl.node_init_fields(mesh)).cuda(), m_erlang=4)
     F = wl.synthetic_node_fields(mesh, wk.ns, seed=5)
     Fd = torch.from_numpy(F).cuda()
-    ctx.pdf_step(Fd, 0)
+    choice, _, used = ctx.autotune(Fd, 0, steps_per_trial=2, rounds=1)
+    ctx.pdf_step(Fd, used)
     rc, status = ctx.status(raise_on_error=False)
     assert rc == lpdf.LPDF_OK, status
     before = gc.host_state(ctx.get_state(device=False), wk.ns)
-    ctx.pdf_step(Fd, 1)
+    s1 = used + 1
+    ctx.pdf_step(Fd, s1)
     rc, status = ctx.status(raise_on_error=False)
     assert rc == lpdf.LPDF_OK, status
     after = gc.host_state(ctx.get_state(device=False), wk.ns)
@@ -62,7 +67,7 @@ def test_full_size_sampled_parity(torch_cuda, name):
     sel = np.sort(rng.choice(before.n, 20000, replace=False))
     st = gc.reorder(before, sel)
     g = gc.reorder(after, gc.match_pids(st.pid, after.pid))
-    gc.compare_step(mesh, om, params, F, st, 1, g, check_locate=False)
+    gc.compare_step(mesh, om, params, F, st, s1, g, check_locate=False)
     for i in rng.choice(st.n, 300, replace=False):
         assert om.locate_brute(float(g.x[i]), float(g.y[i])) == g.elem[i]
 
@@ -78,3 +83,22 @@ def test_full_size_sampled_parity(torch_cuda, name):
     tol = 48 * gc.EPS32 * Sabs[nodes] + np.maximum(So[nodes, :1], 1.0) * 8.0 * 2.0 ** -33
     err = np.abs(S[nodes] - So[nodes])
     assert np.all(err <= tol), (nodes[np.argwhere(err > tol)[:5, 0]], err[err > tol][:5], tol[err > tol][:5])
+
+    # the tuned configuration and another one, from the same input state: the same bits
+    other = (0, 0) if tuple(choice) != (0, 0) else (3, 2)
+    outs = []
+    for tune in (tuple(choice), other):
+        ctx.set_state(gc.torch_state(before))
+        ctx.set_tune(*tune)
+        ctx.pdf_step(Fd, s1)
+        rc, status = ctx.status(raise_on_error=False)
+        assert rc == lpdf.LPDF_OK, status
+        S2 = torch.empty((mesh.n_nodes, nq), dtype=torch.float64, device="cuda")
+        ctx.grid_statistics(S2, raw=True)
+        torch.cuda.synchronize()
+        outs.append((gc.host_state(ctx.get_state(device=False), wk.ns), S2.cpu().numpy()))
+    (a, Sa), (b, Sb) = outs
+    for k in gc.FIELDS + ("elem", "pid"):
+        assert np.array_equal(getattr(a, k), getattr(b, k)), (tune, k)
+    assert np.array_equal(a.psi, b.psi)
+    assert np.array_equal(Sa, Sb)
