@@ -462,6 +462,15 @@ def run_surrogate(wk, train_steps: int, run_steps: int, check_every: int, thresh
                     "over the calls that ran the plain solve alone / the network alone"}
 
 
+def workload_config(wk, P: int, world: int, parallelism: str | None = None) -> dict:
+    """The `config` of the JSON line: the workload by name and its sizes (both arms)."""
+    name = "channel-50k-25M" if wk.n_per_elem == 500 else f"channel-50k-{P}"
+    return {"workload": name, "particles_per_gpu": P, "triangles": wk.mesh.n_tri,
+            "particles_per_element": wk.n_per_elem, "scalars": wk.ns,
+            "l2": "inputs larger than L2 (state 0.9 GB per step)", "node_fields": "synthetic, held fixed",
+            "parallelism": parallelism or (f"replicas x{world}" if world > 1 else "single GPU")}
+
+
 def cpu_baseline_sample(wk, n_sample: int, first_elem: int = 0):
     """FP64 oracle (single-threaded C) on n_sample particles of the same workload (the particles of
     the elements from first_elem on, at the workload's particles per element): one step plus the
@@ -562,7 +571,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
-                "config": {"workload": "channel-50k-25M", "particles": wk.n_particles, "triangles": wk.mesh.n_tri},
+                "config": workload_config(wk, wk.n_particles, 1, "FP64 oracle, one host thread, on a bounded sample"),
                 "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                  "sample": f"{n} particles of the channel workload per step (one FP64 step + moments)"},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -613,11 +622,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "channel-50k-25M" if args.ppe == 500 else f"channel-50k-{P}", "particles_per_gpu": P, "triangles": r["wk"].mesh.n_tri,
-                   "particles_per_element": r["wk"].n_per_elem, "scalars": r["wk"].ns,
-                   "l2": "inputs larger than L2 (state 0.9 GB per step)", "node_fields": "synthetic, held fixed",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "mean_walk_hops": r["hops"]},
+        "config": dict(workload_config(r["wk"], P, world), mean_walk_hops=r["hops"]),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth",
                      "kernel": "advance_kernel", "bytes_per_update": BYTES_PER_UPDATE,
