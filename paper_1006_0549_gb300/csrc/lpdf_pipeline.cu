@@ -39,7 +39,7 @@ constexpr int kScanItems = 4;      // scan: items per thread
 constexpr int kScanThreads = 1024;
 constexpr int kScanTile = kScanItems * kScanThreads;
 
-__device__ __forceinline__ unsigned rec_hash(int key) { return ((unsigned)key * 2654435761u) >> 23; }   // 9 bits
+__device__ __forceinline__ unsigned rec_hash(int key) { return ((unsigned)key * 2654435761u) >> 24; }   // 8 bits
 
 // ------------------------------------------------------------------------------------------
 // K1
@@ -226,8 +226,8 @@ __global__ void element_fields_kernel(const __grid_constant__ DevMesh M, const f
 // ------------------------------------------------------------------------------------------
 constexpr int kHWarps = 8;             // warps (record blocks) per CTA
 constexpr int kRows = kBlk / 32;       // rows of 32 positions in a record block
-constexpr int kWHash = 512;            // per-warp hash slots (a block has at most kBlk elements)
-static_assert(kWHash == 512 && kWHash >= kBlk, "rec_hash gives 9 bits; a block has at most kBlk elements");
+constexpr int kWHash = 256;            // per-warp hash slots (a block has at most kBlk elements)
+static_assert(kWHash == 256 && kWHash >= kBlk, "rec_hash gives 8 bits; a block has at most kBlk elements");
 
 __global__ void __launch_bounds__(32 * kHWarps) histogram_kernel(const int* __restrict__ elem, int64_t n,
                                                                uint16_t* __restrict__ rrank,
