@@ -14,7 +14,7 @@ def declared_functions():
     return sorted(set(re.findall(r"\b(lpdf_\w+)\s*\(", text)))
 
 
-def test_header_declares_the_survey_calls():
+def test_header_declares_the_boundary_calls():
     names = declared_functions()
     for n in ("lpdf_mesh_load", "lpdf_particles_init", "lpdf_pdf_step", "lpdf_grid_statistics", "lpdf_sort",
               "lpdf_pdf_step_static", "lpdf_elliptic_relax_solve"):
