@@ -11,7 +11,8 @@ can compute one by one:
   * the moment sums at 300 sampled gridpoints against the oracle's reduction of every particle
     whose new element touches them.
 Then the same step, from the same input state, in the autotuner's configuration and in another
-one: bit-identical state and moment sums at full size."""
+one: bit-identical state and moment sums at full size. The 64-channel batch (268M particles) is
+checked per component (last test)."""
 import numpy as np
 import pytest
 
@@ -102,3 +103,68 @@ def test_full_size_sampled_parity(torch_cuda, name):
         assert np.array_equal(getattr(a, k), getattr(b, k)), (tune, k)
     assert np.array_equal(a.psi, b.psi)
     assert np.array_equal(Sa, Sb)
+
+
+def _subset(d, idx, ns):
+    """The particles `idx` (a device index tensor) of a device state dict, on the host."""
+    sub = {k: v[idx] for k, v in d.items() if k != "psi"}
+    sub["psi"] = d["psi"][:, idx]
+    return gc.host_state(sub, ns)
+
+
+def test_full_size_batched_sampled_parity(torch_cuda):
+    """The 64 channel ensembles of uneven size (268M particles) in one multi-component mesh, set up
+    and autotuned as the bench's batched run. For the smallest, a middle and the largest component,
+    4,000 sampled particles of one step are re-run by the oracle on that component's own mesh with
+    its own seed, source and node fields (particles matched by their per-component pid): FP32 state
+    within the per-step tolerance, and 200 of them located by the oracle's brute force."""
+    torch = torch_cuda
+    wk = wl.batched_channels()
+    parts = wk.mesh.parts
+    gm = lpdf.Mesh(wk.mesh)
+    ctx = lpdf.Context(gm, lpdf.make_params(nu=wk.nu, dt=wk.dt, seed=wk.seeds[0], ns=wk.ns), wk.n_particles)
+    ctx.set_components(list(zip(wk.seeds, wk.sources)))
+    ctx.particles_init_multi(wk.n_per_elem,
+                             torch.from_numpy(wl.stack_node_arrays([wl.node_init_fields(m) for m in parts])).cuda())
+    Fs = [wl.synthetic_node_fields(m, wk.ns, seed=5 + k) for k, m in enumerate(parts)]
+    F = torch.from_numpy(wl.stack_node_arrays(Fs)).cuda()
+    _, _, used = ctx.autotune(F, 0, steps_per_trial=1, rounds=1)
+    ctx.pdf_step(F, used)
+    rc, status = ctx.status(raise_on_error=False)
+    assert rc == lpdf.LPDF_OK, status
+    tri_off = torch.from_numpy(np.asarray(wk.mesh.tri_off, dtype=np.int64)).cuda()
+    sizes = [m.n_tri for m in parts]
+    comps = [int(np.argmin(sizes)), int(np.argsort(sizes)[len(sizes) // 2]), int(np.argmax(sizes))]
+    rng = np.random.default_rng(31)
+    before = ctx.get_state()
+    cb = torch.searchsorted(tri_off, before["elem"].long(), right=True) - 1
+    picked = {}
+    for k in comps:
+        idx = torch.nonzero(cb == k).squeeze(1)
+        sel = torch.from_numpy(np.sort(rng.choice(idx.numel(), 4000, replace=False))).cuda()
+        st = _subset(before, idx[sel], wk.ns)
+        st.elem = (st.elem - wk.mesh.tri_off[k]).astype(np.int32)
+        picked[k] = st
+    del before
+    s1 = used + 1
+    ctx.pdf_step(F, s1)
+    rc, status = ctx.status(raise_on_error=False)
+    assert rc == lpdf.LPDF_OK, status
+    after = ctx.get_state()
+    ca = torch.searchsorted(tri_off, after["elem"].long(), right=True) - 1
+    for k in comps:
+        st = picked[k]
+        idx = torch.nonzero(ca == k).squeeze(1)
+        pid_k = after["pid"][idx].long()
+        order = torch.argsort(pid_k)
+        want = torch.from_numpy(st.pid.astype(np.int64)).cuda()
+        pos = torch.searchsorted(pid_k[order], want).clamp(max=pid_k.numel() - 1)
+        assert torch.equal(pid_k[order][pos], want), "the step lost or invented particles"
+        g = _subset(after, idx[order][pos], wk.ns)
+        g.elem = (g.elem - wk.mesh.tri_off[k]).astype(np.int32)
+        mesh_k = parts[k]
+        om = oracle.OracleMesh(mesh_k)
+        p_k = lpdf.make_params(nu=wk.nu, dt=wk.dt, seed=wk.seeds[k], ns=wk.ns, sources=wk.sources[k])
+        gc.compare_step(mesh_k, om, p_k, Fs[k], st, s1, g, check_locate=False)
+        for i in rng.choice(st.n, 200, replace=False):
+            assert om.locate_brute(float(g.x[i]), float(g.y[i])) == g.elem[i]
