@@ -62,7 +62,7 @@ def _norm_for(feat, tgt):
     return n.astype(np.float32)
 
 
-@pytest.mark.parametrize("B", [1, 128, 300, 1031])
+@pytest.mark.parametrize("B", [1, 128, 300, 1031, 100489])   # 100,489: the nodes of the 20M cavity
 def test_mlp_forward_matches_the_oracle(torch_cuda, B):
     torch = torch_cuda
     feat, tgt = wl.mlp_random_data(B, 10 + B)
