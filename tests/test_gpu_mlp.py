@@ -156,12 +156,22 @@ def _channel(torch):
     return mesh, gm, params
 
 
-def test_surrogate_inputs_and_targets_match_the_oracle(torch_cuda):
+@pytest.mark.parametrize("case", ["channel-small", "cavity-200k"])
+def test_surrogate_inputs_and_targets_match_the_oracle(torch_cuda, case):
+    """The network's inputs and targets per node; the cavity case is the full 199,712-triangle mesh
+    (100,489 nodes, four scalars) that the surrogate configuration runs on."""
     torch = torch_cuda
-    mesh, gm, params = _channel(torch)
-    st = wl.synthetic_statistics(mesh, 1, 8)
+    if case == "channel-small":
+        mesh, gm, params = _channel(torch)
+        ns = 1
+    else:
+        wk = wl.cavity_20m()
+        mesh, ns = wk.mesh, wk.ns
+        gm = lpdf.Mesh(mesh)
+        params = lpdf.params_for(wk)
+    st = wl.synthetic_statistics(mesh, ns, 8)
     S = torch.from_numpy(st).cuda()
-    nfp = wl.n_fields_padded(1)
+    nfp = wl.n_fields_padded(ns)
     F = torch.empty((mesh.n_nodes, nfp), dtype=torch.float32, device="cuda")
     gm.elliptic_relax_solve(params, S, F, 1e-10)
     feat = torch.empty((mesh.n_nodes, 8), dtype=torch.float32, device="cuda")
