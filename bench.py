@@ -410,6 +410,104 @@ def run_batched(steps: int, warmup: int):
             "setup_s": setup_s}
 
 
+def _timed(ctx, F, step: int, steps: int, warmup: int, per_step=None):
+    """`warmup` then `steps` steps of ctx (with `per_step(step)` after each, inside the timed
+    region); returns (ms, per-kernel ms per step, status, next step)."""
+    import torch
+    from paper_1006_0549_gb300 import lpdf
+    for _ in range(warmup):
+        ctx.pdf_step(F, step)
+        if per_step:
+            per_step(step)
+        step += 1
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ctx.set_timing(True)
+    ctx.timings()
+    ctx.status()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        ctx.pdf_step(F, step)
+        if per_step:
+            per_step(step)
+        step += 1
+    t1.record(stream)
+    torch.cuda.synchronize()
+    kms, ks = ctx.timings()
+    ctx.set_timing(False)
+    rc, status = ctx.status(raise_on_error=False)
+    if rc != lpdf.LPDF_OK:
+        raise RuntimeError(f"step status {rc}: {status}")
+    return t0.elapsed_time(t1), {"advance": kms[0] / ks, "rebucket": kms[1] / ks, "moments": kms[2] / ks}, status, step
+
+
+def _line(name, P, steps, ms, kms, status, ns, peak):
+    bytes_per_update = (8 + ns) * 4 + (7 + ns) * 4
+    achieved = bytes_per_update * P / (kms["advance"] * 1e-3) / 1e9
+    return {"workload": name, "particles": int(P), "steps": steps, "ms_per_step": ms / steps,
+            "value": P * steps / (ms * 1e-3), "unit": "particle-updates/s", "kernels_ms_per_step": kms,
+            "advance_roofline": {"bytes_per_update": bytes_per_update, "achieved_gbs": achieved,
+                                 "frac": achieved / peak},
+            "mean_walk_hops": float(status[3]) / (P * steps)}
+
+
+def run_mixing(steps: int, warmup: int, peak: float):
+    """Eq. 9 with IECM and a reactive source on the 25M channel: three scalars (two released from
+    line sources, psi_0 + psi_1 -> psi_2 at rate 4), and every step the loop of the method's
+    mixing: the step (which also sums the scalar fluxes at the gridpoints), the statistics, the
+    flux covariances and the conditional-mean slopes for the next step."""
+    import torch
+    from paper_1006_0549_gb300 import lpdf, workloads as wl
+    wk = wl.channel_25m()
+    wk.ns = 3
+    wk.sources = [(0.25, 0.67, 0.02, 0), (0.25, 1.33, 0.02, 1)]
+    gm = lpdf.Mesh(wk.mesh)
+    params = lpdf.params_for(wk, mixing=1, react_k=4.0, react_a=0, react_b=1, react_p=2)
+    ctx = lpdf.Context(gm, params, wk.n_particles)
+    ctx.particles_init(wk.n_per_elem, torch.from_numpy(wl.node_init_fields(wk.mesh)).cuda(), m_erlang=4)
+    F = torch.from_numpy(wl.synthetic_node_fields(wk.mesh, wk.ns, seed=5)).cuda()
+    N = wk.mesh.n_nodes
+    S = torch.empty((N, 11 + 2 * wk.ns), dtype=torch.float64, device="cuda")
+    Fx = torch.empty((N, 3 * wk.ns), dtype=torch.float64, device="cuda")
+    beta = torch.zeros((N, 3 * wk.ns), dtype=torch.float32, device="cuda")
+    ctx.set_iecm(beta)
+    ctx.status()
+    tune, _, step = ctx.autotune(F, 0, steps_per_trial=3, rounds=3)
+
+    def slopes(_):
+        ctx.grid_statistics(S, raw=False)
+        ctx.grid_flux_statistics(Fx, raw=False)
+        gm.iecm_coefficients(wk.ns, S, Fx, beta)
+
+    ms, kms, status, _ = _timed(ctx, F, step, steps, warmup, slopes)
+    out = _line(f"channel-50k-25M with IECM and a reaction: {wk.ns} scalars, conditional-mean slopes from "
+                "the gridpoint fluxes every step", ctx.n, steps, ms, kms, status, wk.ns, peak)
+    out["tune"] = {"advance_variant": tune[0], "moments_variant": tune[1]}
+    return out
+
+
+def run_walls(steps: int, warmup: int, peak: float):
+    """Walls of any shape: the channel with a smooth bump on its bottom wall (250 x 100 cells,
+    50,000 triangles, 500 particles per element, one scalar): particles that cross the curved
+    wall are mirrored across the wall edge inside the walk."""
+    import torch
+    from paper_1006_0549_gb300 import lpdf, workloads as wl
+    wk = wl.channel_25m()
+    wk.mesh = wl.bump_channel_mesh(250, 100, 1006054905)
+    gm = lpdf.Mesh(wk.mesh)
+    ctx = lpdf.Context(gm, lpdf.params_for(wk), wk.n_particles)
+    ctx.particles_init(wk.n_per_elem, torch.from_numpy(wl.node_init_fields(wk.mesh)).cuda(), m_erlang=4)
+    F = torch.from_numpy(wl.synthetic_node_fields(wk.mesh, wk.ns, seed=5)).cuda()
+    ctx.status()
+    tune, _, step = ctx.autotune(F, 0, steps_per_trial=3, rounds=3)
+    ms, kms, status, _ = _timed(ctx, F, step, steps, warmup)
+    out = _line("bump-channel-50k-25M: the channel with a curved bottom wall (edge walls mirrored in the walk)",
+                ctx.n, steps, ms, kms, status, wk.ns, peak)
+    out["tune"] = {"advance_variant": tune[0], "moments_variant": tune[1]}
+    return out
+
+
 def run_surrogate(wk, train_steps: int, run_steps: int, check_every: int, threshold: float, pressure_solve: int = 0,
                   dpdx0: float = -1.0, tol: float = 1e-8, maxit: int = 20000):
     """The learned surrogate of the gridpoint solve beside the plain solve, in the coupled time loop
@@ -567,6 +665,8 @@ def main():
     ap.add_argument("--surrogate-run-steps", type=int, default=40)
     ap.add_argument("--batched", type=int, default=1, help="1: also report the 64-ensemble batched step")
     ap.add_argument("--cavity", type=int, default=1, help="1: also report the 20M-particle cavity step")
+    ap.add_argument("--mixing", type=int, default=1, help="1: also report the step with IECM and a reaction")
+    ap.add_argument("--walls", type=int, default=1, help="1: also report the channel with a curved wall")
     ap.add_argument("--surrogate-cavity", type=int, default=0,
                     help="steps of the cavity surrogate report (training and run; 0: none)")
     ap.add_argument("--tune", default="auto",
@@ -636,6 +736,8 @@ def main():
     par_n, par_dt = cpu_baseline_parallel(max(500, args.cpu_sample // ncores), ncores)
     batched = run_batched(args.steps, args.warmup) if args.batched else None
     cavity = run_cavity(args.steps, args.warmup, peak) if args.cavity else None
+    mixing = run_mixing(args.steps, args.warmup, peak) if args.mixing else None
+    walls = run_walls(args.steps, args.warmup, peak) if args.walls else None
     surrogate = surrogate_cavity = None
     if args.surrogate_train_steps > 0:
         surrogate = run_surrogate(r["wk"], args.surrogate_train_steps, args.surrogate_run_steps, 10, 0.02)
@@ -669,6 +771,8 @@ def main():
         "surrogate": surrogate,
         "surrogate_cavity": surrogate_cavity,
         "batched": batched,
+        "mixing": mixing,
+        "walls": walls,
         "cavity": cavity,
         "tune": r["tune"],
     }

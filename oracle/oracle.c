@@ -339,6 +339,29 @@ static double image_shift(const OMesh* m, int e, double px)
     return k * m->period;
 }
 
+/* The exit of a walk step in a periodic image frame (sh != 0), which only navigates toward the
+ * seam: with edge walls a periodic edge the point lies beyond (`per`, the most negative) is crossed
+ * first, since the point's own frame is on the other side and this image can lie beyond a wall
+ * where the seam meets one; else the most negative interior edge (`best`); else
+ * the element's periodic edge; else, when the point lies beyond a wall of this image (at a corner
+ * of the seam), the interior neighbour nearest the seam: the least centroid x for sh < 0 (the
+ * image lies toward x0), the greatest for sh > 0. */
+static int seam_exit(const OMesh* m, int e, double sh, int per, int best)
+{
+    if (per >= 0 && m->edge_walls) return per;
+    if (best >= 0) return best;
+    for (int k = 0; k < 3; ++k)
+        if (m->tag[3 * e + k] == 3) return k;
+    double bc = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        int n = m->nbr[3 * e + k];
+        if (n < 0) continue;
+        float c = (float)m->cx[n];
+        if (best < 0 || (sh < 0.0 ? c < bc : c > bc)) { best = k; bc = c; }
+    }
+    return best >= 0 ? best : 0;
+}
+
 /* Barycentric neighbour walk: start at `start`; while p is not inside, leave through the edge
  * whose barycentric is most negative among the interior edges it lies beyond, else through the
  * most negative wall edge (ties: lowest local index). Inside tests are exact and
@@ -351,8 +374,8 @@ int oracle_locate_walk(const OMesh* m, int start, double px, double py, int* hop
     for (int h = 0; h <= ORACLE_HOP_CAP; ++h) {
         double sh = image_shift(m, e, px);
         double qx = px + sh;
-        int best = -1;
-        double bestv = 0.0;
+        int best = -1, per = -1;
+        double bestv = 0.0, perv = 0.0;
         int all_in = 1;
         for (int k = 0; k < 3; ++k) {
             int a = m->tri[3 * e + k], b = m->tri[3 * e + (k + 1) % 3];
@@ -363,9 +386,10 @@ int oracle_locate_walk(const OMesh* m, int start, double px, double py, int* hop
                 in = (m->edge_walls && m->nbr[3 * e + k] < 0) ? oracle_orient2d_sign(ax, ay, bx, by, qx, py) >= 0
                                                                : edge_in(ax, ay, bx, by, qx, py);
             } else {
-                /* shifted frame: navigation only; a point of the domain is never beyond a wall */
+                /* shifted frame: navigation only */
                 all_in = 0;
                 in = (val > 0.0) || (m->nbr[3 * e + k] < 0);
+                if (!in && m->tag[3 * e + k] == 3 && (per < 0 || val < perv)) { per = k; perv = val; }
             }
             if (!in) {
                 all_in = 0;
@@ -375,11 +399,7 @@ int oracle_locate_walk(const OMesh* m, int start, double px, double py, int* hop
             }
         }
         if (sh == 0.0 && all_in) { if (hops_out) *hops_out = h; return e; }
-        if (best < 0) {
-            /* shifted frame and every edge positive: cross the periodic edge */
-            for (int k = 0; k < 3; ++k) if (m->tag[3 * e + k] == 3) { best = k; break; }
-            if (best < 0) best = 0;
-        }
+        if (sh != 0.0) best = seam_exit(m, e, sh, per, best);
         int n = m->nbr[3 * e + best];
         if (n < 0) { if (hops_out) *hops_out = h; return -1; }
         e = n;
@@ -391,7 +411,8 @@ int oracle_locate_walk(const OMesh* m, int start, double px, double py, int* hop
 /* The walk of oracle_locate_walk for walls of any shape: when it would leave through a wall edge
  * (edge k of element e, from node a to node b), the FP32 position is mirrored across the edge's
  * line -- t = ((p - a).d)/(d.d), foot f = a + t d, p' = 2 f - p with d = b - a, in FP64, then
- * rounded to FP32 -- the velocity becomes 2 U_w - U (U_w = (lid_u, 0, 0) on a moving-wall edge,
+ * rounded to FP32; an image that rounds back onto the point moves one FP32 step along the inward
+ * normal (-d_y, d_x) -- the velocity becomes 2 U_w - U (U_w = (lid_u, 0, 0) on a moving-wall edge,
  * else 0), and the walk goes on from e; at most ORACLE_REFL_CAP mirrorings. Returns the owner or
  * a negative value as oracle_locate_walk. */
 int oracle_locate_walk_reflect(const OMesh* m, int start, float* px, float* py, double* U, double* V, double* W,
@@ -401,8 +422,8 @@ int oracle_locate_walk_reflect(const OMesh* m, int start, float* px, float* py, 
     for (;;) {
         double sh = image_shift(m, e, *px);
         double qx = *px + sh;
-        int best = -1;
-        double bestv = 0.0;
+        int best = -1, per = -1;
+        double bestv = 0.0, perv = 0.0;
         int all_in = 1;
         for (int k = 0; k < 3; ++k) {
             int a = m->tri[3 * e + k], b = m->tri[3 * e + (k + 1) % 3];
@@ -415,6 +436,7 @@ int oracle_locate_walk_reflect(const OMesh* m, int start, float* px, float* py, 
             } else {
                 all_in = 0;
                 in = (val > 0.0) || (m->nbr[3 * e + k] < 0);
+                if (!in && m->tag[3 * e + k] == 3 && (per < 0 || val < perv)) { per = k; perv = val; }
             }
             if (!in) {
                 all_in = 0;
@@ -424,10 +446,7 @@ int oracle_locate_walk_reflect(const OMesh* m, int start, float* px, float* py, 
             }
         }
         if (sh == 0.0 && all_in) { *hops_out = h; *nref_out = nref; return e; }
-        if (best < 0) {
-            for (int k = 0; k < 3; ++k) if (m->tag[3 * e + k] == 3) { best = k; break; }
-            if (best < 0) best = 0;
-        }
+        if (sh != 0.0) best = seam_exit(m, e, sh, per, best);
         int n = m->nbr[3 * e + best];
         if (n < 0) {
             if (nref >= ORACLE_REFL_CAP) { *hops_out = h; *nref_out = nref; return -1; }
@@ -435,8 +454,21 @@ int oracle_locate_walk_reflect(const OMesh* m, int start, float* px, float* py, 
             double dx = m->x[b] - m->x[a], dy = m->y[b] - m->y[a];
             double t = (((double)*px - m->x[a]) * dx + ((double)*py - m->y[a]) * dy) / (dx * dx + dy * dy);
             double fx = m->x[a] + t * dx, fy = m->y[a] + t * dy;
-            *px = (float)(2.0 * fx - (double)*px);
-            *py = (float)(2.0 * fy - (double)*py);
+            float nx = (float)(2.0 * fx - (double)*px), ny = (float)(2.0 * fy - (double)*py);
+            if (nx == *px && ny == *py) {
+                /* an image that rounds back onto the point (within about an ulp beyond the wall):
+                 * one FP32 step along the inward normal (-dy, dx) of the edge */
+                if (dy != 0.0) *px = nextafterf(*px, dy < 0.0 ? INFINITY : -INFINITY);
+                if (dx != 0.0) *py = nextafterf(*py, dx > 0.0 ? INFINITY : -INFINITY);
+            } else {
+                *px = nx;
+                *py = ny;
+            }
+            /* the image across a wall edge not parallel to the seam can leave the frame in x */
+            if (m->period > 0.0) {
+                if (*px < (float)m->x0) *px = (float)((double)*px + m->period);
+                else if (*px >= (float)m->x1) *px = (float)((double)*px - m->period);
+            }
             *U = (m->tag[3 * e + best] == 2 ? 2.0 * lid_u : 0.0) - *U;
             *V = -*V;
             *W = -*W;

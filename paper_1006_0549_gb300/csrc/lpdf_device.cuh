@@ -193,15 +193,34 @@ static __device__ __noinline__ bool walk_test(const DevMesh& M, int e, float px,
             return true;
         }
     } else {
+        // periodic image frame: navigate toward the seam. With edge walls a periodic edge the point
+        // lies beyond is crossed first (the point's own frame is on the other side, and this image
+        // can lie beyond a wall where the seam meets one); else the most negative interior edge;
+        // else the element's periodic edge; else the interior neighbour nearest the seam.
         const float qx = px + sh;
+        int per = -1;
+        float perv = 0.0f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const int a = k, b = (k + 1) % 3;
             const float val = (xs[b] - xs[a]) * (py - ys[a]) - (ys[b] - ys[a]) * (qx - xs[a]);
             const bool in = (val > 0.0f) || nb[k] < 0;
             if (!in && (best < 0 || val < bestv)) { best = k; bestv = val; }
+            if (!in && ((N.w >> k) & 1) && (per < 0 || val < perv)) { per = k; perv = val; }
         }
-        if (best < 0) best = (N.w & 1) ? 0 : (N.w & 2) ? 1 : (N.w & 4) ? 2 : 0;
+        if (per >= 0 && M.edge_walls) best = per;
+        if (best < 0) best = (N.w & 1) ? 0 : (N.w & 2) ? 1 : (N.w & 4) ? 2 : -1;
+        if (best < 0) {
+            // sh < 0: the image lies left of this element, toward x0; sh > 0: right, toward x1
+            float bc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (nb[k] < 0) continue;
+                const float c = __ldg(&M.ex[nb[k]]).w;
+                if (best < 0 || (sh < 0.0f ? c < bc : c > bc)) { best = k; bc = c; }
+            }
+            if (best < 0) best = 0;
+        }
     }
     next = best == 0 ? N.x : (best == 1 ? N.y : N.z);
     if (next < 0) next = -1 - best;   // a wall: -1 - (the exit edge)
@@ -275,21 +294,32 @@ __device__ __forceinline__ int walk_test_fast(const DevMesh& M, int e, float px,
     return 0;
 }
 
-// Mirror image of (px, py) across the line of edge k of element e (FP32, every operation rounded
-// once in this order): t = ((p - a).d) / (d.d), foot f = a + t d, p' = 2 f - p, d = b - a.
+// Mirror image of (px, py) across the line of edge k of element e, in FP64 with every operation
+// rounded once in this order, then rounded to FP32: d = b - a, t = ((p - a).d) / (d.d), foot
+// f = a + t d, p' = 2 f - p. A point within about an ulp beyond the wall can have an image that
+// rounds back onto itself; it then moves one FP32 step along the edge's inward normal (-d_y, d_x),
+// so that the walk makes progress.
 static __device__ __noinline__ void mirror_across_edge(const DevMesh& M, int e, int k, float& px, float& py)
 {
     const float4 X = __ldg(&M.ex[e]);
     const float4 Y = __ldg(&M.ey[e]);
     const float xs[3] = {X.x, X.y, X.z}, ys[3] = {Y.x, Y.y, Y.z};
     const int b = k == 2 ? 0 : k + 1;
-    const float dx = __fsub_rn(xs[b], xs[k]), dy = __fsub_rn(ys[b], ys[k]);
-    const float qx = __fsub_rn(px, xs[k]), qy = __fsub_rn(py, ys[k]);
-    const float t = __fdiv_rn(__fadd_rn(__fmul_rn(qx, dx), __fmul_rn(qy, dy)),
-                              __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)));
-    const float fx = __fadd_rn(xs[k], __fmul_rn(t, dx)), fy = __fadd_rn(ys[k], __fmul_rn(t, dy));
-    px = __fsub_rn(__fmul_rn(2.0f, fx), px);
-    py = __fsub_rn(__fmul_rn(2.0f, fy), py);
+    const double ax = xs[k], ay = ys[k];
+    const double dx = __dsub_rn(xs[b], ax), dy = __dsub_rn(ys[b], ay);
+    const double qx = __dsub_rn(px, ax), qy = __dsub_rn(py, ay);
+    const double t = __ddiv_rn(__dadd_rn(__dmul_rn(qx, dx), __dmul_rn(qy, dy)),
+                               __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+    const double fx = __dadd_rn(ax, __dmul_rn(t, dx)), fy = __dadd_rn(ay, __dmul_rn(t, dy));
+    const float nx = __double2float_rn(__dsub_rn(__dmul_rn(2.0, fx), (double)px));
+    const float ny = __double2float_rn(__dsub_rn(__dmul_rn(2.0, fy), (double)py));
+    if (nx == px && ny == py) {
+        if (dy != 0.0) px = nextafterf(px, dy < 0.0 ? CUDART_INF_F : -CUDART_INF_F);
+        if (dx != 0.0) py = nextafterf(py, dx > 0.0 ? CUDART_INF_F : -CUDART_INF_F);
+        return;
+    }
+    px = nx;
+    py = ny;
 }
 
 // The whole walk from element e: the owner of (px, py) (and its barycentrics), -1 on a wall

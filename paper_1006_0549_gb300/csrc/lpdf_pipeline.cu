@@ -78,6 +78,18 @@ static __device__ __noinline__ int walk_mirroring(const DevMesh& M, float lid_u,
             if (nref >= kReflCap) return -1;
             const int k = -1 - next;
             mirror_across_edge(M, e, k, px, py);
+            if (M.periodic) {
+                // the image of a wall edge that is not parallel to the seam can leave the frame
+                // in x: wrap it again (the frame of the element's component)
+                float fx0 = M.x0, fx1 = M.x1;
+                if (M.n_comp > 1) {
+                    const float4 fr = __ldg(&M.cframe[__ldg(&M.ecomp[e])]);
+                    fx0 = fr.x;
+                    fx1 = fr.y;
+                }
+                if (px < fx0) px += M.period;
+                else if (px >= fx1) px -= M.period;
+            }
             const bool moving = (__ldg(&M.en[e]).w >> (3 + k)) & 1;
             u = (moving ? 2.0f * lid_u : 0.0f) - u;
             v = -v;

@@ -198,6 +198,27 @@ def _loglaw(yw, re_tau=180.0):
     return np.where(yp < 11.0, yp, np.log(np.maximum(yp, 1e-30)) / 0.41 + 5.2)
 
 
+def channel_wall_distance(mesh: Mesh) -> np.ndarray:
+    """Distance of every node to the channel's walls: min(y, 2 - y) when both walls are flat
+    (every wall node at y = 0 or y = 2), else the distance to the nearest wall edge (tags 1, 2;
+    the x-periodic images included), e.g. over the bump of bump_channel_mesh."""
+    xy = mesh.node_xy
+    y = xy[:, 1]
+    wall = [(e, k) for e in range(mesh.n_tri) for k in range(3) if mesh.edge_tag[e, k] in (1, 2)]
+    wall_nodes = np.unique([mesh.tri[e, k] for e, k in wall] + [mesh.tri[e, (k + 1) % 3] for e, k in wall])
+    if np.all((y[wall_nodes] == 0.0) | (y[wall_nodes] == 2.0)):
+        return np.minimum(y, 2.0 - y)
+    a = np.array([xy[mesh.tri[e, k]] for e, k in wall])
+    d = np.array([xy[mesh.tri[e, (k + 1) % 3]] for e, k in wall]) - a
+    best = np.full(len(xy), np.inf)
+    for sx in ([-mesh.period_x, 0.0, mesh.period_x] if mesh.period_x > 0 else [0.0]):
+        for i in range(len(a)):
+            r = xy - a[i] - np.array([sx, 0.0])
+            t = np.clip(r @ d[i] / (d[i] @ d[i]), 0.0, 1.0)
+            best = np.minimum(best, np.hypot(r[:, 0] - t * d[i, 0], r[:, 1] - t * d[i, 1]))
+    return best
+
+
 def synthetic_node_fields(mesh: Mesh, ns: int, seed: int, noise: float = 0.05) -> np.ndarray:
     """(N, n_fields_padded(ns)) float32 node fields for parity / throughput runs."""
     rng = np.random.default_rng(seed)
@@ -206,7 +227,7 @@ def synthetic_node_fields(mesh: Mesh, ns: int, seed: int, noise: float = 0.05) -
     F = np.zeros((N, nfp), dtype=np.float64)
     x, y = mesh.node_xy[:, 0], mesh.node_xy[:, 1]
     if mesh.kind == "channel":
-        yw = np.minimum(y, 2.0 - y)
+        yw = channel_wall_distance(mesh)
         U = _loglaw(yw)
         F[:, F_U] = U
         sgn = np.where(y < 1.0, 1.0, -1.0)
@@ -316,7 +337,7 @@ def node_init_fields(mesh: Mesh, sigma: float = 1.0, re_tau: float = 180.0) -> n
     out = np.zeros((N, 8), dtype=np.float64)
     y = mesh.node_xy[:, 1]
     if mesh.kind == "channel":
-        yw = np.minimum(y, 2.0 - y)
+        yw = channel_wall_distance(mesh)
         out[:, 0] = _loglaw(yw, re_tau)
         out[:, 3] = sigma
         out[:, 4] = 1.0 / (0.3 * 0.41 * np.maximum(yw, 10.0 / re_tau))

@@ -70,3 +70,66 @@ def test_no_particle_leaves_through_a_wall(torch_cuda, kind):
     assert g.n == st.n
     for i in range(0, g.n, 7):
         assert om.locate_brute(float(g.x[i]), float(g.y[i])) == g.elem[i]
+
+
+def test_corner_of_the_seam_and_the_top_wall(torch_cuda):
+    """Particles near the top-left corner of the 50,000-triangle bump channel moving up and to the
+    left: each step wraps them across the periodic seam and beyond the top wall at once. The GPU
+    step equals the oracle's (the walk crosses the periodic edge, then mirrors), nothing is lost."""
+    from tests.test_oracle_walls import _corner_state
+    torch = torch_cuda
+    mesh = wl.bump_channel_mesh(250, 100, 1006054905)
+    om = oracle.OracleMesh(mesh)
+    st = _corner_state(mesh, om, 4000, np.random.default_rng(41))
+    params = lpdf.make_params(nu=1.0 / 180.0, ns=1, seed=42)
+    F = np.zeros((mesh.n_nodes, wl.n_fields_padded(1)), dtype=np.float32)
+    F[:, wl.F_OMEGA] = 1.0
+    ctx = lpdf.Context(lpdf.Mesh(mesh), params, st.n + 128)
+    g, _, rc, status = gc.gpu_step(ctx, torch.from_numpy(F).cuda(), st, 3)
+    assert rc == lpdf.LPDF_OK, status
+    gc.compare_step(mesh, om, params, F, st, 3, g)
+
+
+def test_mirror_image_that_rounds_back_onto_the_point(torch_cuda):
+    """A particle of the 25M bump-channel run whose move ends within about an ulp beyond the curved
+    bottom wall: mirrored in FP32, its image rounded back onto the point itself and eight
+    mirrorings made no progress (the particle was lost). The mirror is taken in FP64 as in the
+    oracle, and an image that still rounds onto the point steps one ulp along the inward normal:
+    the GPU finds the owner the oracle finds, after one mirroring."""
+    torch = torch_cuda
+    mesh = wl.bump_channel_mesh(250, 100, 1006054905)
+    om = oracle.OracleMesh(mesh)
+    f = lambda v: np.array([v], dtype=np.float32)
+    st = wl.State(f(4.090161), f(0.12242391), f(1.5177567), f(-0.53100747), f(0.0), f(1.0),
+                  np.zeros((1, 1), np.float32), np.array([32402], np.int32), np.array([16201350], np.uint32))
+    params = lpdf.make_params(nu=1.0 / 180.0, dt=1e-3, seed=wl.channel_25m().seed, ns=1)
+    F = np.zeros((mesh.n_nodes, wl.n_fields_padded(1)), dtype=np.float32)
+    F[:, wl.F_OMEGA] = 1.0
+    ctx = lpdf.Context(lpdf.Mesh(mesh), params, 128)
+    g, _, rc, status = gc.gpu_step(ctx, torch.from_numpy(F).cuda(), st, 0)
+    assert rc == lpdf.LPDF_OK, status
+    res, oelem, aux, lost = oracle.pdf_step(om, gc.oracle_params(params), F, st, 0, locate_mode=2)
+    assert lost == 0 and aux[0, 2] == 1
+    assert g.x[0] == np.float32(res["x"][0]) and g.y[0] == np.float32(res["y"][0])
+    assert g.elem[0] == oelem[0] == om.locate_brute(float(g.x[0]), float(g.y[0])) >= 0
+
+
+def test_image_across_a_sloped_wall_is_wrapped_into_the_frame(torch_cuda):
+    """The same particle on the GPU: the image below the seam's first wall edge leaves the frame
+    in x and is wrapped; the GPU step equals the oracle's and nothing is lost."""
+    torch = torch_cuda
+    mesh = wl.bump_channel_mesh(250, 100, 1006054905)
+    om = oracle.OracleMesh(mesh)
+    f = lambda v: np.array([v], dtype=np.float32)
+    st = wl.State(f(0.00021887), f(0.00056443), f(-0.12476623), f(1.2149805), f(0.0), f(1.0),
+                  np.zeros((1, 1), np.float32), np.array([0], np.int32), np.array([1810], np.uint32))
+    params = lpdf.make_params(nu=1.0 / 180.0, dt=1e-3, seed=wl.channel_25m().seed, ns=1)
+    F = np.zeros((mesh.n_nodes, wl.n_fields_padded(1)), dtype=np.float32)
+    F[:, wl.F_OMEGA] = 1.0
+    ctx = lpdf.Context(lpdf.Mesh(mesh), params, 128)
+    g, _, rc, status = gc.gpu_step(ctx, torch.from_numpy(F).cuda(), st, 1)
+    assert rc == lpdf.LPDF_OK, status
+    res, oelem, aux, lost = oracle.pdf_step(om, gc.oracle_params(params), F, st, 1, locate_mode=2)
+    assert lost == 0
+    assert g.x[0] == np.float32(res["x"][0]) and g.y[0] == np.float32(res["y"][0])
+    assert g.elem[0] == oelem[0] == om.locate_brute(float(g.x[0]), float(g.y[0])) >= 0

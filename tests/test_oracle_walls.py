@@ -97,3 +97,64 @@ def test_particles_stay_in_the_bump_channel():
     assert lost == 0
     assert np.all(oelem >= 0)
     assert (aux[:, 2] > 0).sum() > 10                      # some particles met a wall
+
+
+def _corner_state(mesh, om, n, rng):
+    """Particles near the top-left corner (the periodic seam meets the top wall), moving up and
+    to the left: the move crosses the seam and the top wall in the same step."""
+    x = rng.uniform(0.0005, 0.004, n).astype(np.float32)
+    y = (2.0 - rng.uniform(0.0005, 0.004, n)).astype(np.float32)
+    elem = np.array([om.locate_brute(float(a), float(b)) for a, b in zip(x, y)], dtype=np.int32)
+    assert np.all(elem >= 0)
+    u = -rng.uniform(4.0, 8.0, n).astype(np.float32)
+    v = rng.uniform(4.0, 8.0, n).astype(np.float32)
+    return wl.State(x, y, u, v, np.zeros(n, np.float32), np.ones(n, np.float32), np.zeros((1, n), np.float32),
+                    elem, np.arange(n, dtype=np.uint32))
+
+
+def test_corner_of_the_seam_and_a_curved_walled_channel():
+    """A step that wraps a particle across the periodic seam and carries it beyond the (flat) top
+    wall: the walk starts in the image frame of the old element, crosses the periodic edge, mirrors
+    the position across the top wall and finds the owner; nothing is lost. On this mesh the first
+    element of such a walk can have the point beyond both its periodic edge and its diagonal, the
+    diagonal more negative: a walk that took the diagonal reached a triangle with no periodic edge
+    where the point lies beyond the wall only, and went round until the hop cap."""
+    mesh = wl.bump_channel_mesh(250, 100, 1006054905)
+    om = oracle.OracleMesh(mesh)
+    # that walk: from element 198 to the wrapped position beyond the top wall
+    e, hops = om.locate_walk(198, 6.2829685, 2.0009649)
+    assert e == -1 and hops <= 2                  # it reaches the top wall, which the step mirrors
+    rng = np.random.default_rng(21)
+    st = _corner_state(mesh, om, 2000, rng)
+    p = oracle.make_params(nu=1e-30, dt=1e-3, seed=22, ns=1)
+    res, oelem, aux, lost = oracle.pdf_step(om, p, _still_fields(mesh, 1), st, 1, locate_mode=2)
+    assert lost == 0
+    pre_x, pre_y = aux[:, 0], aux[:, 1]
+    assert np.all(pre_x < 0.0) and np.all(pre_y > 2.0)          # beyond the seam and the wall
+    assert np.all(aux[:, 2] == 1)                                # one mirroring each
+    L = np.float32(mesh.period_x)
+    assert np.allclose(res["x"], np.float32(pre_x) + L, atol=4e-7)
+    assert np.allclose(res["y"], 4.0 - pre_y, atol=4e-7)        # mirror across y = 2
+    assert np.array_equal(res["v"], -st.v.astype(np.float64))
+    for i in range(st.n):
+        assert om.locate_brute(res["x"][i], res["y"][i]) == oelem[i] >= 0
+
+
+def test_image_across_a_sloped_wall_is_wrapped_into_the_frame():
+    """A particle at the bottom-left corner of the 50,000-triangle bump channel (pid 1810 of the
+    25M run, its state at step 1) moves just below the bottom wall near the seam. The wall edge
+    there rises slightly, so the mirror image lands at x = -1.5e-6, outside the periodic frame:
+    it is wrapped to the other side, and the walk finds its owner instead of going back and forth
+    across the seam until the hop cap."""
+    mesh = wl.bump_channel_mesh(250, 100, 1006054905)
+    om = oracle.OracleMesh(mesh)
+    f = lambda v: np.array([v], dtype=np.float32)
+    st = wl.State(f(0.00021887), f(0.00056443), f(-0.12476623), f(1.2149805), f(0.0), f(1.0),
+                  np.zeros((1, 1), np.float32), np.array([0], np.int32), np.array([1810], np.uint32))
+    p = oracle.make_params(nu=1.0 / 180.0, dt=1e-3, seed=wl.channel_25m().seed, ns=1)
+    res, oelem, aux, lost = oracle.pdf_step(om, p, _still_fields(mesh, 1), st, 1, locate_mode=2)
+    assert aux[0, 1] < 0.0 and aux[0, 2] == 1          # below the wall, one mirroring
+    assert lost == 0
+    L = mesh.period_x
+    assert L - 1e-4 < res["x"][0] < L                  # wrapped to the right end of the frame
+    assert om.locate_brute(res["x"][0], res["y"][0]) == oelem[0] >= 0
