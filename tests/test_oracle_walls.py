@@ -158,3 +158,31 @@ def test_image_across_a_sloped_wall_is_wrapped_into_the_frame():
     L = mesh.period_x
     assert L - 1e-4 < res["x"][0] < L                  # wrapped to the right end of the frame
     assert om.locate_brute(res["x"][0], res["y"][0]) == oelem[0] >= 0
+
+
+def test_walks_across_the_seam_end_at_the_owner_or_at_a_wall():
+    """Points near the periodic seam of a curved-wall channel, walked from elements on the other
+    side of the seam (so the walk starts in a periodic image frame): a point of the domain ends at
+    its brute-force owner; a point just beyond the top or bottom wall near the seam ends at a wall
+    (-1), never at the hop cap."""
+    mesh = wl.bump_channel_mesh(30, 10, 13, amp=0.3)
+    om = oracle.OracleMesh(mesh)
+    L = mesh.period_x
+    cx = mesh.node_xy[mesh.tri].mean(axis=1)[:, 0]
+    right = np.nonzero(cx > L - 0.5)[0]                 # starts on the far side of the seam
+    left = np.nonzero(cx < 0.5)[0]
+    rng = np.random.default_rng(17)
+    # points of the domain near x = 0, walked from the right end
+    e_true, xy = _inside_points(mesh, rng, 20000)
+    near = np.nonzero(xy[:, 0] < 0.3)[0][:1500]
+    for k in near:
+        e, hops = om.locate_walk(int(rng.choice(right)), xy[k, 0], xy[k, 1])
+        assert e == om.locate_brute(xy[k, 0], xy[k, 1]) and hops <= 64, (k, xy[k])
+    # points just beyond the walls near the seam, on both sides of it
+    for _ in range(1500):
+        x = float(np.float32(rng.choice([rng.uniform(0.0, 0.05), rng.uniform(L - 0.05, L)])))
+        top = rng.random() < 0.5
+        y = float(np.float32(2.0 + rng.uniform(1e-6, 2e-3) if top else -rng.uniform(1e-6, 2e-3)))
+        start = int(rng.choice(right if x < 0.5 else left))
+        e, hops = om.locate_walk(start, min(x, np.nextafter(np.float32(L), np.float32(0))), y)
+        assert e == -1 and hops <= 64, (x, y, start, e, hops)
