@@ -212,8 +212,13 @@ int lpdf_get_state(const lpdf_ctx* ctx, float* x, float* y, float* u, float* v, 
  * Per particle, with the state at t_n: Eq. 4 for U, Eq. 5 for omega (sqrt(max(omega,0)),
  * then omega <- |omega|), Eq. 9 for psi (IEM, or IECM with params->mixing = 1, plus the reactive
  * source when params->react_k > 0, both from the state at t_n), Eq. 2 for X with the same dW_1, dW_2;
- * periodic wrap; wall reflection (X mirrored, U <- 2 U_w - U); exact point location by a
- * barycentric neighbour walk (hop cap 64); psi_alpha <- 1 inside scalar source discs; then
+ * periodic wrap; wall reflection (X mirrored, U <- 2 U_w - U): across the frame's sides, or,
+ * on a mesh with wall edges off the frame (walls of any shape), across the wall edge that the
+ * walk meets, in FP64 rounded to FP32 (an image that rounds back onto the point moves one FP32
+ * step along the inward normal; the image is wrapped into the periodic frame again; at most 8
+ * mirrorings); exact point location by a barycentric neighbour walk (hop cap 64; a particle
+ * that exceeds a cap keeps its old element and is counted as lost); psi_alpha <- 1 inside
+ * scalar source discs; then
  * S_k(n) += lambda_n(X') q_k, q = 1, u, v, w, uu, uv, uw, vv, vw, ww, omega, psi_a, psi_a^2.
  * Errors are recorded in the context's device status word (read with lpdf_status); the
  * call itself only reports argument and launch errors.
