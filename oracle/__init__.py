@@ -60,6 +60,8 @@ def lib():
         L.oracle_locate_walk.restype = ctypes.c_int
         L.oracle_locate_walk.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, vp]
         L.oracle_barycentric.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, vp]
+        L.oracle_locate_walk_reflect.restype = ctypes.c_int
+        L.oracle_locate_walk_reflect.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, ctypes.c_double, vp, vp]
         L.oracle_pdf_step.restype = ctypes.c_long
         L.oracle_flux_moments.argtypes = [vp, ctypes.c_int, ctypes.c_long] + [vp] * 8
         L.oracle_pdf_step.argtypes = [vp, vp, vp, ctypes.c_int, vp, ctypes.c_long] + [vp] * 9 + \
@@ -142,6 +144,17 @@ class OracleMesh:
         h = ctypes.c_int(0)
         e = lib().oracle_locate_walk(self.ptr, int(start), float(px), float(py), ctypes.byref(h))
         return e, h.value
+
+    def locate_walk_reflect(self, start, px, py, u=0.0, v=0.0, w=0.0, lid_u=0.0):
+        """The walk that mirrors the FP32 position across the wall edges it meets (walls of any
+        shape): returns (owner or a negative code, x, y, u, v, w, hops, mirrorings)."""
+        x, y = ctypes.c_float(px), ctypes.c_float(py)
+        U, V, W = ctypes.c_double(u), ctypes.c_double(v), ctypes.c_double(w)
+        h, n = ctypes.c_int(0), ctypes.c_int(0)
+        e = lib().oracle_locate_walk_reflect(self.ptr, int(start), ctypes.byref(x), ctypes.byref(y), ctypes.byref(U),
+                                             ctypes.byref(V), ctypes.byref(W), float(lid_u), ctypes.byref(h),
+                                             ctypes.byref(n))
+        return e, x.value, y.value, U.value, V.value, W.value, h.value, n.value
 
     def inside(self, e, px, py) -> bool:
         return bool(lib().oracle_inside(self.ptr, int(e), float(px), float(py)))

@@ -189,3 +189,41 @@ def test_walks_across_the_seam_end_at_the_owner_or_at_a_wall(seed):
         start = int(rng.choice(right if x < 0.5 else left))
         e, hops = om.locate_walk(start, min(x, np.nextafter(np.float32(L), np.float32(0))), y)
         assert e == -1 and hops <= 64, (x, y, start, e, hops)
+
+
+def test_an_image_that_rounds_back_onto_the_point_steps_one_ulp_inward():
+    """FP32 points just beyond a sloped wall edge of the bump whose FP64 mirror image rounds back
+    onto the point itself (found by search): the reflecting walk moves each one FP32 step along
+    the edge's inward normal (-d_y, d_x), with one mirroring, and ends at the owner of the result."""
+    mesh = wl.bump_channel_mesh(250, 100, 1006054905)
+    om = oracle.OracleMesh(mesh)
+    xy = mesh.node_xy
+    f32 = np.float32
+    rng = np.random.default_rng(3)
+    walls = [(e, k) for e in range(mesh.n_tri) for k in range(3)
+             if mesh.edge_tag[e, k] == 1 and xy[mesh.tri[e, k], 1] < 0.5]
+    found = []
+    for e, k in walls[::7][:400]:
+        a, b = xy[mesh.tri[e, k]], xy[mesh.tri[e, (k + 1) % 3]]
+        d = b - a
+        if abs(d[1]) < 1e-4:
+            continue
+        n_in = np.array([-d[1], d[0]]) / np.hypot(*d)
+        for t in rng.uniform(0.2, 0.8, 30):
+            q = a + t * d - 1e-9 * n_in
+            px, py = f32(q[0]), f32(q[1])
+            tt = ((float(px) - a[0]) * d[0] + (float(py) - a[1]) * d[1]) / (d[0] * d[0] + d[1] * d[1])
+            mx, my = f32(2.0 * (a[0] + tt * d[0]) - float(px)), f32(2.0 * (a[1] + tt * d[1]) - float(py))
+            beyond = (float(px) - a[0]) * n_in[0] + (float(py) - a[1]) * n_in[1] < 0.0
+            if mx == px and my == py and beyond:
+                found.append((e, d, px, py))
+        if len(found) >= 5:
+            break
+    assert len(found) >= 3
+    for e, d, px, py in found:
+        assert om.locate_brute(float(px), float(py)) == -1           # the point is outside
+        r, x, y, _, _, _, hops, nref = om.locate_walk_reflect(e, px, py)
+        want_x = np.nextafter(px, f32(np.inf) if d[1] < 0 else f32(-np.inf), dtype=np.float32)
+        want_y = np.nextafter(py, f32(np.inf) if d[0] > 0 else f32(-np.inf), dtype=np.float32)
+        assert nref == 1 and f32(x) == want_x and f32(y) == want_y
+        assert r == om.locate_brute(x, y) >= 0
