@@ -410,6 +410,17 @@ def run_batched(steps: int, warmup: int):
             "setup_s": setup_s}
 
 
+def aux_section(fn, *args, **kwargs):
+    """fn(*args) for a report beside the metric; a library status error (LpdfError, or the
+    RuntimeError of a bad step status) becomes {"error": message}. Anything else is raised."""
+    from paper_1006_0549_gb300 import lpdf
+    try:
+        return fn(*args, **kwargs)
+    except (lpdf.LpdfError, RuntimeError) as e:
+        print(f"{getattr(fn, '__name__', 'section')}: {e}", file=sys.stderr)
+        return {"error": str(e)}
+
+
 def _timed(ctx, F, step: int, steps: int, warmup: int, per_step=None):
     """`warmup` then `steps` steps of ctx (with `per_step(step)` after each, inside the timed
     region); returns (ms, per-kernel ms per step, status, next step)."""
@@ -734,17 +745,20 @@ def main():
     cpu_n, cpu_dt = cpu_baseline_sample(r["wk"], args.cpu_sample)
     ncores = os.cpu_count() or 1
     par_n, par_dt = cpu_baseline_parallel(max(500, args.cpu_sample // ncores), ncores)
-    batched = run_batched(args.steps, args.warmup) if args.batched else None
-    cavity = run_cavity(args.steps, args.warmup, peak) if args.cavity else None
-    mixing = run_mixing(args.steps, args.warmup, peak) if args.mixing else None
-    walls = run_walls(args.steps, args.warmup, peak) if args.walls else None
+    # the other configurations are reports beside the metric: an error in one of them (a status
+    # the library returns, e.g. a lost particle) is recorded in its place, not raised
+    batched = aux_section(run_batched, args.steps, args.warmup) if args.batched else None
+    cavity = aux_section(run_cavity, args.steps, args.warmup, peak) if args.cavity else None
+    mixing = aux_section(run_mixing, args.steps, args.warmup, peak) if args.mixing else None
+    walls = aux_section(run_walls, args.steps, args.warmup, peak) if args.walls else None
     surrogate = surrogate_cavity = None
     if args.surrogate_train_steps > 0:
-        surrogate = run_surrogate(r["wk"], args.surrogate_train_steps, args.surrogate_run_steps, 10, 0.02)
+        surrogate = aux_section(run_surrogate, r["wk"], args.surrogate_train_steps, args.surrogate_run_steps, 10,
+                                0.02)
     if args.surrogate_cavity:
         from paper_1006_0549_gb300 import workloads as wl
-        surrogate_cavity = run_surrogate(wl.cavity_20m(), args.surrogate_cavity, args.surrogate_cavity, 5, 0.02,
-                                         pressure_solve=0, dpdx0=0.0, tol=1e-8, maxit=20000)
+        surrogate_cavity = aux_section(run_surrogate, wl.cavity_20m(), args.surrogate_cavity, args.surrogate_cavity,
+                                       5, 0.02, pressure_solve=0, dpdx0=0.0, tol=1e-8, maxit=20000)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms_step, "ms_per_step_median": statistics.median(r["per"]),

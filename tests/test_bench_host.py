@@ -37,3 +37,22 @@ def test_traffic_figure_follows_the_hash(tmp_path, monkeypatch):
     assert bench.ncu_traffic(1000, 3) is None          # no figure for that variant
     (csrc / "lpdf_device.cuh").write_text((csrc / "lpdf_device.cuh").read_text() + "\nnamespace lpdf {}\n")
     assert bench.ncu_traffic(1000, 2) is None          # taken on other code
+
+
+def test_aux_section_records_library_errors_and_raises_the_rest():
+    from paper_1006_0549_gb300 import lpdf
+
+    def lost():
+        raise lpdf.LpdfError(lpdf.LPDF_ERR_LOST_PARTICLE, "3 particle(s) lost")
+
+    def bug():
+        raise ValueError("not a library status")
+
+    assert bench.aux_section(lambda a, b=1: {"v": a + b}, 2, b=3) == {"v": 5}
+    assert "lost" in bench.aux_section(lost)["error"]
+    try:
+        bench.aux_section(bug)
+    except ValueError:
+        pass
+    else:
+        raise AssertionError("a non-library error must propagate")
