@@ -13,7 +13,9 @@
  *                                      + G_ij (U_j - <U_j>) dt + (C_0 eps)^(1/2) dW'_i
  *   frequency           Eq. 5   d omega = -C_3 <w>(w - <w>) dt - S_w <w> w dt + (2 C_3 C_4 <w>^2 w)^(1/2) dW
  *   frequency source    Eq. 6   S_w enters as a node field
- *   mixing (IEM form)   Eq. 9   d psi = -(psi - <phi>)/t_m dt,  t_m = 2/(C_phi <omega>)
+ *   mixing              Eq. 9   d psi = -(psi - <phi|V>)/t_m dt + S(psi) dt,  t_m = 2/(C_phi <omega>):
+ *                               IEM (<phi|V> -> <phi>), or IECM with <phi|V> linear in V, and an
+ *                               optional second-order reaction psi_a + psi_b -> psi_p
  *   time integration    forward Euler (Section "Governing equations", summary paragraph);
  *                       every right-hand side uses the state at t_n
  *   statistics          extracted at gridpoints of the unstructured mesh, evaluated at particle
@@ -25,7 +27,12 @@
  *   - Wiener increments are sqrt(dt) * N(0,1); normals come from Philox4x32-10 (Salmon et al.,
  *     SC'11) keyed (seed) and countered (pid, step, tag<<16 | block), Box-Muller (1958) pairs.
  *   - sqrt(max(omega, 0)) inside Eq. 5, then omega <- |omega|.
- *   - reflection mirrors the position across the wall and sets U <- 2 U_w - U.
+ *   - reflection mirrors the position across the wall and sets U <- 2 U_w - U; on a mesh with
+ *     walls of any shape (wall edges off the bounding box) the walk mirrors across the wall edge
+ *     it meets (FP64, rounded to FP32; an image that rounds back onto the point steps one FP32
+ *     value along the inward normal; the image is wrapped into the periodic frame again).
+ *   - the walk leaves through the edge of the most negative barycentric, interior edges before
+ *     walls; in a periodic image frame it only navigates toward the seam (seam_exit).
  *   - a point exactly on an edge belongs to the element for which that edge is "top-left"
  *     (edge a->b of a CCW triangle includes its points iff b.y < a.y or (b.y == a.y and b.x > a.x));
  *     the domain is half-open ([x0,x1) x [y0,y1)), so positions equal to x1 or y1 are moved to the
