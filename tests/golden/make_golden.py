@@ -4,7 +4,7 @@ The paper prints no worked numerical example: no table of values, no constants o
 sizes of its runs beyond the Reynolds numbers of its two testcases (Section "Two testcases":
 Re_tau = 1080 for the channel, Re = 4000 for the cavity), which are configuration values, not
 results. So nothing here is a printed value of the paper. These fixtures freeze what the FP64
-oracle computes on tiny seeded inputs, so that any later change of its arithmetic shows up as a
+oracle computes on tiny seeded inputs (including a step on a channel with a curved wall), so that any later change of its arithmetic shows up as a
 failing test and has to be justified by the passage it follows. This script calls only the oracle
 and the seeded input generators (which hold none of the method's arithmetic).
 
@@ -40,6 +40,20 @@ def step_case():
     return res, elem, lost, S
 
 
+def walls_case():
+    """One step on a small channel with a curved bottom wall (12 x 6 cells), fast wall-normal
+    motion so that particles meet the walls and the periodic seam: walls mirrored in the walk."""
+    mesh = wl.bump_channel_mesh(12, 6, 7, amp=0.3)
+    om = oracle.OracleMesh(mesh)
+    st = wl.synthetic_state(mesh, 3, 1, seed=31)
+    st.u = (st.u * 4.0).astype(np.float32)
+    st.v = (st.v * 20.0).astype(np.float32)
+    F = wl.synthetic_node_fields(mesh, 1, seed=32)
+    p = oracle.make_params(nu=1.0 / 180.0, dt=1e-3, seed=33, ns=1)
+    res, elem, aux, lost = oracle.pdf_step(om, p, F, st, 2, locate_mode=2)
+    return res, elem, aux, lost
+
+
 def lines():
     out = []
     for ctr, key in PHILOX_CASES:
@@ -56,6 +70,12 @@ def lines():
     out.append("step psi0 : %s" % " ".join("%.17g" % v for v in res["psi"][0]))
     out.append("step elem : %s" % " ".join("%d" % e for e in elem))
     out.append("moments : %s" % " ".join("%.17g" % v for v in S.ravel()))
+    res, elem, aux, lost = walls_case()
+    out.append("walls lost : %d" % lost)
+    for k in ("x", "y", "u", "v"):
+        out.append("walls %s : %s" % (k, " ".join("%.17g" % v for v in res[k])))
+    out.append("walls elem : %s" % " ".join("%d" % e for e in elem))
+    out.append("walls mirrorings : %s" % " ".join("%d" % int(v) for v in aux[:, 2]))
     return out
 
 
