@@ -475,6 +475,8 @@ int oracle_locate_walk_reflect(const OMesh* m, int start, float* px, float* py, 
             if (m->period > 0.0) {
                 if (*px < (float)m->x0) *px = (float)((double)*px + m->period);
                 else if (*px >= (float)m->x1) *px = (float)((double)*px - m->period);
+                /* the half-open frame: an image that rounds to x1 belongs to x0 */
+                if (*px >= (float)m->x1) *px = (float)m->x0;
             }
             *U = (m->tag[3 * e + best] == 2 ? 2.0 * lid_u : 0.0) - *U;
             *V = -*V;

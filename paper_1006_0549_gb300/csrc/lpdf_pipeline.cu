@@ -26,6 +26,7 @@
 // Every step leaves perm_new as the next step's perm, so the ensemble is re-bucketed by element
 // every step without a separate sort, and the reduction never needs a hash or a binning pass.
 #include <algorithm>
+#include <atomic>
 
 #include "lpdf_device.cuh"
 
@@ -89,6 +90,8 @@ static __device__ __noinline__ int walk_mirroring(const DevMesh& M, float lid_u,
                 }
                 if (px < fx0) px += M.period;
                 else if (px >= fx1) px -= M.period;
+                // the half-open frame: an image that rounds to x1 belongs to x0
+                if (px >= fx1) px = fx0;
             }
             const bool moving = (__ldg(&M.en[e]).w >> (3 + k)) & 1;
             u = (moving ? 2.0f * lid_u : 0.0f) - u;
@@ -704,14 +707,17 @@ cudaError_t scan_pair(const int* in0, int* out0, const int* in1, int* out1, int 
     return cudaGetLastError();
 }
 
+// SM count of the current device (kept per device: contexts may live on different GPUs)
 int sm_count_cached()
 {
-    static int n = 0;
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> n_of_dev[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 1;
+    int n = n_of_dev[dev].load(std::memory_order_relaxed);
     if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+        n_of_dev[dev].store(n, std::memory_order_relaxed);
     }
     return n;
 }

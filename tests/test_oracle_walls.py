@@ -227,3 +227,26 @@ def test_an_image_that_rounds_back_onto_the_point_steps_one_ulp_inward():
         want_y = np.nextafter(py, f32(np.inf) if d[0] > 0 else f32(-np.inf), dtype=np.float32)
         assert nref == 1 and f32(x) == want_x and f32(y) == want_y
         assert r == om.locate_brute(x, y) >= 0
+
+
+def test_an_image_that_wraps_onto_x1_belongs_to_x0():
+    """The corner of the seam and the flat top wall of a curved-wall channel, computed by hand: the
+    point (2^-149, 2 + 2^-22) lies one FP32 ulp above the wall and one denormal step right of the
+    seam. Its mirror image across y = 2 is (-2^-149, 2 - 2^-22); the wrap adds the period, and
+    -2^-149 + L rounds to L = x1 exactly, outside the half-open frame [x0, x1), so the image is put
+    at x0 = 0 (periodic wrap: a result equal to x1 becomes x0). The walk ends, after one mirroring,
+    at the owner of (0, 2 - 2^-22); without the rule it walked to the hop cap."""
+    mesh = wl.bump_channel_mesh(25, 20, 7)
+    om = oracle.OracleMesh(mesh)
+    f32 = np.float32
+    px, py = f32(2.0 ** -149), f32(2.0 + 2.0 ** -22)
+    want_y = f32(2.0 - 2.0 ** -22)
+    owner = om.locate_brute(0.0, float(want_y))
+    assert owner >= 0 and om.locate_brute(float(px), float(py)) == -1
+    # from the owner, and from every element that touches the corner node (0, 2)
+    corner = int(np.nonzero((mesh.node_xy[:, 0] == 0.0) & (mesh.node_xy[:, 1] == 2.0))[0][0])
+    starts = sorted({owner} | {int(e) for e in np.nonzero((mesh.tri == corner).any(axis=1))[0]})
+    for s in starts:
+        r, x, y, u, v, w, hops, nref = om.locate_walk_reflect(s, px, py, 0.5, 0.25, 0.125)
+        assert nref == 1 and x == 0.0 and f32(y) == want_y, (s, r, x, y, nref)
+        assert r == owner and (u, v, w) == (-0.5, -0.25, -0.125)
