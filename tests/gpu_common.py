@@ -88,7 +88,10 @@ def compare_step(mesh: wl.Mesh, om: oracle.OracleMesh, params: lpdf.Params, F, s
        outcome (reflection, wrap, source) legitimately differs because the FP32 positions of the
        two sides straddle the decision boundary by a rounding error;
     2. the GPU's element of every particle equals the oracle's exact owner of the GPU's FP32
-       position (bit-exact).
+       position (bit-exact): by the oracle's brute force over every element, or, with
+       check_locate="walk" (meshes too large for brute force on many particles), by the oracle's
+       neighbour walk from the particle's input element, which its own pins tie to brute force;
+       where the two sides' positions are bit-equal, the elements are equal too.
     Returns a dict of diagnostics."""
     ns = params.ns
     # the step may list its output in another order (it keeps the ensemble in element order):
@@ -138,7 +141,10 @@ def compare_step(mesh: wl.Mesh, om: oracle.OracleMesh, params: lpdf.Params, F, s
     # element ids: exact owner of the GPU position, by the oracle's brute force location
     if check_locate:
         for i in range(st_in.n):
-            e = om.locate_brute(float(g.x[i]), float(g.y[i]))
+            if check_locate == "walk" and not om.edge_walls:
+                e, _ = om.locate_walk(int(st_in.elem[i]), float(g.x[i]), float(g.y[i]))
+            else:
+                e = om.locate_brute(float(g.x[i]), float(g.y[i]))
             assert e == g.elem[i], (i, g.x[i], g.y[i], g.elem[i], e)
         same = (g.x.astype(np.float64) == res["x"]) & (g.y.astype(np.float64) == res["y"])
         assert np.array_equal(g.elem[same], oelem[same])
@@ -152,9 +158,9 @@ def compare_moments(om: oracle.OracleMesh, g: wl.State, S_gpu, ns: int):
 
     Tolerance from the arithmetic: each term lambda_a q_k is formed in FP32 (barycentric
     determinants with one FMA-compensated rounding, the division, the products) and summed in
-    FP32 over at most 4 particles of a lane and 32 lanes of a warp before the exact integer
-    accumulation: |error| <= 48 eps32 sum_p |lambda_a q_k| + 2^-33 per FP32 partial converted
-    (at most one per particle)."""
+    FP32 over at most 16 particles of a lane and 32 lanes of a warp (5 levels) before the exact
+    integer accumulation: |error| <= 48 eps32 sum_p |lambda_a q_k| + 2^-33 per FP32 partial
+    converted (at most one per particle)."""
     f = lambda a: a.astype(np.float64)
     S_o, Sabs = oracle.moments(om, ns, f(g.x), f(g.y), f(g.u), f(g.v), f(g.w), f(g.omega), f(g.psi), g.elem)
     count = np.maximum(S_o[:, :1], 1.0) * 8.0

@@ -7,7 +7,9 @@ so it is in the pipeline's element order; the next step is checked on samples th
 can compute one by one:
   * 20,000 sampled particles re-run by the oracle from the GPU's input state (matched by pid):
     FP32 state within the per-step tolerance;
-  * 300 of them located by the oracle's brute force: element ids bit-exact;
+  * all of them located by the oracle's neighbour walk from their input element (pinned against
+    brute force by the oracle tests), and 300 by the oracle's brute force: element ids
+    bit-exact; where the GPU position equals the oracle's bit for bit, the element does too;
   * the moment sums at 300 sampled gridpoints against the oracle's reduction of every particle
     whose new element touches them.
 Then the same step, from the same input state, in the autotuner's configuration and in another
@@ -68,7 +70,8 @@ def test_full_size_sampled_parity(torch_cuda, name):
     sel = np.sort(rng.choice(before.n, 20000, replace=False))
     st = gc.reorder(before, sel)
     g = gc.reorder(after, gc.match_pids(st.pid, after.pid))
-    gc.compare_step(mesh, om, params, F, st, s1, g, check_locate=False)
+    diag, _, _ = gc.compare_step(mesh, om, params, F, st, s1, g, check_locate="walk")
+    assert diag["bitwise_equal_positions"] > 0.1, diag
     for i in rng.choice(st.n, 300, replace=False):
         assert om.locate_brute(float(g.x[i]), float(g.y[i])) == g.elem[i]
 
@@ -117,7 +120,8 @@ def test_full_size_batched_sampled_parity(torch_cuda):
     and autotuned as the bench's batched run. For the smallest, a middle and the largest component,
     4,000 sampled particles of one step are re-run by the oracle on that component's own mesh with
     its own seed, source and node fields (particles matched by their per-component pid): FP32 state
-    within the per-step tolerance, and 200 of them located by the oracle's brute force."""
+    within the per-step tolerance, every element id against the oracle's walk from the input
+    element, and 200 of them located by the oracle's brute force."""
     torch = torch_cuda
     wk = wl.batched_channels()
     parts = wk.mesh.parts
@@ -165,6 +169,6 @@ def test_full_size_batched_sampled_parity(torch_cuda):
         mesh_k = parts[k]
         om = oracle.OracleMesh(mesh_k)
         p_k = lpdf.make_params(nu=wk.nu, dt=wk.dt, seed=wk.seeds[k], ns=wk.ns, sources=wk.sources[k])
-        gc.compare_step(mesh_k, om, p_k, Fs[k], st, s1, g, check_locate=False)
+        gc.compare_step(mesh_k, om, p_k, Fs[k], st, s1, g, check_locate="walk")
         for i in rng.choice(st.n, 200, replace=False):
             assert om.locate_brute(float(g.x[i]), float(g.y[i])) == g.elem[i]

@@ -247,3 +247,36 @@ def test_consecutive_steps_through_the_element_order(torch_cuda, workload):
         torch.cuda.synchronize()
         gc.compare_step(mesh, om, params, F, before, step, after, check_locate=(step == 3))
         gc.compare_moments(om, after, S.cpu().numpy(), wk.ns)
+
+
+@pytest.mark.parametrize("case", ["w_nan", "u_nan", "field_inf"])
+def test_non_finite_state_is_reported_and_the_context_recovers(torch_cuda, case):
+    """Non-finite values put in on the host: a NaN third velocity component of one particle (its
+    position stays finite), a NaN streamwise velocity (the position becomes NaN too, so the walk
+    cannot find an owner and the particle is also lost), and an Inf in one node's G11 (every
+    particle of the elements around that node gets a non-finite velocity). The status word carries
+    the non-finite bit (2); lpdf_status returns LPDF_ERR_NONFINITE, or LPDF_ERR_LOST_PARTICLE when
+    the particle was lost as well; the next step from a clean state returns LPDF_OK."""
+    import torch
+    wk = wl.channel_small()
+    mesh, gm, om, params, F, Fd, ctx, npe = _setup(wk, n_per_elem=10)
+    st = wl.synthetic_state(mesh, npe, wk.ns, seed=44)
+    bad_st = st.copy()
+    bad_F = F.copy()
+    if case == "w_nan":
+        bad_st.w[17] = np.nan
+    elif case == "u_nan":
+        bad_st.u[17] = np.nan
+    else:
+        bad_F[int(mesh.tri[100, 0]), wl.F_G11] = np.inf
+    g, S, rc, status = gc.gpu_step(ctx, torch.from_numpy(bad_F).cuda(), bad_st, 0)
+    assert status[0] & 2, status
+    if case == "u_nan":
+        assert rc == lpdf.LPDF_ERR_LOST_PARTICLE and status[1] == 1 and status[2] == st.pid[17], (rc, status)
+    else:
+        assert rc == lpdf.LPDF_ERR_NONFINITE and status[1] == 0, (rc, status)
+        assert not np.all(np.isfinite(g.w if case == "w_nan" else g.u))
+    # the status was read and cleared; a clean step works and matches the oracle
+    g, S, rc, status = gc.gpu_step(ctx, Fd, st, 1)
+    assert rc == lpdf.LPDF_OK and status[0] == 0, status
+    gc.compare_step(mesh, om, params, F, st, 1, g, check_locate=False)
