@@ -25,6 +25,7 @@
 // addition is associative: the gridpoint sums are bit-reproducible.
 #include <algorithm>
 #include <cstddef>
+#include <mutex>
 
 #include "lpdf_device.cuh"
 
@@ -637,14 +638,26 @@ cudaError_t launch_step_ns(const DevMesh& m, const DevState& s, const float* fie
                            unsigned long long* node_acc, unsigned long long* status, cudaStream_t st)
 {
     const size_t smem = sizeof(Smem<NS>);
-    static int n_sm = 0;
-    if (n_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(pdf_step_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int dev = 0;
-        e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
+    // the shared-memory opt-in and the SM count belong to the device that is current: kept per
+    // device, set once under a lock (host threads may call from several devices at once)
+    constexpr int kMaxDev = 64;
+    static std::mutex mu;
+    static int sm_of_dev[kMaxDev] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    int n_sm = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (sm_of_dev[dev] == 0) {
+            e = cudaFuncSetAttribute(pdf_step_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            int c = 0;
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+            sm_of_dev[dev] = c > 0 ? c : 1;
+        }
+        n_sm = sm_of_dev[dev];
     }
     const int64_t ntiles = (s.n + kT - 1) / kT;
     if (ntiles == 0) return cudaSuccess;

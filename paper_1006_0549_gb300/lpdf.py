@@ -402,13 +402,54 @@ class Context:
         return out
 
 
+def check_static_args(n_nodes: int, ns: int, state: dict, node_fields, moments) -> int:
+    """The buffers of lpdf_pdf_step_static, checked before any launch: the library receives bare
+    pointers and cannot size them, so a wrong dtype, shape or layout would become out-of-bounds
+    device accesses. Raises ValueError; returns the particle count n."""
+    import torch
+
+    def need(name, t, dtypes, shape):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if t.dtype not in dtypes:
+            raise ValueError(f"{name} must be {' or '.join(str(d) for d in dtypes)}, not {t.dtype}")
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} must have shape {tuple(shape)}, not {tuple(t.shape)}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+
+    if not (1 <= ns <= MAX_SCALARS):
+        raise ValueError(f"ns must be in 1..{MAX_SCALARS}, not {ns}")
+    missing = [k for k in ("x", "y", "u", "v", "w", "omega", "psi", "elem", "pid") if k not in state]
+    if missing:
+        raise ValueError(f"state lacks {missing}")
+    x = state["x"]
+    if not isinstance(x, torch.Tensor) or x.dim() != 1:
+        raise ValueError("state['x'] must be a 1-D torch tensor")
+    n = int(x.shape[0])
+    for k in ("x", "y", "u", "v", "w", "omega"):
+        need(f"state[{k!r}]", state[k], (torch.float32,), (n,))
+    need("state['psi']", state["psi"], (torch.float32,), (ns, n))
+    need("state['elem']", state["elem"], (torch.int32,), (n,))
+    need("state['pid']", state["pid"], (torch.int32, getattr(torch, "uint32", torch.int32)), (n,))
+    need("node_fields", node_fields, (torch.float32,), (n_nodes, wl.n_fields_padded(ns)))
+    need("moments", moments, (torch.float64,), (n_nodes, 11 + 2 * ns))
+    tensors = [state[k] for k in ("x", "y", "u", "v", "w", "omega", "psi", "elem", "pid")] + [node_fields, moments]
+    dev = {t.device for t in tensors}
+    if len(dev) != 1 or next(iter(dev)).type != "cuda":
+        raise ValueError(f"every buffer must be on one CUDA device, not {sorted(str(d) for d in dev)}")
+    return n
+
+
 def pdf_step_static(mesh: Mesh, params: Params, state: dict, node_fields, step: int, moments,
                     read_status: bool = True, stream=None):
     """lpdf_pdf_step_static: the step on caller-owned device buffers; allocates nothing.
 
-    `state` holds torch CUDA tensors x, y, u, v, w, omega, psi (ns x n), elem, pid, advanced in
-    place; `moments` (n_nodes x (11 + 2 ns) float64, CUDA) receives the raw gridpoint sums."""
-    n = int(state["x"].shape[0])
+    `state` holds torch CUDA tensors x, y, u, v, w, omega (float32, n), psi (float32, ns x n),
+    elem and pid (int32, n), advanced in place; node_fields is n_nodes x n_fields_padded(ns)
+    float32; `moments` (n_nodes x (11 + 2 ns) float64) receives the raw gridpoint sums. All on one
+    CUDA device and contiguous (checked: ValueError)."""
+    n = check_static_args(mesh.n_nodes, int(params.ns), state, node_fields, moments)
     st = np.zeros(4, dtype=np.int64) if read_status else None
     rc = lib().lpdf_pdf_step_static(mesh.h, ctypes.byref(params), n,
                                     *[_ptr(state[k]) for k in ("x", "y", "u", "v", "w", "omega", "psi", "elem",
