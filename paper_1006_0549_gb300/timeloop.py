@@ -145,3 +145,40 @@ def run_surrogate(loop: TimeLoop, net: lpdf.MLP, steps: int, train_feat=None, tr
             retrains += 1
         loop.advance()
     return {"times": times, "check_errors": errs, "network_used_on": used, "retrains": retrains}
+
+
+def run_coupled(wk: wl.Workload, params: lpdf.Params, state: dict, fields0, steps: int, record=(),
+                tol: float = 1e-12, maxit: int = 20000, step0: int = 1, timing: bool = False):
+    """The plain coupled loop from a given state: for n = 1..steps, lpdf_pdf_step with the current
+    node fields (Philox step number step0 + n - 1), lpdf_grid_statistics (means and central
+    moments), and, before the next step, lpdf_elliptic_relax_solve for the next node fields.
+    `state` is a dict of device tensors for lpdf_set_state, fields0 the first step's node fields
+    (device). Returns (statistics at the steps in `record` as {n: host array}, per-step device
+    times {"step_ms", "solve_ms"} when timing, the final status)."""
+    import torch
+    gm = lpdf.Mesh(wk.mesh)
+    n = int(state["x"].shape[0])
+    ctx = lpdf.Context(gm, params, n)
+    ctx.set_state(state)
+    F = fields0.clone()
+    S = torch.zeros((wk.mesh.n_nodes, 11 + 2 * params.ns), dtype=torch.float64, device="cuda")
+    out, step_ms, solve_ms = {}, [], []
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    for k in range(1, steps + 1):
+        e0, e1, e2 = ev(), ev(), ev()
+        e0.record()
+        ctx.pdf_step(F, step0 + k - 1)
+        ctx.grid_statistics(S, raw=False)
+        e1.record()
+        if k in record:
+            out[k] = S.cpu().numpy()
+        if k < steps:
+            gm.elliptic_relax_solve(params, S, F, tol, maxit)
+        e2.record()
+        if timing:
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            solve_ms.append(e1.elapsed_time(e2))
+    torch.cuda.synchronize()
+    rc, status = ctx.status(raise_on_error=False)
+    return out, {"step_ms": step_ms, "solve_ms": solve_ms}, (rc, status)
