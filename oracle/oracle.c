@@ -346,16 +346,18 @@ static double image_shift(const OMesh* m, int e, double px)
     return k * m->period;
 }
 
-/* The exit of a walk step in a periodic image frame (sh != 0), which only navigates toward the
- * seam: with edge walls a periodic edge the point lies beyond (`per`, the most negative) is crossed
- * first, since the point's own frame is on the other side and this image can lie beyond a wall
- * where the seam meets one; else the most negative interior edge (`best`); else
- * the element's periodic edge; else, when the point lies beyond a wall of this image (at a corner
- * of the seam), the interior neighbour nearest the seam: the least centroid x for sh < 0 (the
- * image lies toward x0), the greatest for sh > 0. */
+/* The exit of a walk step in a periodic image frame (sh != 0), where the image of the point lies
+ * inside no element and the step only moves toward the seam. An edge counts as crossed by the
+ * image when the image is not inside it by the exact test of the own frame (top-left rule), so an
+ * edge the walk crosses is inside for the next element and the walk never steps back, even from
+ * a vertex on the seam; walls are never crossed here. A periodic edge crossed by the image
+ * (`per`, the most negative) is taken first, since the point's own frame is on the other side;
+ * else the most negative other crossed edge (`best`); else the element's periodic edge; else,
+ * when the image lies beyond walls only (at a corner of the seam), the interior neighbour nearest
+ * the seam: the least centroid x for sh < 0 (the image lies toward x0), the greatest for sh > 0. */
 static int seam_exit(const OMesh* m, int e, double sh, int per, int best)
 {
-    if (per >= 0 && m->edge_walls) return per;
+    if (per >= 0) return per;
     if (best >= 0) return best;
     for (int k = 0; k < 3; ++k)
         if (m->tag[3 * e + k] == 3) return k;
@@ -393,9 +395,10 @@ int oracle_locate_walk(const OMesh* m, int start, double px, double py, int* hop
                 in = (m->edge_walls && m->nbr[3 * e + k] < 0) ? oracle_orient2d_sign(ax, ay, bx, by, qx, py) >= 0
                                                                : edge_in(ax, ay, bx, by, qx, py);
             } else {
-                /* shifted frame: navigation only */
+                /* shifted frame: the image is tested as a point of the own frame (exact orientation,
+                 * top-left rule), walls excepted (never crossed here); it lies inside no element */
                 all_in = 0;
-                in = (val > 0.0) || (m->nbr[3 * e + k] < 0);
+                in = (m->nbr[3 * e + k] < 0) || edge_in(ax, ay, bx, by, qx, py);
                 if (!in && m->tag[3 * e + k] == 3 && (per < 0 || val < perv)) { per = k; perv = val; }
             }
             if (!in) {
@@ -442,7 +445,7 @@ int oracle_locate_walk_reflect(const OMesh* m, int start, float* px, float* py, 
                                                                : edge_in(ax, ay, bx, by, qx, *py);
             } else {
                 all_in = 0;
-                in = (val > 0.0) || (m->nbr[3 * e + k] < 0);
+                in = (m->nbr[3 * e + k] < 0) || edge_in(ax, ay, bx, by, qx, *py);
                 if (!in && m->tag[3 * e + k] == 3 && (per < 0 || val < perv)) { per = k; perv = val; }
             }
             if (!in) {

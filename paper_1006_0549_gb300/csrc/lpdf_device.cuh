@@ -137,10 +137,83 @@ __device__ __forceinline__ float orient_sign(float ax, float ay, float bx, float
     return val;
 }
 
+// The same orientation for the periodic image (px + sh, py) of a point (sh = +-period): the
+// difference px + sh - ax is formed with one rounding, as in the own frame, because one of
+// ax - sh (sh > 0: an element near the seam at x1) or px + sh (sh < 0: a point near x1) is exact
+// by Sterbenz's lemma when the two lie within a factor of two of each other; otherwise (an
+// element far from the seam) the sign comes from the exact FP64 expansion of the image, whose x
+// coordinate px + sh is exact in FP64. Returns the FP32 value (for choosing among exits) and the
+// exact sign.
+__device__ __forceinline__ float orient_sign_image(float ax, float ay, float bx, float by, float px, float py, float sh,
+                                                   int& sgn)
+{
+    const bool shift_element = sh > 0.0f;
+    const bool exact = shift_element ? (ax >= 0.5f * sh && ax <= 2.0f * sh) : (px >= -0.5f * sh && px <= -2.0f * sh);
+    const float dx1 = __fsub_rn(bx, ax), dy1 = __fsub_rn(by, ay);
+    const float dx2 = shift_element ? __fsub_rn(px, __fsub_rn(ax, sh)) : __fsub_rn(__fadd_rn(px, sh), ax);
+    const float dy2 = __fsub_rn(py, ay);
+    const float w = dy1 * dx2;
+    const float e = fmaf(-dy1, dx2, w);
+    const float f = fmaf(dx1, dy2, -w);
+    const float val = f + e;
+    const float detsum = fmaf(fabsf(dx1), fabsf(dy2), fabsf(w));
+    const float bound = 4.0e-7f * detsum;
+    if (exact && detsum > 1e-25f && val > bound) { sgn = 1; return val; }
+    if (exact && detsum > 1e-25f && -val > bound) { sgn = -1; return val; }
+    sgn = orient_exact((double)bx, (double)by, (double)px + (double)sh, (double)py, (double)ax, (double)ay);
+    return val;
+}
+
 // an edge a->b of a CCW triangle owns the points on it iff it is a "top-left" edge
 __device__ __forceinline__ bool edge_owns(float ax, float ay, float bx, float by)
 {
     return (by < ay) || (by == ay && bx > ax);
+}
+
+// The exit of a walk test in a periodic image frame (sh = +-period). The image (px + sh, py) is
+// tested as a point of the own frame (exact orientation, top-left rule), so an edge the walk
+// crosses is inside for the next element and the walk never steps back, even from a vertex on
+// the seam. The image of a point of the frame lies inside no element of the image frame: the test
+// only picks the exit, never a wall. A periodic edge the image is not inside of first (it leads
+// toward the point's own frame), the most negative one; else the most negative other edge; when
+// the image lies beyond walls only (where the seam meets a wall), the element's periodic edge;
+// else the interior neighbour nearest the seam. Out of line: few particles cross the seam.
+static __device__ __noinline__ int image_exit(const DevMesh& M, int e, float px, float py, float sh)
+{
+    const float4 X = __ldg(&M.ex[e]);
+    const float4 Y = __ldg(&M.ey[e]);
+    const int4 N = __ldg(&M.en[e]);
+    const float xs[3] = {X.x, X.y, X.z}, ys[3] = {Y.x, Y.y, Y.z};
+    const int nb[3] = {N.x, N.y, N.z};
+    int best = -1, per = -1;
+    float bestv = 0.0f, perv = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int a = k, b = (k + 1) % 3;
+        if (nb[k] < 0) continue;
+        int s;
+        const float val = orient_sign_image(xs[a], ys[a], xs[b], ys[b], px, py, sh, s);
+        if (s > 0 || (s == 0 && edge_owns(xs[a], ys[a], xs[b], ys[b]))) continue;
+        if ((N.w >> k) & 1) {
+            if (per < 0 || val < perv) { per = k; perv = val; }
+        } else if (best < 0 || val < bestv) {
+            best = k;
+            bestv = val;
+        }
+    }
+    if (per >= 0) return per;
+    if (best >= 0) return best;
+    best = (N.w & 1) ? 0 : (N.w & 2) ? 1 : (N.w & 4) ? 2 : -1;
+    if (best >= 0) return best;
+    // sh < 0: the image lies left of this element, toward x0; sh > 0: right, toward x1
+    float bc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (nb[k] < 0) continue;
+        const float c = __ldg(&M.ex[nb[k]]).w;
+        if (best < 0 || (sh < 0.0f ? c < bc : c > bc)) { best = k; bc = c; }
+    }
+    return best >= 0 ? best : 0;
 }
 
 // One test of the barycentric neighbour walk at element e: true if e is the unique owner of
@@ -193,34 +266,7 @@ static __device__ __noinline__ bool walk_test(const DevMesh& M, int e, float px,
             return true;
         }
     } else {
-        // periodic image frame: navigate toward the seam. With edge walls a periodic edge the point
-        // lies beyond is crossed first (the point's own frame is on the other side, and this image
-        // can lie beyond a wall where the seam meets one); else the most negative interior edge;
-        // else the element's periodic edge; else the interior neighbour nearest the seam.
-        const float qx = px + sh;
-        int per = -1;
-        float perv = 0.0f;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const int a = k, b = (k + 1) % 3;
-            const float val = (xs[b] - xs[a]) * (py - ys[a]) - (ys[b] - ys[a]) * (qx - xs[a]);
-            const bool in = (val > 0.0f) || nb[k] < 0;
-            if (!in && (best < 0 || val < bestv)) { best = k; bestv = val; }
-            if (!in && ((N.w >> k) & 1) && (per < 0 || val < perv)) { per = k; perv = val; }
-        }
-        if (per >= 0 && M.edge_walls) best = per;
-        if (best < 0) best = (N.w & 1) ? 0 : (N.w & 2) ? 1 : (N.w & 4) ? 2 : -1;
-        if (best < 0) {
-            // sh < 0: the image lies left of this element, toward x0; sh > 0: right, toward x1
-            float bc = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                if (nb[k] < 0) continue;
-                const float c = __ldg(&M.ex[nb[k]]).w;
-                if (best < 0 || (sh < 0.0f ? c < bc : c > bc)) { best = k; bc = c; }
-            }
-            if (best < 0) best = 0;
-        }
+        best = image_exit(M, e, px, py, sh);
     }
     next = best == 0 ? N.x : (best == 1 ? N.y : N.z);
     if (next < 0) next = -1 - best;   // a wall: -1 - (the exit edge)
