@@ -262,10 +262,7 @@ int lpdf_pdf_steps(lpdf_ctx* ctx, const float* node_fields, uint64_t step0, int3
  * Launch configuration of the step's kernels. Every configuration gives bit-identical results.
  *   adv (advance kernel): 0 = 256 threads per CTA, >= 4 CTAs per SM (64 registers);
  *       1 = 256, >= 6 (40 registers); 2 = 128, >= 8; 3 = 256, >= 4 on a persistent grid
- *       (CTAs stride over 256-particle tiles); 4 = 256, >= 6, persistent; 5 = 128, >= 8 and
- *       6 = 256, >= 4 on a persistent grid of contiguous tile ranges, each thread gathering the
- *       state of its next particle into shared memory (asynchronous copies) while it advances
- *       the current one.
+ *       (CTAs stride over 256-particle tiles); 4 = 256, >= 6, persistent.
  *   mom (moments kernel, a warp per element): 0 = 256 threads, >= 2 CTAs per SM; 1 = 128, >= 4;
  *       2 = 512, >= 1; 3 = 256, >= 3.
  * lpdf_ctx_set_tune sets it (LPDF_ERR_ARG outside those ranges). lpdf_ctx_autotune times every
@@ -276,7 +273,7 @@ int lpdf_pdf_steps(lpdf_ctx* ctx, const float* node_fields, uint64_t step0, int3
  * a variant's time is its fastest trial (the ensemble keeps changing while it is timed). The
  * fastest variants are kept. The trial steps are real steps, numbered from step0: *steps_used
  * (host, may be NULL) tells how many were taken. choice (host, 2 ints, may be NULL) = (adv,
- * mom); trial_ms (host, 11 doubles, may be NULL) = milliseconds per step of each variant (7
+ * mom); trial_ms (host, 9 doubles, may be NULL) = milliseconds per step of each variant (5
  * advance, then 4 moments variants). sync.
  * ------------------------------------------------------------------------------------- */
 int lpdf_ctx_set_tune(lpdf_ctx* ctx, int32_t adv, int32_t mom);

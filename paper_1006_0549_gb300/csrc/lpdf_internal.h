@@ -135,14 +135,12 @@ struct PipeScratch {
 // kernels and after the moments kernel
 // launch configuration of the step's kernels (lpdf_ctx_autotune); every choice gives
 // bit-identical results. adv: advance kernel 0 = 256 threads, >= 4 CTAs/SM; 1 = 256, >= 6;
-// 2 = 128, >= 8; 3 = 256, >= 4, persistent grid; 4 = 256, >= 6, persistent; 5 = 128, >= 8 and
-// 6 = 256, >= 4, persistent with contiguous tile ranges and the next tile's state gathered into
-// shared memory by asynchronous copies while the current tile is advanced. mom: moments kernel
+// 2 = 128, >= 8; 3 = 256, >= 4, persistent grid; 4 = 256, >= 6, persistent. mom: moments kernel
 // 0 = 256 threads, >= 2 CTAs/SM; 1 = 128, >= 4; 2 = 512, >= 1; 3 = 256, >= 3.
 struct StepTune {
     int adv = 0, mom = 0;
 };
-constexpr int kAdvVariants = 7, kMomVariants = 4;
+constexpr int kAdvVariants = 5, kMomVariants = 4;
 cudaError_t launch_pdf_step_pipeline(const DevMesh& m, const DevState& cur, const DevState& nxt, int ns,
                                      const float* fields, const StepParams& p, PipeScratch& w,
                                      unsigned long long* node_acc, unsigned long long* status, cudaStream_t st,

@@ -193,89 +193,6 @@ __device__ __forceinline__ void advance_one(const DevMesh& M, const DevState& cu
     advance_store<NS, kKind>(M, nxt, EF, P, status, i, p, err, hops);
 }
 
-// 4-byte asynchronous copy global -> shared (cached in L1, the only form for 4 bytes), and the
-// group bookkeeping: a thread's own copies are complete and visible to it after the wait
-__device__ __forceinline__ void cp_async4(void* dst, const void* src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-
-// K1 with the gathers of the next tile in flight: a persistent CTA takes a contiguous range of
-// ABLK-particle tiles; while a thread advances its particle of tile t, its copies of the state of
-// its particle of tile t + 1 (through perm, 4 bytes per field, into its own column of a two-stage
-// shared-memory buffer) and its load of perm for tile t + 2 are in flight. A thread reads only
-// the column it copied, so no barrier is needed. Same particle arithmetic and output as
-// advance_kernel, position i from thread i of its tile.
-template <int NS, int kKind, int ABLK, int MINB>
-__global__ void __launch_bounds__(ABLK, MINB)
-advance_kernel_pf(const __grid_constant__ DevMesh M, const __grid_constant__ DevState cur,
-                  const __grid_constant__ DevState nxt, const int* __restrict__ perm, const float* __restrict__ EF,
-                  const __grid_constant__ StepParams P, unsigned long long* __restrict__ status, int64_t per)
-{
-    constexpr int NW = 8 + NS;     // x, y, u, v, w, omega, psi[NS], elem, pid
-    __shared__ uint32_t buf[2][NW][ABLK];
-    const int tid = threadIdx.x, lane = tid & 31;
-    unsigned err = 0;
-    int hops = 0;
-    const int64_t ntiles = (cur.n + ABLK - 1) / ABLK;
-    const int64_t t0 = (int64_t)blockIdx.x * per;
-    const int64_t t1 = min(ntiles, t0 + per);
-    auto src_of = [&](int64_t tile) -> int {
-        const int64_t i = tile * ABLK + tid;
-        return (tile < t1 && i < cur.n) ? ld_stream(perm + i) : -1;
-    };
-    auto issue = [&](int stage, int src) {
-        if (src >= 0) {
-            cp_async4(&buf[stage][0][tid], cur.x + src);
-            cp_async4(&buf[stage][1][tid], cur.y + src);
-            cp_async4(&buf[stage][2][tid], cur.u + src);
-            cp_async4(&buf[stage][3][tid], cur.v + src);
-            cp_async4(&buf[stage][4][tid], cur.w + src);
-            cp_async4(&buf[stage][5][tid], cur.om + src);
-#pragma unroll
-            for (int a = 0; a < NS; ++a) cp_async4(&buf[stage][6 + a][tid], cur.psi + (size_t)a * cur.cap + src);
-            cp_async4(&buf[stage][6 + NS][tid], cur.elem + src);
-            cp_async4(&buf[stage][7 + NS][tid], cur.pid + src);
-        }
-        cp_async_commit();   // an empty group keeps the count of groups uniform
-    };
-    if (t0 < t1) {
-        issue(0, src_of(t0));
-        int src_next = src_of(t0 + 1);
-#pragma unroll 1
-        for (int64_t tile = t0; tile < t1; ++tile) {
-            const int s = (int)((tile - t0) & 1);
-            issue(s ^ 1, src_next);
-            src_next = src_of(tile + 2);
-            cp_async_wait_prev();
-            const int64_t i = tile * ABLK + tid;
-            if (i < cur.n) {
-                ParticleState<NS> p;
-                p.x = __uint_as_float(buf[s][0][tid]);
-                p.y = __uint_as_float(buf[s][1][tid]);
-                p.u = __uint_as_float(buf[s][2][tid]);
-                p.v = __uint_as_float(buf[s][3][tid]);
-                p.w = __uint_as_float(buf[s][4][tid]);
-                p.om = __uint_as_float(buf[s][5][tid]);
-#pragma unroll
-                for (int a = 0; a < NS; ++a) p.psi[a] = __uint_as_float(buf[s][6 + a][tid]);
-                p.elem = (int)buf[s][6 + NS][tid];
-                p.pid = buf[s][7 + NS][tid];
-                advance_store<NS, kKind>(M, nxt, EF, P, status, i, p, err, hops);
-            }
-        }
-        asm volatile("cp.async.wait_all;" ::: "memory");
-    }
-    const unsigned e_or = __reduce_or_sync(kFull, err);
-    const int h_sum = __reduce_add_sync(kFull, hops);
-    if (lane == 0) {
-        if (e_or) atomicOr(&status[0], (unsigned long long)e_or);
-        if (h_sum) atomicAdd(&status[3], (unsigned long long)h_sum);
-    }
-}
-
 // K1 variants (the autotuner picks one per context; all give bit-identical results): ABLK
 // threads per CTA, at least MINB CTAs per SM (the register cap), and either one particle per
 // thread over the whole grid or a persistent grid striding over ABLK-particle tiles.
@@ -823,24 +740,11 @@ void launch_advance_v(const DevMesh& m, const DevState& cur, const DevState& nxt
     advance_kernel<NS, kKind, ABLK, MINB, kPersist><<<(unsigned)grid, ABLK, 0, st>>>(m, cur, nxt, perm, ef, p, status);
 }
 
-template <int NS, int kKind, int ABLK, int MINB>
-void launch_advance_pf(const DevMesh& m, const DevState& cur, const DevState& nxt, const int* perm, const float* ef,
-                       const StepParams& p, unsigned long long* status, cudaStream_t st)
-{
-    const int64_t ntiles = (cur.n + ABLK - 1) / ABLK;
-    const int64_t slots = (int64_t)sm_count_cached() * MINB;
-    const int64_t per = (ntiles + slots - 1) / slots;
-    const int64_t grid = (ntiles + per - 1) / per;
-    advance_kernel_pf<NS, kKind, ABLK, MINB><<<(unsigned)grid, ABLK, 0, st>>>(m, cur, nxt, perm, ef, p, status, per);
-}
-
 template <int NS, int kKind>
 void launch_advance(int v, const DevMesh& m, const DevState& cur, const DevState& nxt, const int* perm,
                     const float* ef, const StepParams& p, unsigned long long* status, cudaStream_t st)
 {
     switch (v) {
-        case 5: launch_advance_pf<NS, kKind, 128, 8>(m, cur, nxt, perm, ef, p, status, st); break;
-        case 6: launch_advance_pf<NS, kKind, 256, 4>(m, cur, nxt, perm, ef, p, status, st); break;
         case 1: launch_advance_v<NS, kKind, 256, 6, false>(m, cur, nxt, perm, ef, p, status, st); break;
         case 2: launch_advance_v<NS, kKind, 128, 8, false>(m, cur, nxt, perm, ef, p, status, st); break;
         case 3: launch_advance_v<NS, kKind, 256, 4, true>(m, cur, nxt, perm, ef, p, status, st); break;
