@@ -286,6 +286,35 @@ def run_gpu(args, rank, world, dist):
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - te) / Ke
     d_stats = d_stats[(Ke - 1) % 2]
+    # the same step with compensated moment sums (lpdf_params.moment_sums = 1: within 1e-9 of the
+    # FP64 sums instead of 48 eps32), beside the metric
+    ctx.set_params(lpdf.params_for(wk, moment_sums=1))
+    for _ in range(2):
+        ctx.pdf_step(fields, step)
+        step += 1
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    ctx.timings()
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    for _ in range(K):
+        ctx.pdf_step(fields, step)
+        step += 1
+    c1.record(stream)
+    torch.cuda.synchronize()
+    ckms, cks = ctx.timings()
+    ctx.set_timing(False)
+    ctx.set_params(lpdf.params_for(wk))
+    rc, status = ctx.status(raise_on_error=False)
+    if rc != lpdf.LPDF_OK:
+        raise RuntimeError(f"step status {rc}: {status} (compensated moment sums)")
+    comp_ms = c0.elapsed_time(c1) / K
+    compensated = {"ms_per_step": comp_ms, "value": P / (comp_ms * 1e-3), "unit": UNIT,
+                   "kernels_ms_per_step": {"advance": ckms[0] / cks, "rebucket": ckms[1] / cks,
+                                           "moments": ckms[2] / cks},
+                   "note": "the same workload with lpdf_params.moment_sums = 1: gridpoint sums in compensated "
+                           "FP32 (double-float), within 1e-9 of sum |lambda q| of the FP64 oracle instead of "
+                           "48 eps32"}
     # the gridpoint side (not part of the metric): node fields from the last statistics, elliptic
     # relaxation and mean-pressure CGs to a relative residual of 1e-6 (far below the statistical noise
     # of the moments); cold (from zero), then warm
@@ -311,6 +340,7 @@ def run_gpu(args, rank, world, dist):
              "note": "lpdf_elliptic_relax_solve: recovery, FP64 elliptic-relaxation and pressure CGs, "
                      "host-timed (it synchronises); not included in the step"}
     return dict(P=P, total_ms=total_ms, per=per, kernel_ms=kernel_ms, clocks=clk.summary(), hops=hops, e2e_s=e2e_s,
+                compensated=compensated,
                 h2d=int(h_fields.numel() * 4), d2h=int(h_stats[0].numel() * 8), wk=wk, solve=solve,
                 tune={"advance_variant": tune[0], "moments_variant": tune[1],
                       "trial_ms_per_step": [round(float(x), 4) for x in tune_ms]})
@@ -596,6 +626,81 @@ def run_surrogate(wk, train_steps: int, run_steps: int, check_every: int, thresh
                     "over the calls that ran the plain solve alone / the network alone"}
 
 
+C1_RECORD = (1, 10, 50, 200)
+C1_GROUPS = {"U_i": [1, 2, 3], "u_i u_j": [4, 5, 6, 7, 8, 9], "omega": [10], "phi": [11], "phi'^2": [12]}
+C1_SOLVE = dict(gmodel=0, pressure_solve=1, dpdx0=-1.0)
+
+
+def _dev_state(st):
+    import torch
+    d = {k: torch.from_numpy(np.ascontiguousarray(getattr(st, k))).cuda() for k in ("x", "y", "u", "v", "w", "omega")}
+    d["psi"] = torch.from_numpy(np.ascontiguousarray(st.psi)).cuda()
+    d["elem"] = torch.from_numpy(np.ascontiguousarray(st.elem, dtype=np.int32)).cuda()
+    d["pid"] = torch.from_numpy(np.ascontiguousarray(st.pid).view(np.int32)).cuda()
+    return d
+
+
+def c1_inputs():
+    """C1: the 1,000-triangle channel, 50 particles per element (50,000), one scalar, its seeded
+    start state and first node fields, and the plain gridpoint solve (elliptic relaxation and
+    mean-pressure projection)."""
+    from paper_1006_0549_gb300 import workloads as wl
+    wk = wl.channel_small()
+    st0 = wl.synthetic_state(wk.mesh, wk.n_per_elem, wk.ns, seed=1006054901)
+    F0 = wl.synthetic_node_fields(wk.mesh, wk.ns, seed=5)
+    return wk, st0, F0
+
+
+def run_c1(steps: int = 200):
+    """C1 on the GPU: the coupled loop (step, statistics, gridpoint solve) for `steps` steps from
+    the seeded state, and the same loop under another seed (the ensemble's statistical spread);
+    device times of the step with its statistics and of the solve."""
+    import torch
+    from paper_1006_0549_gb300 import lpdf, timeloop as tl
+    wk, st0, F0 = c1_inputs()
+    params = lpdf.params_for(wk, **C1_SOLVE)
+    g, timing, (rc, status) = tl.run_coupled(wk, params, _dev_state(st0), torch.from_numpy(F0).cuda(), steps,
+                                             C1_RECORD, timing=True)
+    if rc != lpdf.LPDF_OK:
+        raise RuntimeError(f"C1 step status {rc}: {status}")
+    other = lpdf.params_for(wk, **C1_SOLVE)
+    other.seed = params.seed + 12345
+    s, _, (rc, status) = tl.run_coupled(wk, other, _dev_state(st0), torch.from_numpy(F0).cuda(), steps, C1_RECORD)
+    if rc != lpdf.LPDF_OK:
+        raise RuntimeError(f"C1 step status {rc}: {status}")
+    step_ms = float(np.median(timing["step_ms"]))
+    return {"workload": f"{wk.name}: coupled loop, {steps} steps (step, statistics, elliptic relaxation and "
+                        "mean-pressure solve)", "particles": int(st0.n), "steps": steps,
+            "gpu_step_ms_median": step_ms, "gpu_step_value": st0.n / (step_ms * 1e-3),
+            "gpu_solve_ms_median": float(np.median(timing["solve_ms"][:-1])), "unit": "particle-updates/s",
+            "_stats": g, "_spread": s, "_params_seed": int(params.seed)}
+
+
+def c1_against_oracle(c1):
+    """The FP64 oracle's own coupled loop from the same state (CPU-baseline leg): its host time on
+    one thread, and the relative error (Frobenius over all nodes) of every statistic of the GPU loop
+    against it at the recorded steps, beside the GPU seed-to-seed spread."""
+    import oracle
+    from oracle import timeloop as otl
+    from paper_1006_0549_gb300 import timeloop as tl
+    wk, st0, F0 = c1_inputs()
+    op = oracle.make_params(nu=wk.nu, dt=wk.dt, seed=c1["_params_seed"], ns=wk.ns, sources=wk.sources,
+                            lid_u=wk.lid_u)
+    times = {}
+    o, _, lost = otl.run_coupled(wk.mesh, op, st0, F0, c1["steps"], C1_RECORD, solve=dict(nu=wk.nu, **C1_SOLVE),
+                                 timings=times)
+    g, s = c1.pop("_stats"), c1.pop("_spread")
+    c1.pop("_params_seed")
+    table = {str(n): {k: {"gpu_vs_oracle": tl.relative_difference(g[n], o[n], cols),
+                          "seed_spread": tl.relative_difference(s[n], g[n], cols)}
+                      for k, cols in C1_GROUPS.items()} for n in C1_RECORD}
+    c1.update({"oracle_lost": int(lost), "oracle_step_s": times["step_s"], "oracle_solve_s": times["solve_s"],
+               "oracle_step_value_1core": st0.n * c1["steps"] / times["step_s"], "relative_error": table,
+               "note": "relative error = Frobenius norm over all nodes of (GPU - oracle) / oracle per statistic "
+                       "group; seed spread = the GPU loop under another seed against the GPU loop"})
+    return c1
+
+
 def workload_config(wk, P: int, world: int, parallelism: str | None = None) -> dict:
     """The `config` of the JSON line: the workload by name and its sizes (both arms)."""
     name = "channel-50k-25M" if wk.n_per_elem == 500 else f"channel-50k-{P}"
@@ -675,6 +780,8 @@ def main():
                     help="plain steps whose fields train the surrogate (0: no surrogate report)")
     ap.add_argument("--surrogate-run-steps", type=int, default=40)
     ap.add_argument("--batched", type=int, default=1, help="1: also report the 64-ensemble batched step")
+    ap.add_argument("--c1", type=int, default=1,
+                    help="1: also report the 200-step coupled loop on the small channel against the oracle's")
     ap.add_argument("--cavity", type=int, default=1, help="1: also report the 20M-particle cavity step")
     ap.add_argument("--mixing", type=int, default=1, help="1: also report the step with IECM and a reaction")
     ap.add_argument("--walls", type=int, default=1, help="1: also report the channel with a curved wall")
@@ -742,11 +849,19 @@ def main():
     achieved = BYTES_PER_UPDATE * P / (kms["advance"] * 1e-3) / 1e9
     step_gbs = BYTES_PER_UPDATE * P / (ms_step * 1e-3) / 1e9
     traffic = ncu_traffic(P, r["tune"]["advance_variant"])
+    # the other configurations are reports beside the metric: an error in one of them (a status
+    # the library returns, e.g. a lost particle) is recorded in its place, not raised
+    c1 = aux_section(run_c1) if args.c1 else None
+    # CPU-baseline leg (the FP64 oracle on the host cores): the channel sample on one core and on
+    # all cores, the cavity sample on one core, and the oracle's own C1 loop with the error of the
+    # GPU loop's statistics against it
     cpu_n, cpu_dt = cpu_baseline_sample(r["wk"], args.cpu_sample)
     ncores = os.cpu_count() or 1
     par_n, par_dt = cpu_baseline_parallel(max(500, args.cpu_sample // ncores), ncores)
-    # the other configurations are reports beside the metric: an error in one of them (a status
-    # the library returns, e.g. a lost particle) is recorded in its place, not raised
+    from paper_1006_0549_gb300 import workloads as wl_
+    cav_n, cav_dt = cpu_baseline_sample(wl_.cavity_20m(), 200_000)
+    if c1 is not None and "error" not in c1:
+        c1 = c1_against_oracle(c1)
     batched = aux_section(run_batched, args.steps, args.warmup) if args.batched else None
     cavity = aux_section(run_cavity, args.steps, args.warmup, peak) if args.cavity else None
     mixing = aux_section(run_mixing, args.steps, args.warmup, peak) if args.mixing else None
@@ -773,7 +888,10 @@ def main():
         "cpu_baseline": {"value": par_n / par_dt, "unit": UNIT, "cores": ncores, "kind": "oracle",
                          "sample": f"{par_n} particles of the same workload ({ncores} processes on the host cores, "
                                    f"{cpu_model()}, each on its own elements), one FP64 step + gridpoint moments; "
-                                   f"single core: {cpu_n / cpu_dt:.4g} particle-updates/s on {cpu_n} particles"},
+                                   f"single core: {cpu_n / cpu_dt:.4g} particle-updates/s on {cpu_n} particles",
+                         "single_core": cpu_n / cpu_dt,
+                         "cavity_single_core": {"value": cav_n / cav_dt, "sample": f"{cav_n} particles of the "
+                                                "cavity-200k-20M workload, one FP64 step + gridpoint moments"}},
         "clocks": r["clocks"],
         "e2e": {"value": P_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"],
                 "note": "per step: node fields host->device from pinned memory, pdf_step, grid_statistics, "
@@ -781,7 +899,9 @@ def main():
                         "(double-buffered) and the host reads step k's statistics while step k + 1 runs; the "
                         "particle state stays resident in HBM"},
         "gpu_launches": K * LAUNCHES_PER_STEP,
+        "moment_sums_compensated": r["compensated"],
         "gridpoint_solve": r["solve"],
+        "c1": c1,
         "surrogate": surrogate,
         "surrogate_cavity": surrogate_cavity,
         "batched": batched,

@@ -90,6 +90,16 @@ typedef struct {
      * psi_a + psi_b -> psi_p at rate react_k, S_a = S_b = -react_k psi_a psi_b, S_p = +react_k psi_a psi_b */
     int32_t react_a, react_b, react_p;
     double react_k;
+    /* precision of the gridpoint moment sums of lpdf_pdf_step (the statistics at gridpoints,
+     * Introduction item i): 0, each term lambda_a q_k formed in FP32 and summed in FP32 over at
+     * most 16 particles of a lane and the 32 lanes of a warp before the exact 64-bit fixed-point
+     * accumulation (error at most 48 eps32 sum |lambda_a q_k|); 1, compensated: the sums of q,
+     * dx q and dy q over an element's particles ((dx, dy) from its first vertex, formed exactly)
+     * in double-float FP32 arithmetic (error-free products and additions), combined with the
+     * element's FP64 barycentric coefficients in FP64 (error at most 1e-9 sum |lambda_a q_k|,
+     * about 1e-13 in practice). Other values: LPDF_ERR_ARG. lpdf_pdf_step_static supports 0 only
+     * (LPDF_ERR_UNSUPPORTED). */
+    int32_t moment_sums;
 } lpdf_params;
 
 typedef struct lpdf_mesh lpdf_mesh;
@@ -98,7 +108,7 @@ typedef struct lpdf_ctx lpdf_ctx;
 /* Fills *p with C3 = 5, C4 = 0.25, Cphi = 2, C0 = 2.1, Comega1 = 0.5, Comega2 = 0.73,
  * CL = 0.134, Ceta = 72, nu = 1/180, dt = 1e-3, ns = 1, no sources, seed = 1, lid_u = 0,
  * gmodel = 0, pressure_solve = 0, cg_warm_start = 0, dpdx0 = dpdy0 = 0, mixing = 0 (IEM),
- * react_k = 0 (no reaction), react_a = react_b = react_p = 0. */
+ * react_k = 0 (no reaction), react_a = react_b = react_p = 0, moment_sums = 0. */
 void lpdf_params_default(lpdf_params* p);
 
 /* Message of the calling thread's last error ("" if none). Owned by the library. */

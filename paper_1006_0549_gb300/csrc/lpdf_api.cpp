@@ -112,7 +112,7 @@ cudaError_t alloc_pipe(PipeScratch& w, int64_t cap, size_t E, int ns)
 void free_mesh_device(DevMesh& d)
 {
     cudaFree(d.ex); cudaFree(d.ey); cudaFree(d.en); cudaFree(d.ev); cudaFree(d.em); cudaFree(d.master);
-    cudaFree(d.ea); cudaFree(d.eb); cudaFree(d.ecomp); cudaFree(d.cframe);
+    cudaFree(d.ea); cudaFree(d.eb); cudaFree(d.ec); cudaFree(d.ecomp); cudaFree(d.cframe);
     d = DevMesh();
 }
 
@@ -157,6 +157,7 @@ StepParams lpdf::make_step_params(const lpdf_params& p, const lpdf_mesh* m, uint
     }
     source_box(p.n_sources, p.src_x, p.src_y, p.src_r, s.src_box);
     (void)m;
+    s.moment_sums = p.moment_sums;
     return s;
 }
 
@@ -174,6 +175,8 @@ int check_params(const lpdf_params* p)
             return fail(LPDF_ERR_ARG, "source %d sets scalar %d, but ns = %d", i, p->src_alpha[i], p->ns);
     if (!(p->dt > 0.0) || !(p->nu >= 0.0)) return fail(LPDF_ERR_ARG, "need dt > 0 and nu >= 0");
     if (p->mixing < 0 || p->mixing > 1) return fail(LPDF_ERR_ARG, "mixing = %d (0 IEM, 1 IECM)", p->mixing);
+    if (p->moment_sums < 0 || p->moment_sums > 1)
+        return fail(LPDF_ERR_ARG, "moment_sums = %d (0 FP32 partial sums, 1 compensated)", p->moment_sums);
     if (p->react_k > 0.0 && (p->react_a < 0 || p->react_a >= p->ns || p->react_b < 0 || p->react_b >= p->ns ||
                              p->react_p < 0 || p->react_p >= p->ns))
         return fail(LPDF_ERR_ARG, "reaction scalars %d + %d -> %d outside 0..%d", p->react_a, p->react_b, p->react_p,
@@ -262,6 +265,7 @@ int build_mesh(const double* node_xy, int32_t n_nodes, const int32_t* tri, int32
         y0 = std::min(y0, fr[4 * c + 2]); y1 = std::max(y1, fr[4 * c + 3]);
     }
     std::vector<float> ex(4 * (size_t)n_tri), ey(4 * (size_t)n_tri), ea(4 * (size_t)n_tri), eb(4 * (size_t)n_tri);
+    std::vector<double> ec(4 * (size_t)n_tri);
     std::vector<int32_t> en(4 * (size_t)n_tri, -1), ev(4 * (size_t)n_tri, 0), em(4 * (size_t)n_tri, 0);
     for (int e = 0; e < n_tri; ++e) {
         const int* t = tri + 3 * e;
@@ -288,6 +292,10 @@ int build_mesh(const double* node_xy, int32_t n_nodes, const int32_t* tri, int32
         eb[4 * e + 1] = (float)((bx - ax) / A);
         eb[4 * e + 2] = ex[4 * e + 3];
         eb[4 * e + 3] = 0.0f;
+        ec[4 * e + 0] = (cy - ay) / A;
+        ec[4 * e + 1] = -(cx - ax) / A;
+        ec[4 * e + 2] = -(by - ay) / A;
+        ec[4 * e + 3] = (bx - ax) / A;
         for (int k = 0; k < 3; ++k) ev[4 * e + k] = t[k];
         ev[4 * e + 3] = 0;
         en[4 * e + 3] = 0;   // bit k: edge k is periodic
@@ -395,6 +403,8 @@ int build_mesh(const double* node_xy, int32_t n_nodes, const int32_t* tri, int32
         (ce = dalloc(&d.en, n_tri)) != cudaSuccess || (ce = dalloc(&d.ev, n_tri)) != cudaSuccess ||
         (ce = dalloc(&d.em, n_tri)) != cudaSuccess || (ce = dalloc(&d.master, n_nodes)) != cudaSuccess ||
         (ce = dalloc(&d.ea, n_tri)) != cudaSuccess || (ce = dalloc(&d.eb, n_tri)) != cudaSuccess ||
+        (ce = dalloc(&d.ec, n_tri)) != cudaSuccess ||
+        (ce = cudaMemcpy(d.ec, ec.data(), sizeof(double) * ec.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (ce = cudaMemcpy(d.ea, ea.data(), sizeof(float) * ea.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (ce = cudaMemcpy(d.eb, eb.data(), sizeof(float) * eb.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (ce = cudaMemcpy(d.ex, ex.data(), sizeof(float) * ex.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||

@@ -39,6 +39,7 @@ struct DevMesh {
     // lambda_0 = 1 - lambda_1 - lambda_2, (dx, dy) = p - vertex 0
     float4* ea = nullptr;     // (x_v0, y_v0, b1, g1)
     float4* eb = nullptr;     // (b2, g2, centroid x, 0)
+    double4* ec = nullptr;    // (b1, g1, b2, g2) in FP64: the barycentric combination of the moment sums
     // several independent meshes in one (lpdf_mesh_load_multi): the component of every element
     // and each component's half-open frame [x0, x1) x [y0, y1); n_comp = 1 leaves both NULL
     int n_comp = 1;
@@ -74,6 +75,7 @@ struct StepParams {
     const float* beta;        // IECM: n_nodes x 3 ns conditional-mean slopes, else NULL (IEM)
     float react_k;            // reactive source psi_a + psi_b -> psi_p (none when <= 0)
     int react_a, react_b, react_p;
+    int moment_sums;          // 0: FP32 partial sums; 1: compensated (lpdf_params.moment_sums)
 };
 
 struct DevState {

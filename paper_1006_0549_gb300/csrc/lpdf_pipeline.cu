@@ -19,10 +19,12 @@
 //   S4  particle_scatter_kernel: perm_new[offset(record) + rank] = i. perm_new lists the next
 //       buffer in (new element, position) order: a stable counting sort, fully deterministic.
 //   K2  moments_kernel (a warp per element): the element's particles, gathered through perm_new
-//       in canonical order (with one scalar the gathers of the next batch are in flight while
-//       a batch is accumulated); lambda_a' q_k accumulated in FP32 per lane over at most
-//       kLaneChunk particles, a fixed reduce-scatter across the lanes (recursive halving), one
-//       64-bit fixed-point atomic add per node and quantity.
+//       in canonical order, a fixed reduce-scatter across the lanes (recursive halving), one
+//       64-bit fixed-point atomic add per node and quantity. Two precisions (lpdf_params
+//       moment_sums): 0, lambda_a' q_k in FP32 summed in FP32 per lane over at most kLaneChunk
+//       particles; 1, per lane the sums of q, dx q and dy q ((dx, dy) from vertex 0) in
+//       compensated FP32 (double-floats), combined in FP64 with the element's FP64 affine
+//       barycentric coefficients.
 // Every step leaves perm_new as the next step's perm, so the ensemble is re-bucketed by element
 // every step without a separate sort, and the reduction never needs a hash or a binning pass.
 #include <algorithm>
@@ -35,7 +37,7 @@ namespace lpdf {
 namespace {
 
 constexpr int kBlk = 256;          // H: positions per record block
-constexpr int kLaneChunk = 16;     // K2: particles a lane sums in FP32 before the warp reduction
+constexpr int kLaneChunk = 16;     // K2: particles a lane sums before the warp reduction
 constexpr int kScanItems = 4;      // scan: items per thread
 constexpr int kScanThreads = 1024;
 constexpr int kScanTile = kScanItems * kScanThreads;
@@ -526,7 +528,316 @@ __global__ void particle_scatter_kernel(int64_t n, const uint16_t* __restrict__ 
 // ------------------------------------------------------------------------------------------
 // K2
 // ------------------------------------------------------------------------------------------
-// kFlux: the same reduction of the scalar fluxes u_i psi_a (IECM) into their own accumulators
+// Error-free transformations in FP32 (Knuth's two-sum; the two-product by FMA): a + b = s + e and
+// a b = p + e exactly. A double-float is an unevaluated sum h + l of two FP32 values.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    const float t = __fadd_rn(a, b);
+    const float bb = __fsub_rn(t, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(t, bb)), __fsub_rn(b, bb));
+    s = t;
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e)
+{
+    const float t = __fmul_rn(a, b);
+    e = fmaf(a, b, -t);
+    p = t;
+}
+// (s + c) += (th + tl): the rounding error of s + th is kept exactly and added to c with tl
+__device__ __forceinline__ void df_acc(float& s, float& c, float th, float tl)
+{
+    float e;
+    two_sum(s, th, s, e);
+    c = __fadd_rn(c, __fadd_rn(e, tl));
+}
+// the same on pairs of independent values (packed FP32x2 instructions of sm_100+)
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e)
+{
+    const float2 t = __fadd2_rn(a, b);
+    const float2 bb = __fadd2_rn(t, neg2(a));
+    e = __fadd2_rn(__fadd2_rn(a, neg2(__fadd2_rn(t, neg2(bb)))), __fadd2_rn(b, neg2(bb)));
+    s = t;
+}
+__device__ __forceinline__ void df_acc2(float2& s, float2& c, float2 th, float2 tl)
+{
+    float2 e;
+    two_sum2(s, th, s, e);
+    c = __fadd2_rn(c, __fadd2_rn(e, tl));
+}
+
+// Quantity groups of the moment sums (columns of the node accumulators from COL0 on, NQTOT per node):
+//   G = 0: 1, u, v, w, uu, uv, uw, vv, vw, ww, omega (the velocity and frequency statistics);
+//   G = 1: psi_a, psi_a^2 (a < NS);  G = 2: u psi_a, v psi_a, w psi_a (the scalar fluxes of IECM).
+// PROD(j): quantity j is a product of two state fields (a double-float); else it is exact in FP32.
+template <int NS, int G>
+struct QGroup {
+    static constexpr int NQ = G == 0 ? 11 : (G == 1 ? 2 * NS : 3 * NS);
+    static constexpr int COL0 = G == 1 ? 11 : 0;
+    static constexpr int NQTOT = G == 2 ? 3 * NS : 11 + 2 * NS;
+    static constexpr int NFLD = G == 0 ? 4 : (G == 1 ? NS : 3 + NS);   // gathered fields besides x, y
+    __host__ __device__ static constexpr bool PROD(int j)
+    {
+        return G == 0 ? (j >= 4 && j <= 9) : (G == 1 ? j >= NS : true);
+    }
+};
+
+template <int NS, int G>
+__device__ __forceinline__ void gather_fields(const DevState& S, int j, float* f)
+{
+    if (G == 0) {
+        f[0] = S.u[j];
+        f[1] = S.v[j];
+        f[2] = S.w[j];
+        f[3] = S.om[j];
+    } else if (G == 1) {
+#pragma unroll
+        for (int a = 0; a < NS; ++a) f[a] = S.psi[(size_t)a * S.cap + j];
+    } else {
+        f[0] = S.u[j];
+        f[1] = S.v[j];
+        f[2] = S.w[j];
+#pragma unroll
+        for (int a = 0; a < NS; ++a) f[3 + a] = S.psi[(size_t)a * S.cap + j];
+    }
+}
+
+template <int NS, int G>
+__device__ __forceinline__ void quantities_df(const float* f, float* qh, float* ql)
+{
+    if (G == 0) {
+        const float u = f[0], v = f[1], w = f[2];
+        qh[0] = 1.0f; qh[1] = u; qh[2] = v; qh[3] = w; qh[10] = f[3];
+        ql[0] = ql[1] = ql[2] = ql[3] = ql[10] = 0.0f;
+        two_prod(u, u, qh[4], ql[4]);
+        two_prod(u, v, qh[5], ql[5]);
+        two_prod(u, w, qh[6], ql[6]);
+        two_prod(v, v, qh[7], ql[7]);
+        two_prod(v, w, qh[8], ql[8]);
+        two_prod(w, w, qh[9], ql[9]);
+    } else if (G == 1) {
+#pragma unroll
+        for (int a = 0; a < NS; ++a) {
+            qh[a] = f[a];
+            ql[a] = 0.0f;
+            two_prod(f[a], f[a], qh[NS + a], ql[NS + a]);
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < NS; ++a)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) two_prod(f[c], f[3 + a], qh[3 * a + c], ql[3 * a + c]);
+    }
+}
+
+// One step of the warp reduce-scatter of double-float columns: with offset O, a lane keeps the half
+// of its live columns that its lane bit O selects, in its low entries, and adds the partner's copy
+// of them (a compensated addition). LA, LB: live entries of (ah, al) (columns i) and (bh, bl)
+// (columns i + 32) before the step.
+template <int O, int LA, int LB>
+__device__ __forceinline__ void halve_df(float (&ah)[32], float (&al)[32], float (&bh)[32], float (&bl)[32], bool up)
+{
+#pragma unroll
+    for (int i = 0; i < (LA < O ? LA : O); ++i) {
+        const float loh = ah[i], lol = al[i];
+        const float hih = O + i < LA ? ah[O + i] : 0.0f, hil = O + i < LA ? al[O + i] : 0.0f;
+        const float rh = __shfl_xor_sync(kFull, up ? loh : hih, O), rl = __shfl_xor_sync(kFull, up ? lol : hil, O);
+        float s, e;
+        two_sum(up ? hih : loh, rh, s, e);
+        ah[i] = s;
+        al[i] = __fadd_rn(__fadd_rn(up ? hil : lol, rl), e);
+    }
+#pragma unroll
+    for (int i = 0; i < (LB < O ? LB : O); ++i) {
+        const float loh = bh[i], lol = bl[i];
+        const float hih = O + i < LB ? bh[O + i] : 0.0f, hil = O + i < LB ? bl[O + i] : 0.0f;
+        const float rh = __shfl_xor_sync(kFull, up ? loh : hih, O), rl = __shfl_xor_sync(kFull, up ? lol : hil, O);
+        float s, e;
+        two_sum(up ? hih : loh, rh, s, e);
+        bh[i] = s;
+        bl[i] = __fadd_rn(__fadd_rn(up ? hil : lol, rl), e);
+    }
+}
+
+__host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
+
+// Column sums of NK <= 64 per-lane double-floats over the warp, by recursive halving: after the
+// steps with offsets 16, 8, 4, 2, 1 lane j holds the sums of columns j and j + 32 (zero when
+// j + 32 >= NK). The order of the additions is fixed: every launch gives the same bits.
+template <int NK>
+__device__ __forceinline__ void warp_reduce_scatter_df(const float (&sh)[NK], const float (&sl)[NK], int lane,
+                                                       float& h0, float& l0, float& h1, float& l1)
+{
+    static_assert(NK >= 1 && NK <= 64, "at most two columns per lane");
+    constexpr int A0 = cmin(NK, 32), B0 = NK > 32 ? NK - 32 : 0;
+    float ah[32], al[32], bh[32], bl[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        ah[i] = i < NK ? sh[i] : 0.0f;
+        al[i] = i < NK ? sl[i] : 0.0f;
+        bh[i] = 32 + i < NK ? sh[32 + i] : 0.0f;
+        bl[i] = 32 + i < NK ? sl[32 + i] : 0.0f;
+    }
+    halve_df<16, A0, B0>(ah, al, bh, bl, (lane & 16) != 0);
+    halve_df<8, cmin(A0, 16), cmin(B0, 16)>(ah, al, bh, bl, (lane & 8) != 0);
+    halve_df<4, cmin(A0, 8), cmin(B0, 8)>(ah, al, bh, bl, (lane & 4) != 0);
+    halve_df<2, cmin(A0, 4), cmin(B0, 4)>(ah, al, bh, bl, (lane & 2) != 0);
+    halve_df<1, cmin(A0, 2), cmin(B0, 2)>(ah, al, bh, bl, (lane & 1) != 0);
+    h0 = ah[0];
+    l0 = al[0];
+    h1 = B0 > 0 ? bh[0] : 0.0f;
+    l1 = B0 > 0 ? bl[0] : 0.0f;
+}
+
+__device__ __forceinline__ long long to_fixed64(double v, unsigned& err)
+{
+    if (!(fabs(v) < (double)kFixLimit)) err |= kErrOverflow;
+    return __double2ll_rn(v * 4294967296.0);
+}
+
+// One quantity group over the particles idx[0..LC) of a lane (a chunk of the element's particles).
+// With (dx, dy) = p - vertex 0 formed exactly as double-floats, the barycentrics are affine,
+// lambda_1 = b1 dx + g1 dy, lambda_2 = b2 dx + g2 dy, lambda_0 = 1 - lambda_1 - lambda_2, so the
+// element's sums are
+//   S_1 = b1 Tx + g1 Ty,  S_2 = b2 Tx + g2 Ty,  S_0 = T0 - S_1 - S_2,
+//   T0 = sum q,  Tx = sum dx q,  Ty = sum dy q.
+// T0, Tx, Ty are summed in double-float (exact products, compensated additions) per lane and over
+// the warp; the FP64 coefficients of the element combine them in FP64 and each node sum gets one
+// 64-bit fixed-point add per quantity.
+template <int NS, int G>
+__device__ __forceinline__ void moment_group(const DevState& S, const int* __restrict__ perm, int base, int end,
+                                            float X0, float Y0, const double4& co, const int4& mv, int lane,
+                                            unsigned long long* __restrict__ node_acc, unsigned& err)
+{
+    using Q = QGroup<NS, G>;
+    constexpr int NQ = Q::NQ, NK = 3 * NQ, NF = Q::NFLD;
+    constexpr int NP = (NQ + 1) / 2;
+    float2 s0[NP], c0[NP], sxy[NQ], cxy[NQ];   // T0 of quantities (2i, 2i + 1); (Tx, Ty) of quantity j
+#pragma unroll
+    for (int k = 0; k < NP; ++k) s0[k] = c0[k] = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) sxy[k] = cxy[k] = make_float2(0.0f, 0.0f);
+    // the lane's particles base + lane + 32 k in canonical order, one per iteration (the loop is
+    // not unrolled: its body is already several hundred instructions); the gather order two
+    // particles ahead and the fields one particle ahead are loaded before a particle is summed
+    int pos = base + lane;
+    int j1 = pos < end ? perm[pos] : -1;
+    int j2 = pos + 32 < end ? perm[pos + 32] : -1;
+    float cx = 0.0f, cy = 0.0f, cf[NF];
+    if (j1 >= 0) {
+        cx = S.x[j1];
+        cy = S.y[j1];
+        gather_fields<NS, G>(S, j1, cf);
+    }
+#pragma unroll 1
+    for (; j1 >= 0; pos += 32) {
+        const int j3 = pos + 64 < end ? perm[pos + 64] : -1;
+        float nx = 0.0f, ny = 0.0f, nf[NF];
+        if (j2 >= 0) {
+            nx = S.x[j2];
+            ny = S.y[j2];
+            gather_fields<NS, G>(S, j2, nf);
+        }
+        // (dx, dy) = p - vertex 0 as exact double-floats (dh + dl), x and y packed
+        float2 dh, dl;
+        two_sum2(make_float2(cx, cy), make_float2(-X0, -Y0), dh, dl);
+        float qh[NQ], ql[NQ];
+        quantities_df<NS, G>(cf, qh, ql);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            const int j = 2 * i;
+            df_acc2(s0[i], c0[i], make_float2(qh[j], j + 1 < NQ ? qh[j + 1] : 0.0f),
+                    make_float2(ql[j], j + 1 < NQ ? ql[j + 1] : 0.0f));
+        }
+#pragma unroll
+        for (int j = 0; j < NQ; ++j) {
+            // (dh + dl)(qh + ql): the exact product of the leading parts plus the cross terms
+            const float2 q2 = make_float2(qh[j], qh[j]);
+            const float2 ph = __fmul2_rn(dh, q2);
+            float2 pl = __ffma2_rn(dh, q2, neg2(ph));
+            pl = __ffma2_rn(dl, q2, pl);
+            if (Q::PROD(j)) pl = __ffma2_rn(dh, make_float2(ql[j], ql[j]), pl);
+            df_acc2(sxy[j], cxy[j], ph, pl);
+        }
+        j1 = j2;
+        j2 = j3;
+        cx = nx;
+        cy = ny;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) cf[f] = nf[f];
+    }
+    // columns T0 (0 .. NQ - 1), Tx (NQ ..), Ty (2 NQ ..); lane j ends with columns j and j + 32
+    float sh[NK], sl[NK];
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) {
+        sh[j] = j & 1 ? s0[j / 2].y : s0[j / 2].x;
+        sl[j] = j & 1 ? c0[j / 2].y : c0[j / 2].x;
+        sh[NQ + j] = sxy[j].x;
+        sl[NQ + j] = cxy[j].x;
+        sh[2 * NQ + j] = sxy[j].y;
+        sl[2 * NQ + j] = cxy[j].y;
+    }
+    float h0, l0, h1, l1;
+    warp_reduce_scatter_df<NK>(sh, sl, lane, h0, l0, h1, l1);
+    // lane j < NQ: T0 (column j, its own), Tx (column NQ + j) and Ty (column 2 NQ + j)
+    const int cxc = NQ + lane, cyc = 2 * NQ + lane;
+    const float xh0 = __shfl_sync(kFull, h0, cxc & 31), xl0 = __shfl_sync(kFull, l0, cxc & 31);
+    const float xh1 = __shfl_sync(kFull, h1, cxc & 31), xl1 = __shfl_sync(kFull, l1, cxc & 31);
+    const float yh0 = __shfl_sync(kFull, h0, cyc & 31), yl0 = __shfl_sync(kFull, l0, cyc & 31);
+    const float yh1 = __shfl_sync(kFull, h1, cyc & 31), yl1 = __shfl_sync(kFull, l1, cyc & 31);
+    if (lane < NQ) {
+        const double T0 = (double)h0 + (double)l0;
+        const double Tx = cxc < 32 ? (double)xh0 + (double)xl0 : (double)xh1 + (double)xl1;
+        const double Ty = cyc < 32 ? (double)yh0 + (double)yl0 : (double)yh1 + (double)yl1;
+        const double S1 = co.x * Tx + co.y * Ty;
+        const double S2 = co.z * Tx + co.w * Ty;
+        const double S0 = (T0 - S1) - S2;
+        const int col = Q::COL0 + lane;
+        const long long v0 = to_fixed64(S0, err), v1 = to_fixed64(S1, err), v2 = to_fixed64(S2, err);
+        if (v0 != 0) atomicAdd(&node_acc[(size_t)mv.x * Q::NQTOT + col], (unsigned long long)v0);
+        if (v1 != 0) atomicAdd(&node_acc[(size_t)mv.y * Q::NQTOT + col], (unsigned long long)v1);
+        if (v2 != 0) atomicAdd(&node_acc[(size_t)mv.z * Q::NQTOT + col], (unsigned long long)v2);
+    }
+}
+
+// K2 with compensated sums (moment_sums = 1). kFlux: the sums of the scalar fluxes u_i psi_a
+// (IECM) into their own accumulators instead
+template <int NS, int MBLK, int MMINB, bool kFlux = false>
+__global__ void __launch_bounds__(MBLK, MMINB) moments_kernel_df(const __grid_constant__ DevMesh M,
+                                                      const __grid_constant__ DevState S,
+                                                      const int* __restrict__ perm, const int* __restrict__ kstart,
+                                                      unsigned long long* __restrict__ node_acc,
+                                                      unsigned long long* __restrict__ status)
+{
+    const int e = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (e >= M.n_tri) return;
+    const int p0 = kstart[e], p1 = kstart[e + 1];
+    if (p0 >= p1) return;
+    const float4 A = __ldg(&M.ea[e]);
+    const double2 c01 = __ldg(reinterpret_cast<const double2*>(M.ec + e)), c23 = __ldg(reinterpret_cast<const double2*>(M.ec + e) + 1);
+    const double4 co = make_double4(c01.x, c01.y, c23.x, c23.y);
+    const int4 mv = __ldg(&M.em[e]);
+    unsigned err = 0;
+    constexpr int LC = kLaneChunk;   // particles per lane and chunk
+#pragma unroll 1
+    for (int base = p0; base < p1; base += 32 * LC) {
+        const int end = min(p1, base + 32 * LC);
+        if (kFlux) {
+            moment_group<NS, 2>(S, perm, base, end, A.x, A.y, co, mv, lane, node_acc, err);
+        } else {
+            moment_group<NS, 0>(S, perm, base, end, A.x, A.y, co, mv, lane, node_acc, err);
+            moment_group<NS, 1>(S, perm, base, end, A.x, A.y, co, mv, lane, node_acc, err);
+        }
+    }
+    const unsigned e_or = __reduce_or_sync(kFull, err);
+    if (lane == 0 && e_or) atomicOr(&status[0], (unsigned long long)e_or);
+}
+
+// K2 with FP32 partial sums (moment_sums = 0, the throughput configuration): lambda_a' q_k formed
+// in FP32 and accumulated in FP32 per lane over at most kLaneChunk particles, then a fixed
+// reduce-scatter across the lanes, one 64-bit fixed-point atomic add per node and quantity. kFlux:
+// the same reduction of the scalar fluxes u_i psi_a (IECM) into their own accumulators.
 // One step of the warp reduce-scatter below: with offset O, a lane keeps the half of its live
 // columns that its lane bit O selects, in its low entries, and adds the partner's copy of them.
 // LA, LB: live entries of a (columns base + i) and b (columns base + i + 32) before the step.
@@ -544,8 +855,6 @@ __device__ __forceinline__ void halve(float (&a)[32], float (&b)[32], bool up)
         b[i] = (up ? hi : lo) + __shfl_xor_sync(kFull, up ? lo : hi, O);
     }
 }
-
-__host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
 
 // Column sums of NK <= 64 per-lane values over the warp, by recursive halving: after the steps
 // with offsets 16, 8, 4, 2, 1 lane j holds the sums of columns j (lo) and j + 32 (hi, zero when
@@ -572,7 +881,7 @@ __device__ __forceinline__ void warp_reduce_scatter(const float (&acc)[NK], int 
 }
 
 template <int NS, int MBLK, int MMINB, bool kFlux = false>
-__global__ void __launch_bounds__(MBLK, MMINB) moments_kernel(const __grid_constant__ DevMesh M,
+__global__ void __launch_bounds__(MBLK, MMINB) moments_kernel_f32(const __grid_constant__ DevMesh M,
                                                       const __grid_constant__ DevState S,
                                                       const int* __restrict__ perm, const int* __restrict__ kstart,
                                                       unsigned long long* __restrict__ node_acc,
@@ -754,15 +1063,24 @@ void launch_advance(int v, const DevMesh& m, const DevState& cur, const DevState
 }
 
 template <int NS>
-void launch_moments(int v, const DevMesh& m, const DevState& s, const int* perm, const int* kstart,
+void launch_moments(int v, int mode, const DevMesh& m, const DevState& s, const int* perm, const int* kstart,
                     unsigned long long* node_acc, unsigned long long* status, cudaStream_t st)
 {
     const int64_t threads = (int64_t)m.n_tri * 32;
+    if (mode == 1) {
+        switch (v) {
+            case 1: moments_kernel_df<NS, 128, 4><<<nblocks(threads, 128), 128, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
+            case 2: moments_kernel_df<NS, 512, 1><<<nblocks(threads, 512), 512, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
+            case 3: moments_kernel_df<NS, 256, 1><<<nblocks(threads, 256), 256, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
+            default: moments_kernel_df<NS, 256, 2><<<nblocks(threads, 256), 256, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
+        }
+        return;
+    }
     switch (v) {
-        case 1: moments_kernel<NS, 128, 4><<<nblocks(threads, 128), 128, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
-        case 2: moments_kernel<NS, 512, 1><<<nblocks(threads, 512), 512, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
-        case 3: moments_kernel<NS, 256, 3><<<nblocks(threads, 256), 256, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
-        default: moments_kernel<NS, 256, 2><<<nblocks(threads, 256), 256, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
+        case 1: moments_kernel_f32<NS, 128, 4><<<nblocks(threads, 128), 128, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
+        case 2: moments_kernel_f32<NS, 512, 1><<<nblocks(threads, 512), 512, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
+        case 3: moments_kernel_f32<NS, 256, 3><<<nblocks(threads, 256), 256, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
+        default: moments_kernel_f32<NS, 256, 2><<<nblocks(threads, 256), 256, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
     }
 }
 
@@ -799,10 +1117,15 @@ cudaError_t run_pipeline(const DevMesh& m, const DevState& cur, const DevState& 
                                                                        w.rec_cnt, w.rec_off);
     particle_scatter_kernel<<<nblocks(n, 256 * kScatterPer), 256, 0, st>>>(n, w.rrank, w.rec_off, w.perm_new);
     if (ev) cudaEventRecord(ev[2], st);
-    launch_moments<NS>(tune.mom, m, nxt, w.perm_new, w.kstart, node_acc, status, st);
-    if (flux_acc)
-        moments_kernel<NS, 256, 2, true><<<nblocks((int64_t)E * 32, 256), 256, 0, st>>>(m, nxt, w.perm_new, w.kstart,
-                                                                                      flux_acc, status);
+    launch_moments<NS>(tune.mom, p.moment_sums, m, nxt, w.perm_new, w.kstart, node_acc, status, st);
+    if (flux_acc) {
+        if (p.moment_sums == 1)
+            moments_kernel_df<NS, 256, 2, true><<<nblocks((int64_t)E * 32, 256), 256, 0, st>>>(m, nxt, w.perm_new,
+                                                                                             w.kstart, flux_acc, status);
+        else
+            moments_kernel_f32<NS, 256, 2, true><<<nblocks((int64_t)E * 32, 256), 256, 0, st>>>(m, nxt, w.perm_new,
+                                                                                              w.kstart, flux_acc, status);
+    }
     if (ev) cudaEventRecord(ev[3], st);
     return cudaGetLastError();
 }

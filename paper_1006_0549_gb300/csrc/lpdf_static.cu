@@ -78,6 +78,10 @@ extern "C" int lpdf_pdf_step_static(const lpdf_mesh* mesh, const lpdf_params* pa
         lpdf_set_error(LPDF_ERR_UNSUPPORTED, "pdf_step_static: IECM and reactive sources need a context");
         return LPDF_ERR_UNSUPPORTED;
     }
+    if (params->moment_sums != 0) {
+        lpdf_set_error(LPDF_ERR_UNSUPPORTED, "pdf_step_static: compensated moment sums need a context");
+        return LPDF_ERR_UNSUPPORTED;
+    }
     if (n < 0 || (n > 0 && (!x || !y || !u || !v || !w || !omega || !psi || !elem || !pid))) {
         lpdf_set_error(LPDF_ERR_ARG, "pdf_step_static: bad particle arrays");
         return LPDF_ERR_ARG;

@@ -73,7 +73,7 @@ class Params(ctypes.Structure):
                 ("gmodel", ctypes.c_int32), ("pressure_solve", ctypes.c_int32), ("cg_warm_start", ctypes.c_int32),
                 ("dpdx0", ctypes.c_double), ("dpdy0", ctypes.c_double),
                 ("mixing", ctypes.c_int32), ("react_a", ctypes.c_int32), ("react_b", ctypes.c_int32),
-                ("react_p", ctypes.c_int32), ("react_k", ctypes.c_double)]
+                ("react_p", ctypes.c_int32), ("react_k", ctypes.c_double), ("moment_sums", ctypes.c_int32)]
 
 
 _lib = None

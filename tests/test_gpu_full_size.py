@@ -11,7 +11,8 @@ can compute one by one:
     brute force by the oracle tests), and 300 by the oracle's brute force: element ids
     bit-exact; where the GPU position equals the oracle's bit for bit, the element does too;
   * the moment sums at 300 sampled gridpoints against the oracle's reduction of every particle
-    whose new element touches them.
+    whose new element touches them: FP32 partial sums within 48 eps32 and, from the same input
+    state with compensated sums, within 1e-9 of sum |lambda q|.
 Then the same step, from the same input state, in the autotuner's configuration and in another
 one: bit-identical state and moment sums at full size. The 64-channel batch (268M particles) is
 checked per component (last test)."""
@@ -84,9 +85,32 @@ def test_full_size_sampled_parity(torch_cuda, name):
     f = lambda a: a.astype(np.float64)
     So, Sabs = oracle.moments(om, wk.ns, f(sub.x), f(sub.y), f(sub.u), f(sub.v), f(sub.w), f(sub.omega),
                               f(sub.psi), sub.elem)
-    tol = 48 * gc.EPS32 * Sabs[nodes] + np.maximum(So[nodes, :1], 1.0) * 8.0 * 2.0 ** -33
+    tol = gc.moment_tolerance(So[nodes], Sabs[nodes])
     err = np.abs(S[nodes] - So[nodes])
     assert np.all(err <= tol), (nodes[np.argwhere(err > tol)[:5, 0]], err[err > tol][:5], tol[err > tol][:5])
+
+    # the same step with compensated moment sums: the same new state, sums within 1e-9
+    params.moment_sums = 1
+    ctx.set_params(params)
+    ctx.set_state(gc.torch_state(before))
+    ctx.pdf_step(Fd, s1)
+    rc, status = ctx.status(raise_on_error=False)
+    assert rc == lpdf.LPDF_OK, status
+    S1 = torch.empty((mesh.n_nodes, nq), dtype=torch.float64, device="cuda")
+    ctx.grid_statistics(S1, raw=True)
+    after1 = gc.host_state(ctx.get_state(device=False), wk.ns)
+    torch.cuda.synchronize()
+    after1 = gc.reorder(after1, gc.match_pids(after.pid, after1.pid))   # set_state restarts the order
+    for k in gc.FIELDS + ("elem",):
+        assert np.array_equal(getattr(after1, k), getattr(after, k)), k
+    S1 = S1.cpu().numpy()
+    tol1 = gc.moment_tolerance(So[nodes], Sabs[nodes], "compensated")
+    err1 = np.abs(S1[nodes] - So[nodes])
+    assert np.all(err1 <= tol1), (nodes[np.argwhere(err1 > tol1)[:5, 0]], err1[err1 > tol1][:5])
+    print(name, "sampled node sums, max error / sum|lambda q|:", float(np.max(err / np.maximum(Sabs[nodes], 1e-300))),
+          "(FP32 partials),", float(np.max(err1 / np.maximum(Sabs[nodes], 1e-300))), "(compensated)")
+    params.moment_sums = 0
+    ctx.set_params(params)
 
     # the tuned configuration and another one, from the same input state: the same bits
     other = (0, 0) if tuple(choice) != (0, 0) else (3, 2)

@@ -54,9 +54,11 @@ def test_one_step_with_iecm_and_reaction(torch_cuda):
     gc.compare_moments(om, g, S, NS)
 
 
-def test_flux_sums_and_covariances_match_the_oracle(torch_cuda):
+@pytest.mark.parametrize("ms", [0, 1])
+def test_flux_sums_and_covariances_match_the_oracle(torch_cuda, ms):
     torch = torch_cuda
     mesh, params, st, F, beta = _case()
+    params.moment_sums = ms
     gm = lpdf.Mesh(mesh)
     om = oracle.OracleMesh(mesh)
     ctx = lpdf.Context(gm, params, st.n + 128)
@@ -75,9 +77,9 @@ def test_flux_sums_and_covariances_match_the_oracle(torch_cuda):
     psi = g.psi.astype(np.float64)
     want = oracle.flux_moments(om, NS, x, y, u, v, w, psi, g.elem)
     scale = oracle.flux_moments(om, NS, x, y, np.abs(u), np.abs(v), np.abs(w), np.abs(psi), g.elem)
-    # FP32 products summed over at most 16 particles per lane and a 32-lane butterfly, then exact
-    # fixed-point accumulation: the moment-sum bound of the plain statistics
-    assert np.all(np.abs(Fr.cpu().numpy() - want) <= 48 * 2.0 ** -24 * scale * 3 + 2.0 ** -30)
+    # the flux sums go through the reduction of the plain statistics, in its precision
+    bound = "compensated" if params.moment_sums == 1 else "fp32"
+    assert np.all(np.abs(Fr.cpu().numpy() - want) <= gc.MOMENT_RTOL[bound] * scale + 2.0 ** -30)
     cov = of.flux_covariances(S.cpu().numpy(), Fr.cpu().numpy(), NS)
     assert np.allclose(Fc.cpu().numpy(), cov, rtol=1e-12, atol=1e-12)
 

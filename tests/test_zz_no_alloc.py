@@ -120,15 +120,16 @@ def test_static_entry_point_rejects_oversized_mesh():
 
 
 def test_static_entry_point_rejects_iecm_and_reactions():
-    """The static entry point's fused kernel mixes with IEM only: IECM and a reactive source are
-    refused (they need a context), not silently dropped."""
+    """The static entry point's fused kernel mixes with IEM only and sums the moments in FP32
+    partials: IECM, a reactive source and compensated moment sums are refused (they need a
+    context), not silently dropped."""
     torch = _cuda()
     small = wl.cavity_mesh(4, 4, 1)
     mesh = lpdf.Mesh(small)
     F = torch.zeros((small.n_nodes, wl.n_fields_padded(3)), dtype=torch.float32, device="cuda")
     moments = torch.zeros((small.n_nodes, 17), dtype=torch.float64, device="cuda")
     st = wl.synthetic_state(small, 1, 3, seed=1)
-    for kw in ({"mixing": 1}, {"react_k": 5.0, "react_a": 0, "react_b": 1, "react_p": 2}):
+    for kw in ({"mixing": 1}, {"react_k": 5.0, "react_a": 0, "react_b": 1, "react_p": 2}, {"moment_sums": 1}):
         params = lpdf.make_params(nu=1e-4, dt=1e-3, seed=1, ns=3)
         for k, v in kw.items():
             setattr(params, k, v)
