@@ -112,7 +112,7 @@ cudaError_t alloc_pipe(PipeScratch& w, int64_t cap, size_t E, int ns)
 void free_mesh_device(DevMesh& d)
 {
     cudaFree(d.ex); cudaFree(d.ey); cudaFree(d.en); cudaFree(d.ev); cudaFree(d.em); cudaFree(d.master);
-    cudaFree(d.ea); cudaFree(d.eb); cudaFree(d.ec); cudaFree(d.ecomp); cudaFree(d.cframe);
+    cudaFree(d.ea); cudaFree(d.eb); cudaFree(d.ec); cudaFree(d.ew); cudaFree(d.ecomp); cudaFree(d.cframe);
     d = DevMesh();
 }
 
@@ -398,13 +398,22 @@ int build_mesh(const double* node_xy, int32_t n_nodes, const int32_t* tri, int32
     for (size_t q = 0; q < cf.size(); ++q) cf[q] = (float)fr[q];
     d.period = periodic ? (float)period_x : 0.0f;
     m->box[0] = x0; m->box[1] = x1; m->box[2] = y0; m->box[3] = y1;
+    std::vector<float> ew(16 * (size_t)n_tri, 0.0f);
+    for (int e = 0; e < n_tri; ++e) {
+        for (int q = 0; q < 4; ++q) {
+            ew[16 * (size_t)e + q] = ea[4 * (size_t)e + q];
+            ew[16 * (size_t)e + 4 + q] = eb[4 * (size_t)e + q];
+            std::memcpy(&ew[16 * (size_t)e + 8 + q], &en[4 * (size_t)e + q], sizeof(float));
+        }
+    }
     cudaError_t ce = cudaSuccess;
     if ((ce = dalloc(&d.ex, n_tri)) != cudaSuccess || (ce = dalloc(&d.ey, n_tri)) != cudaSuccess ||
         (ce = dalloc(&d.en, n_tri)) != cudaSuccess || (ce = dalloc(&d.ev, n_tri)) != cudaSuccess ||
         (ce = dalloc(&d.em, n_tri)) != cudaSuccess || (ce = dalloc(&d.master, n_nodes)) != cudaSuccess ||
         (ce = dalloc(&d.ea, n_tri)) != cudaSuccess || (ce = dalloc(&d.eb, n_tri)) != cudaSuccess ||
-        (ce = dalloc(&d.ec, n_tri)) != cudaSuccess ||
+        (ce = dalloc(&d.ec, n_tri)) != cudaSuccess || (ce = dalloc(&d.ew, 4 * (size_t)n_tri)) != cudaSuccess ||
         (ce = cudaMemcpy(d.ec, ec.data(), sizeof(double) * ec.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (ce = cudaMemcpy(d.ew, ew.data(), sizeof(float) * ew.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (ce = cudaMemcpy(d.ea, ea.data(), sizeof(float) * ea.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (ce = cudaMemcpy(d.eb, eb.data(), sizeof(float) * eb.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (ce = cudaMemcpy(d.ex, ex.data(), sizeof(float) * ex.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||

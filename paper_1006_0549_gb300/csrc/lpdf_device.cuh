@@ -313,9 +313,10 @@ static __device__ __noinline__ int fast_wall_exit(float l0, float l1, float l2, 
 template <bool kWalls = false>
 __device__ __forceinline__ int walk_test_fast(const DevMesh& M, int e, float px, float py, int& next)
 {
-    const float4 A = __ldg(&M.ea[e]);
-    const float4 B = __ldg(&M.eb[e]);
-    const int4 N = __ldg(&M.en[e]);
+    const float4* W = M.ew + 4 * (size_t)e;
+    const float4 A = __ldg(W);
+    const float4 B = __ldg(W + 1);
+    const int4 N = __ldg(reinterpret_cast<const int4*>(W + 2));
     if (M.periodic && fabsf(B.z - px) > 0.5f * M.period) return -1;
     const float dx = __fsub_rn(px, A.x), dy = __fsub_rn(py, A.y);
     const float t1 = A.z * dx, s1 = A.w * dy, t2 = B.x * dx, s2 = B.y * dy;

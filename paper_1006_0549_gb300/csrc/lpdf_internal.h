@@ -40,6 +40,9 @@ struct DevMesh {
     float4* ea = nullptr;     // (x_v0, y_v0, b1, g1)
     float4* eb = nullptr;     // (b2, g2, centroid x, 0)
     double4* ec = nullptr;    // (b1, g1, b2, g2) in FP64: the barycentric combination of the moment sums
+    // the walk's fast test reads one 64-byte record per element: ea, eb and en side by side
+    // (one cache line instead of three), the fourth float4 unused
+    float4* ew = nullptr;
     // several independent meshes in one (lpdf_mesh_load_multi): the component of every element
     // and each component's half-open frame [x0, x1) x [y0, y1); n_comp = 1 leaves both NULL
     int n_comp = 1;
