@@ -92,7 +92,7 @@ typedef struct {
     double react_k;
     /* precision of the gridpoint moment sums of lpdf_pdf_step (the statistics at gridpoints,
      * Introduction item i): 0, each term lambda_a q_k formed in FP32 and summed in FP32 over at
-     * most 16 particles of a lane and the 32 lanes of a warp before the exact 64-bit fixed-point
+     * most 8 particles of a lane and the 32 lanes of a warp before the exact 64-bit fixed-point
      * accumulation (error at most 48 eps32 sum |lambda_a q_k|); 1, compensated: the sums of q,
      * dx q and dy q over an element's particles ((dx, dy) from its first vertex, formed exactly)
      * in double-float FP32 arithmetic (error-free products and additions), combined with the

@@ -37,7 +37,8 @@ namespace lpdf {
 namespace {
 
 constexpr int kBlk = 256;          // H: positions per record block
-constexpr int kLaneChunk = 16;     // K2: particles a lane sums before the warp reduction
+constexpr int kLaneChunk = 8;      // K2: particles a lane sums before the warp reduction
+constexpr int kLaneChunkDf = 16;   // the same with compensated sums (its warp reduction costs more)
 constexpr int kScanItems = 4;      // scan: items per thread
 constexpr int kScanThreads = 1024;
 constexpr int kScanTile = kScanItems * kScanThreads;
@@ -819,7 +820,7 @@ __global__ void __launch_bounds__(MBLK, MMINB) moments_kernel_df(const __grid_co
     const double4 co = make_double4(c01.x, c01.y, c23.x, c23.y);
     const int4 mv = __ldg(&M.em[e]);
     unsigned err = 0;
-    constexpr int LC = kLaneChunk;   // particles per lane and chunk
+    constexpr int LC = kLaneChunkDf;   // particles per lane and chunk
 #pragma unroll 1
     for (int base = p0; base < p1; base += 32 * LC) {
         const int end = min(p1, base + 32 * LC);

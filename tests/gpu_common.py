@@ -163,7 +163,7 @@ def compare_step(mesh: wl.Mesh, om: oracle.OracleMesh, params: lpdf.Params, F, s
 #   elements whose weights cancel.
 # moment_sums = 0 (lpdf_pdf_step's default) and lpdf_pdf_step_static's fused kernel: each term lambda_a q_k formed in FP32 (barycentric
 #   determinants with one FMA-compensated rounding, the division, the products) and summed in FP32
-#   over at most 16 particles of a lane and 5 levels of the warp reduction (the fused kernel: units
+#   over at most 8 particles of a lane and 5 levels of the warp reduction (the fused kernel: units
 #   of at most 6 particles, column sums of at most 32 units): 48 eps32.
 MOMENT_RTOL = {"compensated": 1e-9, "fp32": 48 * EPS32}
 

@@ -23,7 +23,7 @@ def test_source_hash_ignores_comments_but_not_code(tmp_path, monkeypatch):
     text = f.read_text()
     f.write_text("// an added line comment\n/* and a\n block comment */\n\n" + text.replace("\n", "\n\n", 3))
     assert bench.kernel_source_hash() == h0
-    f.write_text(text.replace("constexpr int kLaneChunk = 16;", "constexpr int kLaneChunk = 8;"))
+    f.write_text(text.replace("constexpr int kLaneChunk = 8;", "constexpr int kLaneChunk = 4;"))
     assert bench.kernel_source_hash() != h0
 
 

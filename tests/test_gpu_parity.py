@@ -73,7 +73,7 @@ def test_three_chained_steps_channel(torch_cuda):
 
 @pytest.mark.parametrize("ms", [0, 1])
 def test_ragged_and_tiny_ensembles(torch_cuda, ms):
-    """Sizes that are not multiples of the 16-particle lane chunk, 128-particle tile or 4096 CTA range."""
+    """Sizes that are not multiples of the 8-particle lane chunk, 128-particle tile or 4096 CTA range."""
     wk = wl.channel_small()
     mesh, gm, om, params, F, Fd, ctx, npe = _setup(wk, n_per_elem=10, moment_sums=ms)
     full = wl.synthetic_state(mesh, 10, wk.ns, seed=9)
