@@ -271,8 +271,10 @@ int lpdf_pdf_steps(lpdf_ctx* ctx, const float* node_fields, uint64_t step0, int3
 /* ---------------------------------------------------------------------------------------
  * Launch configuration of the step's kernels. Every configuration gives bit-identical results.
  *   adv (advance kernel): 0 = 256 threads per CTA, >= 4 CTAs per SM (64 registers);
- *       1 = 256, >= 6 (40 registers); 2 = 128, >= 8; 3 = 256, >= 4 on a persistent grid
- *       (CTAs stride over 256-particle tiles); 4 = 256, >= 6, persistent.
+ *       1 = 128, >= 10 (48 registers) on a persistent grid (CTAs stride over 128-particle
+ *       tiles); 2 = 128, >= 8 (64 registers); 3 = 256, >= 4, persistent; 4 = 64, >= 18
+ *       (56 registers), persistent; 5 = 128, >= 10, persistent, each warp taking 64-particle
+ *       chunks in order from a counter in the context's scratch.
  *   mom (moments kernel, a warp per element): 0 = 256 threads, >= 2 CTAs per SM; 1 = 128, >= 4;
  *       2 = 512, >= 1; 3 = 256, >= 3.
  * lpdf_ctx_set_tune sets it (LPDF_ERR_ARG outside those ranges). lpdf_ctx_autotune times every
@@ -283,7 +285,7 @@ int lpdf_pdf_steps(lpdf_ctx* ctx, const float* node_fields, uint64_t step0, int3
  * a variant's time is its fastest trial (the ensemble keeps changing while it is timed). The
  * fastest variants are kept. The trial steps are real steps, numbered from step0: *steps_used
  * (host, may be NULL) tells how many were taken. choice (host, 2 ints, may be NULL) = (adv,
- * mom); trial_ms (host, 9 doubles, may be NULL) = milliseconds per step of each variant (5
+ * mom); trial_ms (host, 10 doubles, may be NULL) = milliseconds per step of each variant (6
  * advance, then 4 moments variants). sync.
  * ------------------------------------------------------------------------------------- */
 int lpdf_ctx_set_tune(lpdf_ctx* ctx, int32_t adv, int32_t mom);

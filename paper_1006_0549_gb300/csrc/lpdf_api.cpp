@@ -102,7 +102,7 @@ cudaError_t alloc_pipe(PipeScratch& w, int64_t cap, size_t E, int ns)
     cudaError_t e = cudaSuccess;
     if ((e = dalloc(&w.perm, cap)) || (e = dalloc(&w.perm_new, cap)) || (e = dalloc(&w.rrank, cap)) ||
         (e = dalloc(&w.rec_key, nrec)) || (e = dalloc(&w.rec_cnt, nrec)) || (e = dalloc(&w.rec_off, nrec)) ||
-        (e = dalloc(&w.nrec, nrec / 256)) || (e = dalloc(&w.kwork, 3 * (E + 1))) || (e = dalloc(&w.kstart, E + 1)) ||
+        (e = dalloc(&w.nrec, nrec / 256)) || (e = dalloc(&w.kwork, 3 * (E + 1) + 1)) || (e = dalloc(&w.kstart, E + 1)) ||
         (e = dalloc(&w.krstart, E + 1)) || (e = dalloc(&w.klist, nrec)) || (e = dalloc(&w.klist2, nrec)) ||
         (e = dalloc(&w.scan_part, 2 * 4096)) || (e = dalloc(&w.efields, E * 3 * (size_t)nfields_padded(ns))))
         return e;

@@ -632,7 +632,10 @@ __device__ __forceinline__ void advance_particle(const DevMesh& M, const float* 
     float Fi[NFP];
     interpolate_fields<NS, kElementTable>(M, F, e, x, y, Fi);
     const float dW1 = P.sdt * z0, dW2 = P.sdt * z1;
-    const float c0e = sqrtf(fmaxf(Fi[LPDF_F_C0EPS], 0.0f));
+    // square roots by the special-function unit's reciprocal square root (about 2 ulp; the step's
+    // tolerance is 1e-5): sqrt(a) = a rsqrt(a) for a > 0
+    const float c0a = fmaxf(Fi[LPDF_F_C0EPS], 0.0f);
+    const float c0e = c0a > 0.0f ? c0a * rsqrtf(c0a) : 0.0f;
     const float Ur = u - Fi[LPDF_F_U + 0], Vr = v - Fi[LPDF_F_U + 1], Wr = w - Fi[LPDF_F_U + 2];
     // Eq. 4
     float un = u + (-Fi[LPDF_F_DPDX] + P.nu2 * Fi[LPDF_F_LAPU] + Fi[LPDF_F_G11] * Ur + Fi[LPDF_F_G11 + 1] * Vr) * P.dt
@@ -644,8 +647,9 @@ __device__ __forceinline__ void advance_particle(const DevMesh& M, const float* 
              + P.s2nu * (Fi[LPDF_F_DUDX + 4] * dW1 + Fi[LPDF_F_DUDX + 5] * dW2) + c0e * (P.sdt * z4);
     // Eq. 5 (S_omega of Eq. 6 is a node field)
     const float Om = Fi[LPDF_F_OMEGA];
+    const float oma = 2.0f * P.C3 * P.C4 * Om * Om * fmaxf(om, 0.0f);
     float omn = om - P.C3 * Om * (om - Om) * P.dt - Fi[LPDF_F_SOMEGA] * Om * om * P.dt
-              + sqrtf(2.0f * P.C3 * P.C4 * Om * Om * fmaxf(om, 0.0f)) * (P.sdt * z5);
+              + (oma > 0.0f ? oma * rsqrtf(oma) : 0.0f) * (P.sdt * z5);
     omn = fabsf(omn);
     // Eq. 9: relaxation to the conditional mean, 1/t_m = C_phi <omega> / 2
     const float mix = P.half_cphi * Om * P.dt;

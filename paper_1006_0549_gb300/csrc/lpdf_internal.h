@@ -128,7 +128,7 @@ struct PipeScratch {
     int* rec_cnt = nullptr;
     int* rec_off = nullptr;
     int* nrec = nullptr;         // records per block
-    int* kwork = nullptr;        // 3 (E + 1): particles, records and cursors per element
+    int* kwork = nullptr;        // 3 (E + 1) + 1: particles, records and cursors per element; K1's chunk counter
     int* kstart = nullptr;       // E + 1: bucket starts
     int* krstart = nullptr;      // E + 1: record-list starts
     int* klist = nullptr;        // records grouped by element, then in block order
@@ -139,13 +139,14 @@ struct PipeScratch {
 // ev (may be NULL): 4 events recorded before the advance kernel, after it, after the re-bucketing
 // kernels and after the moments kernel
 // launch configuration of the step's kernels (lpdf_ctx_autotune); every choice gives
-// bit-identical results. adv: advance kernel 0 = 256 threads, >= 4 CTAs/SM; 1 = 256, >= 6;
-// 2 = 128, >= 8; 3 = 256, >= 4, persistent grid; 4 = 256, >= 6, persistent. mom: moments kernel
+// bit-identical results. adv: advance kernel 0 = 256 threads, >= 4 CTAs/SM; 1 = 128, >= 10,
+// persistent grid; 2 = 128, >= 8; 3 = 256, >= 4, persistent; 4 = 64, >= 18, persistent; 5 = 128,
+// >= 10, persistent, warps taking 64-particle chunks from a counter. mom: moments kernel
 // 0 = 256 threads, >= 2 CTAs/SM; 1 = 128, >= 4; 2 = 512, >= 1; 3 = 256, >= 3.
 struct StepTune {
     int adv = 0, mom = 0;
 };
-constexpr int kAdvVariants = 5, kMomVariants = 4;
+constexpr int kAdvVariants = 6, kMomVariants = 4;
 cudaError_t launch_pdf_step_pipeline(const DevMesh& m, const DevState& cur, const DevState& nxt, int ns,
                                      const float* fields, const StepParams& p, PipeScratch& w,
                                      unsigned long long* node_acc, unsigned long long* status, cudaStream_t st,

@@ -197,22 +197,48 @@ __device__ __forceinline__ void advance_one(const DevMesh& M, const DevState& cu
 }
 
 // K1 variants (the autotuner picks one per context; all give bit-identical results): ABLK
-// threads per CTA, at least MINB CTAs per SM (the register cap), and either one particle per
-// thread over the whole grid or a persistent grid striding over ABLK-particle tiles.
-template <int NS, int kKind, int ABLK, int MINB, bool kPersist>
+// threads per CTA, at least MINB CTAs per SM (the register cap), and the grid: kGrid 0, one
+// particle per thread over the whole grid; 1, a persistent grid striding over ABLK-particle
+// tiles; 2, a persistent grid whose warps take kQChunk-particle chunks in order from a counter
+// (tiles, zero at launch). A warp then never waits for its CTA's other warps nor for a fixed
+// share of tiles: the slow walks spread over all warps. 64 particles per chunk: 128 leave a
+// tail of up to one chunk per warp at 5M particles, and 32 make the counter the bottleneck
+// (781k claims per launch at 25M).
+constexpr int kQChunk = 64;
+template <int NS, int kKind, int ABLK, int MINB, int kGrid>
 __global__ void __launch_bounds__(ABLK, MINB)
 advance_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevState cur,
                const __grid_constant__ DevState nxt, const int* __restrict__ perm, const float* __restrict__ EF,
-               const __grid_constant__ StepParams P, unsigned long long* __restrict__ status)
+               const __grid_constant__ StepParams P, unsigned long long* __restrict__ status,
+               unsigned* __restrict__ tiles)
 {
     const int lane = threadIdx.x & 31;
     unsigned err = 0;
     int hops = 0;
-    const int64_t ntiles = (cur.n + ABLK - 1) / ABLK;
+    if constexpr (kGrid == 2) {
+        const int64_t nch = (cur.n + kQChunk - 1) / kQChunk;
+        unsigned c = 0;
+        if (lane == 0) c = atomicAdd(tiles, 1u);
+        c = __shfl_sync(kFull, c, 0);
 #pragma unroll 1
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += kPersist ? gridDim.x : ntiles) {
-        const int64_t i = tile * ABLK + threadIdx.x;
-        if (i < cur.n) advance_one<NS, kKind>(M, cur, nxt, perm, EF, P, status, i, err, hops);
+        while ((int64_t)c < nch) {
+            // the next chunk is claimed before this one is worked on: its latency is hidden
+            unsigned nx = 0;
+            if (lane == 0) nx = atomicAdd(tiles, 1u);
+#pragma unroll 1
+            for (int k = 0; k < kQChunk / 32; ++k) {
+                const int64_t i = (int64_t)c * kQChunk + 32 * k + lane;
+                if (i < cur.n) advance_one<NS, kKind>(M, cur, nxt, perm, EF, P, status, i, err, hops);
+            }
+            c = __shfl_sync(kFull, nx, 0);
+        }
+    } else {
+        const int64_t ntiles = (cur.n + ABLK - 1) / ABLK;
+#pragma unroll 1
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += kGrid == 1 ? gridDim.x : ntiles) {
+            const int64_t i = tile * ABLK + threadIdx.x;
+            if (i < cur.n) advance_one<NS, kKind>(M, cur, nxt, perm, EF, P, status, i, err, hops);
+        }
     }
     const unsigned e_or = __reduce_or_sync(kFull, err);
     const int h_sum = __reduce_add_sync(kFull, hops);
@@ -1041,25 +1067,28 @@ int sm_count_cached()
     return n;
 }
 
-template <int NS, int kKind, int ABLK, int MINB, bool kPersist>
+template <int NS, int kKind, int ABLK, int MINB, int kGrid>
 void launch_advance_v(const DevMesh& m, const DevState& cur, const DevState& nxt, const int* perm, const float* ef,
-                      const StepParams& p, unsigned long long* status, cudaStream_t st)
+                      const StepParams& p, unsigned long long* status, unsigned* tiles, cudaStream_t st)
 {
     const int64_t ntiles = (cur.n + ABLK - 1) / ABLK;
-    const int64_t grid = kPersist ? std::min<int64_t>(ntiles, (int64_t)sm_count_cached() * MINB) : ntiles;
-    advance_kernel<NS, kKind, ABLK, MINB, kPersist><<<(unsigned)grid, ABLK, 0, st>>>(m, cur, nxt, perm, ef, p, status);
+    const int64_t grid = kGrid ? std::min<int64_t>(ntiles, (int64_t)sm_count_cached() * MINB) : ntiles;
+    advance_kernel<NS, kKind, ABLK, MINB, kGrid>
+        <<<(unsigned)grid, ABLK, 0, st>>>(m, cur, nxt, perm, ef, p, status, tiles);
 }
 
 template <int NS, int kKind>
 void launch_advance(int v, const DevMesh& m, const DevState& cur, const DevState& nxt, const int* perm,
-                    const float* ef, const StepParams& p, unsigned long long* status, cudaStream_t st)
+                    const float* ef, const StepParams& p, unsigned long long* status, unsigned* tiles,
+                    cudaStream_t st)
 {
     switch (v) {
-        case 1: launch_advance_v<NS, kKind, 256, 6, false>(m, cur, nxt, perm, ef, p, status, st); break;
-        case 2: launch_advance_v<NS, kKind, 128, 8, false>(m, cur, nxt, perm, ef, p, status, st); break;
-        case 3: launch_advance_v<NS, kKind, 256, 4, true>(m, cur, nxt, perm, ef, p, status, st); break;
-        case 4: launch_advance_v<NS, kKind, 256, 6, true>(m, cur, nxt, perm, ef, p, status, st); break;
-        default: launch_advance_v<NS, kKind, 256, 4, false>(m, cur, nxt, perm, ef, p, status, st); break;
+        case 1: launch_advance_v<NS, kKind, 128, 10, 1>(m, cur, nxt, perm, ef, p, status, tiles, st); break;
+        case 2: launch_advance_v<NS, kKind, 128, 8, 0>(m, cur, nxt, perm, ef, p, status, tiles, st); break;
+        case 3: launch_advance_v<NS, kKind, 256, 4, 1>(m, cur, nxt, perm, ef, p, status, tiles, st); break;
+        case 4: launch_advance_v<NS, kKind, 64, 18, 1>(m, cur, nxt, perm, ef, p, status, tiles, st); break;
+        case 5: launch_advance_v<NS, kKind, 128, 10, 2>(m, cur, nxt, perm, ef, p, status, tiles, st); break;
+        default: launch_advance_v<NS, kKind, 256, 4, 0>(m, cur, nxt, perm, ef, p, status, tiles, st); break;
     }
 }
 
@@ -1094,20 +1123,21 @@ cudaError_t run_pipeline(const DevMesh& m, const DevState& cur, const DevState& 
     if (n == 0) return cudaSuccess;
     const int E = m.n_tri;
     const int64_t nblk = (n + kBlk - 1) / kBlk;
-    cudaError_t e = cudaMemsetAsync(w.kwork, 0, sizeof(int) * 3 * (size_t)(E + 1), st);
+    cudaError_t e = cudaMemsetAsync(w.kwork, 0, sizeof(int) * (3 * (size_t)(E + 1) + 1), st);
     if (e != cudaSuccess) return e;
     int* kcnt = w.kwork;
     int* krc = w.kwork + (E + 1);
     int* kcur = w.kwork + 2 * (E + 1);
+    unsigned* tiles = reinterpret_cast<unsigned*>(w.kwork + 3 * (E + 1));
     if (ev) cudaEventRecord(ev[0], st);
     constexpr int NQ4 = (22 + NS + 3) / 4;
     element_fields_kernel<NS><<<nblocks((int64_t)E * NQ4, 256), 256, 0, st>>>(m, fields, w.efields);
     // the kernel with the least code that covers the mesh and the model: walls off the frame,
     // IECM or reactions (kind 2); several components (kind 1); the plain step (kind 0)
     if (m.edge_walls || p.beta || p.react_k > 0.0f)
-        launch_advance<NS, 2>(tune.adv, m, cur, nxt, w.perm, w.efields, p, status, st);
-    else if (m.n_comp > 1) launch_advance<NS, 1>(tune.adv, m, cur, nxt, w.perm, w.efields, p, status, st);
-    else launch_advance<NS, 0>(tune.adv, m, cur, nxt, w.perm, w.efields, p, status, st);
+        launch_advance<NS, 2>(tune.adv, m, cur, nxt, w.perm, w.efields, p, status, tiles, st);
+    else if (m.n_comp > 1) launch_advance<NS, 1>(tune.adv, m, cur, nxt, w.perm, w.efields, p, status, tiles, st);
+    else launch_advance<NS, 0>(tune.adv, m, cur, nxt, w.perm, w.efields, p, status, tiles, st);
     if (ev) cudaEventRecord(ev[1], st);
     histogram_kernel<<<(unsigned)((nblk + kHWarps - 1) / kHWarps), 32 * kHWarps, 0, st>>>(
         nxt.elem, n, w.rrank, w.rec_key, w.rec_cnt, w.nrec, kcnt, krc, status);

@@ -42,7 +42,7 @@ EXPORTS = ("lpdf_params_default", "lpdf_last_error", "lpdf_version", "lpdf_mesh_
            "lpdf_particles_init_multi", "lpdf_pdf_steps", "lpdf_ctx_set_tune", "lpdf_ctx_autotune",
            "lpdf_grid_flux_statistics", "lpdf_iecm_coefficients", "lpdf_ctx_set_iecm", "lpdf_mlp_request_check")
 
-N_ADV_VARIANTS, N_MOM_VARIANTS = 5, 4
+N_ADV_VARIANTS, N_MOM_VARIANTS = 6, 4
 
 MLP_IN, MLP_OUT, MLP_HIDDEN = 8, 7, 128
 MLP_NPARAMS = 35079
