@@ -133,3 +133,26 @@ def test_image_across_a_sloped_wall_is_wrapped_into_the_frame(torch_cuda):
     assert lost == 0
     assert g.x[0] == np.float32(res["x"][0]) and g.y[0] == np.float32(res["y"][0])
     assert g.elem[0] == oelem[0] == om.locate_brute(float(g.x[0]), float(g.y[0])) >= 0
+
+
+def test_hand_worked_moves_on_the_lshape(torch_cuda):
+    """The hand-worked moves of the L-shaped mesh, made by one GPU step with no diffusion and still
+    fields: the walk round the reentrant corner takes the interior exit (4 hops, no mirroring,
+    although the wall's barycentric coordinate is the more negative one in the second element),
+    and the two moves into the notch are mirrored across the wall they cross. Positions,
+    velocities and owners are exactly the hand-worked ones; the hop count is their sum."""
+    from tests.test_oracle_walls import LSHAPE_MOVES, lshape_mesh, lshape_state
+    torch = torch_cuda
+    mesh = lshape_mesh()
+    st = lshape_state()
+    params = lpdf.make_params(nu=1e-30, dt=0.5, ns=1, seed=31)
+    F = np.zeros((mesh.n_nodes, wl.n_fields_padded(1)), dtype=np.float32)
+    F[:, wl.F_OMEGA] = 1.0
+    ctx = lpdf.Context(lpdf.Mesh(mesh), params, 128)
+    g, _, rc, status = gc.gpu_step(ctx, torch.from_numpy(F).cuda(), st, 0)
+    assert rc == lpdf.LPDF_OK, status
+    k = gc.match_pids(np.arange(st.n), g.pid)
+    for row, (_, _, _, e1, (x1, y1), (u1, v1), _, _) in enumerate(LSHAPE_MOVES):
+        j = k[row]
+        assert (g.elem[j], g.x[j], g.y[j], g.u[j], g.v[j]) == (e1, x1, y1, u1, v1), row
+    assert status[3] == sum(m[6] for m in LSHAPE_MOVES)

@@ -250,3 +250,95 @@ def test_an_image_that_wraps_onto_x1_belongs_to_x0():
         r, x, y, u, v, w, hops, nref = om.locate_walk_reflect(s, px, py, 0.5, 0.25, 0.125)
         assert nref == 1 and x == 0.0 and f32(y) == want_y, (s, r, x, y, nref)
         assert r == owner and (u, v, w) == (-0.5, -0.25, -0.125)
+
+
+def lshape_mesh():
+    """A hand-built L-shaped domain, [0, 2] x [0, 1] joined to [0, 1] x [1, 2], with its reentrant
+    corner at (1, 1); every boundary edge is a wall. Nodes 0..7 are (0,0) (1,0) (2,0) (0,1) (1,1)
+    (2,1) (0,2) (1,2); elements, counter-clockwise (edge k runs from vertex k to vertex k + 1):
+    T0 = (0,1,4) and T1 = (0,4,3) in the lower-left square, T2 = (1,2,5) and T3 = (1,5,4) in the
+    lower-right one, T4 = (3,4,7) and T5 = (3,7,6) in the upper-left one. The walls at y = 1
+    (x in [1, 2]) and x = 1 (y in [1, 2]) are off the sides of the bounding box."""
+    xy = np.array([(0, 0), (1, 0), (2, 0), (0, 1), (1, 1), (2, 1), (0, 2), (1, 2)], dtype=np.float64)
+    tri = np.array([(0, 1, 4), (0, 4, 3), (1, 2, 5), (1, 5, 4), (3, 4, 7), (3, 7, 6)], dtype=np.int32)
+    count = {}
+    for t in tri:
+        for k in range(3):
+            key = tuple(sorted((int(t[k]), int(t[(k + 1) % 3]))))
+            count[key] = count.get(key, 0) + 1
+    tag = np.zeros((len(tri), 3), dtype=np.int32)
+    for e, t in enumerate(tri):
+        for k in range(3):
+            if count[tuple(sorted((int(t[k]), int(t[(k + 1) % 3]))))] == 1:
+                tag[e, k] = wl.EDGE_WALL
+    return wl.Mesh(xy, tri, tag, 0.0, (0.0, 2.0, 0.0, 2.0), "lshape", 0, 0)
+
+
+# Hand-worked moves on the L-shaped mesh, all in exact binary fractions. Each row: start element,
+# start (x, y), velocity (u, v), and after a move of dt = 0.5 the owner, the final (x, y) and
+# (u, v), the hops and the mirrorings.
+#  * From T2 to (0.8125, 1.3125), round the reentrant corner. In T2 only lambda_1 (of node 2,
+#    across the diagonal) is negative: -1.5 -> T3. In T3 (nodes 1, 5, 4) lambda_0 = 1 - y =
+#    -0.3125 lies across the wall y = 1 and lambda_1 = x - 1 = -0.1875 across the interior edge
+#    x = 1: the walk takes the interior exit although the wall's lambda is the more negative one
+#    -> T0, where lambda_1 = x - y = -0.5 -> T1, where lambda_0 = 1 - y = -0.3125 -> T4, where
+#    lambda = (1 - x, x + 1 - y, y - 1) = (0.1875, 0.5, 0.3125): found after 4 hops, no mirroring.
+#    A walk that always left by the most negative lambda would have mirrored at y = 1 and ended
+#    in T0 at (0.8125, 0.6875).
+#  * From T3 into the notch at (1.5, 1.25): in T3 only the wall's lambda_0 = -0.25 is negative, so
+#    the position is mirrored across y = 1 to (1.5, 0.75) and the velocity reversed; T3 owns it.
+#  * From T4 into the notch at (1.25, 1.5): only the wall x = 1 is crossed: mirrored to
+#    (0.75, 1.5), velocity reversed, owned by T4.
+LSHAPE_MOVES = [
+    (2, (1.8125, 0.5), (-2.0, 1.625), 4, (0.8125, 1.3125), (-2.0, 1.625), 4, 0),
+    (3, (1.25, 0.75), (0.5, 1.0), 3, (1.5, 0.75), (-0.5, -1.0), 0, 1),
+    (4, (0.75, 1.5), (1.0, 0.0), 4, (0.75, 1.5), (-1.0, 0.0), 0, 1),
+]
+
+
+def lshape_state():
+    """The start states of the hand-worked moves (pid = row)."""
+    n = len(LSHAPE_MOVES)
+    return wl.State(np.array([m[1][0] for m in LSHAPE_MOVES], np.float32),
+                    np.array([m[1][1] for m in LSHAPE_MOVES], np.float32),
+                    np.array([m[2][0] for m in LSHAPE_MOVES], np.float32),
+                    np.array([m[2][1] for m in LSHAPE_MOVES], np.float32),
+                    np.zeros(n, np.float32), np.ones(n, np.float32), np.zeros((1, n), np.float32),
+                    np.array([m[0] for m in LSHAPE_MOVES], np.int32), np.arange(n, dtype=np.uint32))
+
+
+def test_lshape_mesh_is_as_drawn():
+    mesh = lshape_mesh()
+    om = oracle.OracleMesh(mesh)
+    assert om.edge_walls
+    nbr = om.neighbors()
+    assert sorted(n for n in nbr[3] if n >= 0) == [0, 2]          # T3: the diagonal and x = 1
+    assert sorted(n for n in nbr[1] if n >= 0) == [0, 4]          # T1: the diagonal and y = 1
+    for e, (x, y), *_ in LSHAPE_MOVES:
+        assert om.locate_brute(x, y) == e
+
+
+@pytest.mark.parametrize("row", range(len(LSHAPE_MOVES)))
+def test_hand_worked_walks_on_the_lshape(row):
+    """The walk with mirroring reproduces the hand-worked moves: the owner, the position, the
+    velocity, the hops and the mirrorings."""
+    om = oracle.OracleMesh(lshape_mesh())
+    e0, (x, y), (u, v), e1, (x1, y1), (u1, v1), hops, mirrors = LSHAPE_MOVES[row]
+    qx, qy = x + 0.5 * u, y + 0.5 * v
+    e, px, py, U, V, W, h, n = om.locate_walk_reflect(e0, qx, qy, u, v, 0.0)
+    assert (e, px, py, U, V, h, n) == (e1, x1, y1, u1, v1, hops, mirrors)
+    assert om.locate_brute(px, py) == e1
+
+
+def test_hand_worked_moves_through_a_step_on_the_lshape():
+    """The same moves made by one oracle step with no diffusion and still fields (U, positions
+    and the walk are then exact): every particle ends at its hand-worked owner and state."""
+    mesh = lshape_mesh()
+    om = oracle.OracleMesh(mesh)
+    st = lshape_state()
+    p = oracle.make_params(nu=1e-30, dt=0.5, seed=31, ns=1)
+    res, oelem, aux, lost = oracle.pdf_step(om, p, _still_fields(mesh, 1), st, 0, locate_mode=2)
+    assert lost == 0
+    for k, (_, _, _, e1, (x1, y1), (u1, v1), _, mirrors) in enumerate(LSHAPE_MOVES):
+        assert (oelem[k], res["x"][k], res["y"][k], res["u"][k], res["v"][k]) == (e1, x1, y1, u1, v1)
+        assert aux[k, 2] == mirrors
