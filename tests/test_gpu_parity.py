@@ -87,6 +87,30 @@ def test_ragged_and_tiny_ensembles(torch_cuda, ms):
         gc.compare_moments(om, g, S, wk.ns, BOUND[ms])
 
 
+@pytest.mark.parametrize("adv", range(lpdf.N_ADV_VARIANTS))
+def test_every_advance_variant_on_ragged_ensembles(torch_cuda, adv):
+    """Each advance-kernel launch variant (one CTA per tile, persistent strides, the chunk queue)
+    on sizes around its 64-particle chunks, 64- to 256-particle tiles and persistent grids: the
+    oracle's step, and the same bits as variant 0."""
+    wk = wl.channel_small()
+    mesh, gm, om, params, F, Fd, ctx, npe = _setup(wk, n_per_elem=10)
+    full = wl.synthetic_state(mesh, 10, wk.ns, seed=19)
+    for n in (1, 63, 64, 65, 129, 257, 5003):
+        sel = np.sort(np.random.default_rng(n + 7).choice(full.n, size=n, replace=False))
+        st = wl.State(*(np.ascontiguousarray(getattr(full, k)[sel]) for k in gc.FIELDS),
+                      np.ascontiguousarray(full.psi[:, sel]), full.elem[sel], full.pid[sel])
+        out = []
+        for v in (0, adv):
+            ctx.set_tune(v, 0)
+            g, S, rc, status = gc.gpu_step(ctx, Fd, st, 2)
+            assert rc == lpdf.LPDF_OK, status
+            out.append((g, S))
+        for k in gc.FIELDS + ("elem", "pid"):
+            assert np.array_equal(getattr(out[0][0], k), getattr(out[1][0], k)), (n, k)
+        assert np.array_equal(out[0][0].psi, out[1][0].psi) and np.array_equal(out[0][1], out[1][1]), n
+        gc.compare_step(mesh, om, params, F, st, 2, out[1][0])
+
+
 def test_empty_ensemble(torch_cuda):
     import torch
     wk = wl.channel_small()
