@@ -166,11 +166,46 @@ def compare_step(mesh: wl.Mesh, om: oracle.OracleMesh, params: lpdf.Params, F, s
 #   over at most 8 particles of a lane and 5 levels of the warp reduction (the fused kernel: units
 #   of at most 6 particles, column sums of at most 32 units): 48 eps32.
 MOMENT_RTOL = {"compensated": 1e-9, "fp32": 48 * EPS32}
+LAMBDA_RTOL = 8 * EPS32   # FP32 barycentric weights: per unit of kappa (lambda_rounding_sums)
 
 
-def moment_tolerance(S_o, Sabs, bound: str = "fp32"):
+def lambda_rounding_sums(om: oracle.OracleMesh, g: wl.State, ns: int):
+    """Per node and quantity, sum over the particles of kappa_n(p) |q_k(p)|, where
+    kappa_n = (|dx_b dy_c| + |dy_b dx_c|) / |2A| with (dx_v, dy_v) = vertex v - the particle, b and c
+    the element's other two vertices. The FP32 moments kernel forms lambda_n as the determinant of
+    those four FP32 differences (each rounded once) times the rounded 1/2A, so its absolute error is
+    at most about 2 eps32 kappa_n + 2 eps32 |lambda_n|: for a particle far from node n on a long thin
+    element kappa_n is of the order of the aspect ratio while lambda_n is near 0, and a bound
+    relative to |lambda_n q| alone does not cover it. Folded onto master nodes like the sums."""
+    xy, tri = om.node_xy, om.tri[g.elem]
+    X, Y = xy[tri, 0], xy[tri, 1]                      # (n, 3) vertex coordinates, exact
+    dx = X - g.x.astype(np.float64)[:, None]
+    dy = Y - g.y.astype(np.float64)[:, None]
+    A2 = np.abs((X[:, 1] - X[:, 0]) * (Y[:, 2] - Y[:, 0]) - (Y[:, 1] - Y[:, 0]) * (X[:, 2] - X[:, 0]))
+    kappa = np.empty_like(X)
+    for a in range(3):
+        b, c = (a + 1) % 3, (a + 2) % 3
+        kappa[:, a] = (np.abs(dx[:, b] * dy[:, c]) + np.abs(dy[:, b] * dx[:, c])) / A2
+    u, v, w = (getattr(g, k).astype(np.float64) for k in ("u", "v", "w"))
+    psi = np.asarray(g.psi, dtype=np.float64).reshape(ns, g.n)
+    q = np.stack([np.ones(g.n), u, v, w, u * u, u * v, u * w, v * v, v * w, w * w, g.omega.astype(np.float64)]
+                 + [psi[a] for a in range(ns)] + [psi[a] ** 2 for a in range(ns)], axis=1)
+    masters = om.masters()
+    K = np.zeros((om.n_nodes, q.shape[1]))
+    for a in range(3):
+        np.add.at(K, masters[tri[:, a]], kappa[:, a:a + 1] * np.abs(q))
+    return K[masters]
+
+
+def moment_tolerance(S_o, Sabs, bound: str = "fp32", K=None):
+    """The bound of the kernel that formed the sums: MOMENT_RTOL of sum |lambda q|, with FP32 partial
+    sums also LAMBDA_RTOL of sum kappa |q| (K, lambda_rounding_sums), plus 2^-33 per fixed-point
+    conversion (at most 8 per unit of particle weight)."""
     count = np.maximum(S_o[:, :1], 1.0) * 8.0
-    return MOMENT_RTOL[bound] * Sabs + count * 2.0 ** -33
+    tol = MOMENT_RTOL[bound] * Sabs + count * 2.0 ** -33
+    if bound == "fp32" and K is not None:
+        tol = tol + LAMBDA_RTOL * K
+    return tol
 
 
 def compare_moments(om: oracle.OracleMesh, g: wl.State, S_gpu, ns: int, bound: str = "fp32"):
@@ -178,7 +213,7 @@ def compare_moments(om: oracle.OracleMesh, g: wl.State, S_gpu, ns: int, bound: s
     bound of the kernel that formed them (MOMENT_RTOL). Returns (max error / sum|lambda q|, S_oracle)."""
     f = lambda a: a.astype(np.float64)
     S_o, Sabs = oracle.moments(om, ns, f(g.x), f(g.y), f(g.u), f(g.v), f(g.w), f(g.omega), f(g.psi), g.elem)
-    tol = moment_tolerance(S_o, Sabs, bound)
+    tol = moment_tolerance(S_o, Sabs, bound, lambda_rounding_sums(om, g, ns) if bound == "fp32" else None)
     err = np.abs(S_gpu - S_o)
     ratio = float(np.max(err / np.maximum(Sabs, 1e-300)))
     assert np.all(err <= tol), (np.argwhere(err > tol)[:5], err[err > tol][:5], tol[err > tol][:5])

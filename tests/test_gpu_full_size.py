@@ -85,7 +85,7 @@ def test_full_size_sampled_parity(torch_cuda, name):
     f = lambda a: a.astype(np.float64)
     So, Sabs = oracle.moments(om, wk.ns, f(sub.x), f(sub.y), f(sub.u), f(sub.v), f(sub.w), f(sub.omega),
                               f(sub.psi), sub.elem)
-    tol = gc.moment_tolerance(So[nodes], Sabs[nodes])
+    tol = gc.moment_tolerance(So[nodes], Sabs[nodes], "fp32", gc.lambda_rounding_sums(om, sub, wk.ns)[nodes])
     err = np.abs(S[nodes] - So[nodes])
     assert np.all(err <= tol), (nodes[np.argwhere(err > tol)[:5, 0]], err[err > tol][:5], tol[err > tol][:5])
 
