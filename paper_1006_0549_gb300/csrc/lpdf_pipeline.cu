@@ -18,9 +18,10 @@
 //       record's offset = bucket start + the counts of the element's records in earlier blocks.
 //   S4  particle_scatter_kernel: perm_new[offset(record) + rank] = i. perm_new lists the next
 //       buffer in (new element, position) order: a stable counting sort, fully deterministic.
-//   K2  moments_kernel (a warp per element): the element's particles, gathered through perm_new
-//       in canonical order, a fixed reduce-scatter across the lanes (recursive halving), one
-//       64-bit fixed-point atomic add per node and quantity. Two precisions (lpdf_params
+//   K2  moments_kernel (a warp per element; with at most kHalfPpe particles per element on
+//       average, FP32 sums, a half-warp per element): the element's particles, gathered through
+//       perm_new in canonical order, a fixed reduce-scatter across the lanes (recursive halving),
+//       one 64-bit fixed-point atomic add per node and quantity. Two precisions (lpdf_params
 //       moment_sums): 0, lambda_a' q_k in FP32 summed in FP32 per lane over at most kLaneChunk
 //       particles; 1, per lane the sums of q, dx q and dy q ((dx, dy) from vertex 0) in
 //       compensated FP32 (double-floats), combined in FP64 with the element's FP64 affine
@@ -39,6 +40,7 @@ namespace {
 constexpr int kBlk = 256;          // H: positions per record block
 constexpr int kLaneChunk = 8;      // K2: particles a lane sums before the warp reduction
 constexpr int kLaneChunkDf = 16;   // the same with compensated sums (its warp reduction costs more)
+constexpr int kHalfPpe = 160;      // K2: at most this many particles per element on average -> half-warps
 constexpr int kScanItems = 4;      // scan: items per thread
 constexpr int kScanThreads = 1024;
 constexpr int kScanTile = kScanItems * kScanThreads;
@@ -1027,6 +1029,159 @@ __global__ void __launch_bounds__(MBLK, MMINB) moments_kernel_f32(const __grid_c
     if (lane == 0 && e_or) atomicOr(&status[0], (unsigned long long)e_or);
 }
 
+// Half-warp column sums: lanes 0-15 and lanes 16-31 of a warp hold two different elements'
+// columns (NK <= 64) and reduce them by recursive halving with offsets 8, 4, 2, 1, which never
+// cross the halves; lane j of a half ends with columns j, j + 16, j + 32 and j + 48 (zero past NK).
+// The order of the additions is fixed.
+template <int NK>
+__device__ __forceinline__ void half_reduce_scatter(const float (&acc)[NK], int lane, float (&col)[4])
+{
+    static_assert(NK >= 1 && NK <= 64, "at most four columns per lane");
+    constexpr int A0 = cmin(NK, 16), B0 = NK > 16 ? cmin(NK - 16, 16) : 0;
+    constexpr int C0 = NK > 32 ? cmin(NK - 32, 16) : 0, D0 = NK > 48 ? NK - 48 : 0;
+    float a[32], b[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        a[i] = i < A0 ? acc[i] : 0.0f;
+        b[i] = i < B0 ? acc[cmin(16 + i, NK - 1)] : 0.0f;
+    }
+    halve<8, A0, B0>(a, b, (lane & 8) != 0);
+    halve<4, cmin(A0, 8), cmin(B0, 8)>(a, b, (lane & 4) != 0);
+    halve<2, cmin(A0, 4), cmin(B0, 4)>(a, b, (lane & 2) != 0);
+    halve<1, cmin(A0, 2), cmin(B0, 2)>(a, b, (lane & 1) != 0);
+    col[0] = a[0];
+    col[1] = B0 > 0 ? b[0] : 0.0f;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        a[i] = i < C0 ? acc[cmin(32 + i, NK - 1)] : 0.0f;
+        b[i] = i < D0 ? acc[cmin(48 + i, NK - 1)] : 0.0f;
+    }
+    halve<8, C0, D0>(a, b, (lane & 8) != 0);
+    halve<4, cmin(C0, 8), cmin(D0, 8)>(a, b, (lane & 4) != 0);
+    halve<2, cmin(C0, 4), cmin(D0, 4)>(a, b, (lane & 2) != 0);
+    halve<1, cmin(C0, 2), cmin(D0, 2)>(a, b, (lane & 1) != 0);
+    col[2] = C0 > 0 ? a[0] : 0.0f;
+    col[3] = D0 > 0 ? b[0] : 0.0f;
+}
+
+// K2 for sparsely populated elements (FP32 partial sums): a half-warp per element, so that a warp
+// keeps two elements' chains of dependent loads (bucket bounds, gather indices, state) in flight
+// instead of one. Otherwise as moments_kernel_f32: at most kLaneChunk particles per lane and chunk
+// in position order, the fixed reduction, one fixed-point atomic per node and quantity. Both
+// halves run the same number of chunks (an empty or missing element contributes nothing) because
+// the reduction's shuffles span the warp.
+template <int NS, int MBLK, int MMINB>
+__global__ void __launch_bounds__(MBLK, MMINB) moments_kernel_f32h(const __grid_constant__ DevMesh M,
+                                                       const __grid_constant__ DevState S,
+                                                       const int* __restrict__ perm, const int* __restrict__ kstart,
+                                                       unsigned long long* __restrict__ node_acc,
+                                                       unsigned long long* __restrict__ status)
+{
+    constexpr int NQ = 11 + 2 * NS, NK = 3 * NQ;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (((t >> 5) << 1) >= M.n_tri) return;   // the warp's first element is past the end (warp-uniform)
+    const int e = (int)(t >> 4);
+    const int lane = threadIdx.x & 15;
+    const bool valid = e < M.n_tri;
+    int p0 = 0, p1 = 0;
+    if (valid) {
+        p0 = kstart[e];
+        p1 = kstart[e + 1];
+    }
+    constexpr int LC = kLaneChunk;
+    const int mine = (p1 - p0 + 16 * LC - 1) / (16 * LC);
+    const int nchunk = max(mine, __shfl_xor_sync(kFull, mine, 16));
+    if (nchunk == 0) return;                   // both elements empty (warp-uniform)
+    float4 X = make_float4(0.f, 0.f, 0.f, 0.f), Y = X;
+    int4 mv = make_int4(0, 0, 0, 0);
+    if (valid && p1 > p0) {
+        X = __ldg(&M.ex[e]);
+        Y = __ldg(&M.ey[e]);
+        mv = __ldg(&M.em[e]);
+    }
+    unsigned err = 0;
+#pragma unroll 1
+    for (int ci = 0; ci < nchunk; ++ci) {
+        const int base = p0 + ci * 16 * LC;
+        const int end = min(p1, base + 16 * LC);
+        float acc[NK];
+#pragma unroll
+        for (int k = 0; k < NK; ++k) acc[k] = 0.0f;
+        constexpr int MB = NS <= 2 ? 4 : 2, NB = NS == 1 ? 2 : 1;
+        static_assert(LC % MB == 0, "whole batches per chunk");
+        int idx[LC];
+#pragma unroll
+        for (int k = 0; k < LC; ++k) {
+            const int pos = base + lane + 16 * k;
+            idx[k] = pos < end ? perm[pos] : -1;
+        }
+        float bx[NB][MB], by[NB][MB], bu[NB][MB], bv[NB][MB], bw[NB][MB], bo[NB][MB], bp[NB][MB][NS];
+        auto gather = [&](int buf, int k0) {
+#pragma unroll
+            for (int k = 0; k < MB; ++k) {
+                const int j = idx[k0 + k] >= 0 ? idx[k0 + k] : 0;
+                bx[buf][k] = S.x[j];
+                by[buf][k] = S.y[j];
+                bu[buf][k] = S.u[j];
+                bv[buf][k] = S.v[j];
+                bw[buf][k] = S.w[j];
+                bo[buf][k] = S.om[j];
+#pragma unroll
+                for (int a = 0; a < NS; ++a) bp[buf][k][a] = S.psi[(size_t)a * S.cap + j];
+            }
+        };
+        if (base < end) {
+            if constexpr (NB == 2) gather(0, 0);
+#pragma unroll
+            for (int k0 = 0; k0 < LC; k0 += MB) {
+                if (base + 16 * k0 >= end) break;
+                const int cb = NB == 2 ? (k0 / MB) & 1 : 0;
+                if constexpr (NB == 2) {
+                    if (k0 + MB < LC && base + 16 * (k0 + MB) < end) gather(cb ^ 1, k0 + MB);
+                } else {
+                    gather(0, k0);
+                }
+#pragma unroll
+                for (int k = 0; k < MB; ++k) {
+                    if (idx[k0 + k] < 0) break;
+                    float q[NQ];
+                    const float u = bu[cb][k], v = bv[cb][k], w = bw[cb][k];
+                    q[0] = 1.0f; q[1] = u; q[2] = v; q[3] = w;
+                    q[4] = u * u; q[5] = u * v; q[6] = u * w; q[7] = v * v; q[8] = v * w; q[9] = w * w;
+                    q[10] = bo[cb][k];
+#pragma unroll
+                    for (int a = 0; a < NS; ++a) {
+                        q[11 + a] = bp[cb][k][a];
+                        q[11 + NS + a] = bp[cb][k][a] * bp[cb][k][a];
+                    }
+                    float l0, l1, l2;
+                    barycentric(X, Y, bx[cb][k], by[cb][k], l0, l1, l2);
+#pragma unroll
+                    for (int kq = 0; kq < NQ; ++kq) {
+                        acc[kq] = fmaf(l0, q[kq], acc[kq]);
+                        acc[NQ + kq] = fmaf(l1, q[kq], acc[NQ + kq]);
+                        acc[2 * NQ + kq] = fmaf(l2, q[kq], acc[2 * NQ + kq]);
+                    }
+                }
+            }
+        }
+        float col[4];
+        half_reduce_scatter<NK>(acc, lane, col);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const int c_ = lane + 16 * kk;
+            if (c_ < NK && base < end) {
+                const int c = c_ / NQ, qq = c_ - c * NQ;
+                const int node = c == 0 ? mv.x : (c == 1 ? mv.y : mv.z);
+                const long long val = to_fixed(col[kk], err);
+                if (val != 0) atomicAdd(&node_acc[(size_t)node * NQ + qq], (unsigned long long)val);
+            }
+        }
+    }
+    const unsigned e_or = __reduce_or_sync(kFull, err);
+    if ((threadIdx.x & 31) == 0 && e_or) atomicOr(&status[0], (unsigned long long)e_or);
+}
+
 __global__ void iota_kernel(int* __restrict__ p, int64_t n)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1103,6 +1258,18 @@ void launch_moments(int v, int mode, const DevMesh& m, const DevState& s, const 
             case 2: moments_kernel_df<NS, 512, 1><<<nblocks(threads, 512), 512, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
             case 3: moments_kernel_df<NS, 256, 1><<<nblocks(threads, 256), 256, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
             default: moments_kernel_df<NS, 256, 2><<<nblocks(threads, 256), 256, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
+        }
+        return;
+    }
+    // sparsely populated elements (at most kHalfPpe particles per element on average): a half-warp
+    // per element. The rule depends on the ensemble only, so every launch variant gives the same bits.
+    if (s.n <= (int64_t)kHalfPpe * m.n_tri) {
+        const int64_t ht = ((int64_t)m.n_tri + 1) / 2 * 32;
+        switch (v) {
+            case 1: moments_kernel_f32h<NS, 128, 4><<<nblocks(ht, 128), 128, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
+            case 2: moments_kernel_f32h<NS, 512, 1><<<nblocks(ht, 512), 512, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
+            case 3: moments_kernel_f32h<NS, 256, 3><<<nblocks(ht, 256), 256, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
+            default: moments_kernel_f32h<NS, 256, 2><<<nblocks(ht, 256), 256, 0, st>>>(m, s, perm, kstart, node_acc, status); break;
         }
         return;
     }

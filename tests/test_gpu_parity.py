@@ -87,12 +87,14 @@ def test_ragged_and_tiny_ensembles(torch_cuda, ms):
         gc.compare_moments(om, g, S, wk.ns, BOUND[ms])
 
 
-@pytest.mark.parametrize("adv", range(lpdf.N_ADV_VARIANTS))
-def test_every_advance_variant_on_ragged_ensembles(torch_cuda, adv):
+@pytest.mark.parametrize("workload,adv,mom", [("channel", a, 0) for a in range(lpdf.N_ADV_VARIANTS)] +
+                         [(w, 0, m) for w in ("channel", "cavity") for m in range(1, lpdf.N_MOM_VARIANTS)])
+def test_every_launch_variant_on_ragged_ensembles(torch_cuda, workload, adv, mom):
     """Each advance-kernel launch variant (one CTA per tile, persistent strides, the chunk queue)
-    on sizes around its 64-particle chunks, 64- to 256-particle tiles and persistent grids: the
-    oracle's step, and the same bits as variant 0."""
-    wk = wl.channel_small()
+    and each moments-kernel variant on sizes around the 64-particle chunks, 64- to 256-particle
+    tiles and persistent grids, at up to 10 particles per element (the moments kernel's half-warp
+    form): the oracle's step and moment sums, and the same bits as variant (0, 0)."""
+    wk = wl.channel_small() if workload == "channel" else wl.cavity_small()
     mesh, gm, om, params, F, Fd, ctx, npe = _setup(wk, n_per_elem=10)
     full = wl.synthetic_state(mesh, 10, wk.ns, seed=19)
     for n in (1, 63, 64, 65, 129, 257, 5003):
@@ -100,8 +102,8 @@ def test_every_advance_variant_on_ragged_ensembles(torch_cuda, adv):
         st = wl.State(*(np.ascontiguousarray(getattr(full, k)[sel]) for k in gc.FIELDS),
                       np.ascontiguousarray(full.psi[:, sel]), full.elem[sel], full.pid[sel])
         out = []
-        for v in (0, adv):
-            ctx.set_tune(v, 0)
+        for v in ((0, 0), (adv, mom)):
+            ctx.set_tune(*v)
             g, S, rc, status = gc.gpu_step(ctx, Fd, st, 2)
             assert rc == lpdf.LPDF_OK, status
             out.append((g, S))
@@ -109,6 +111,21 @@ def test_every_advance_variant_on_ragged_ensembles(torch_cuda, adv):
             assert np.array_equal(getattr(out[0][0], k), getattr(out[1][0], k)), (n, k)
         assert np.array_equal(out[0][0].psi, out[1][0].psi) and np.array_equal(out[0][1], out[1][1]), n
         gc.compare_step(mesh, om, params, F, st, 2, out[1][0])
+        gc.compare_moments(om, out[1][0], out[1][1], wk.ns)
+
+
+@pytest.mark.parametrize("npe", [160, 161, 300])
+def test_moments_on_both_sides_of_the_half_warp_threshold(torch_cuda, npe):
+    """The moments kernel takes a half-warp per element when the ensemble averages at most 160
+    particles per element, a warp otherwise: both forms against the oracle's FP64 reduction of the
+    GPU's new state, within the FP32 partial-sum bound."""
+    wk = wl.channel_small()
+    mesh, gm, om, params, F, Fd, ctx, _ = _setup(wk, n_per_elem=npe)
+    st = wl.synthetic_state(mesh, npe, wk.ns, seed=23)
+    g, S, rc, status = gc.gpu_step(ctx, Fd, st, 4)
+    assert rc == lpdf.LPDF_OK, status
+    ratio, _ = gc.compare_moments(om, g, S, wk.ns)
+    print(npe, "moment error / sum|lambda q| max =", ratio)
 
 
 def test_empty_ensemble(torch_cuda):
