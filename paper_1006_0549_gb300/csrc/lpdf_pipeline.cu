@@ -40,7 +40,7 @@ namespace {
 constexpr int kBlk = 256;          // H: positions per record block
 constexpr int kLaneChunk = 8;      // K2: particles a lane sums before the warp reduction
 constexpr int kLaneChunkDf = 16;   // the same with compensated sums (its warp reduction costs more)
-constexpr int kHalfPpe = 160;      // K2: at most this many particles per element on average -> half-warps
+constexpr int kHalfPpe = 384;      // K2: at most this many particles per element on average -> half-warps
 constexpr int kScanItems = 4;      // scan: items per thread
 constexpr int kScanThreads = 1024;
 constexpr int kScanTile = kScanItems * kScanThreads;

@@ -114,9 +114,9 @@ def test_every_launch_variant_on_ragged_ensembles(torch_cuda, workload, adv, mom
         gc.compare_moments(om, out[1][0], out[1][1], wk.ns)
 
 
-@pytest.mark.parametrize("npe", [160, 161, 300])
+@pytest.mark.parametrize("npe", [200, 384, 385, 500])
 def test_moments_on_both_sides_of_the_half_warp_threshold(torch_cuda, npe):
-    """The moments kernel takes a half-warp per element when the ensemble averages at most 160
+    """The moments kernel takes a half-warp per element when the ensemble averages at most 384
     particles per element, a warp otherwise: both forms against the oracle's FP64 reduction of the
     GPU's new state, within the FP32 partial-sum bound."""
     wk = wl.channel_small()
