@@ -92,13 +92,17 @@ typedef struct {
     double react_k;
     /* precision of the gridpoint moment sums of lpdf_pdf_step (the statistics at gridpoints,
      * Introduction item i): 0, each term lambda_a q_k formed in FP32 and summed in FP32 over at
-     * most 8 particles of a lane and the 32 lanes of a warp before the exact 64-bit fixed-point
-     * accumulation (error at most 48 eps32 sum |lambda_a q_k|); 1, compensated: the sums of q,
+     * most 8 particles of a lane and the 32 lanes of a warp (16 lanes, a half-warp per element,
+     * when the ensemble averages at most 384 particles per element) before the exact 64-bit
+     * fixed-point accumulation (error at most 48 eps32 sum |lambda_a q_k| + 8 eps32 sum kappa_a
+     * |q_k|: the FP32 weight lambda_a, a determinant of rounded coordinate differences, is off by
+     * about 2 eps32 kappa_a with kappa_a = (|dx_b dy_c| + |dy_b dx_c|) / |2A| from the particle to
+     * the other two vertices, of the order of the element's aspect ratio); 1, compensated: the sums of q,
      * dx q and dy q over an element's particles ((dx, dy) from its first vertex, formed exactly)
      * in double-float FP32 arithmetic (error-free products and additions), combined with the
      * element's FP64 barycentric coefficients in FP64 (error at most 1e-9 sum |lambda_a q_k|,
-     * about 1e-13 in practice). Other values: LPDF_ERR_ARG. lpdf_pdf_step_static supports 0 only
-     * (LPDF_ERR_UNSUPPORTED). */
+     * about 1e-13 in practice). Both add 2^-33 per fixed-point conversion. Other values:
+     * LPDF_ERR_ARG. lpdf_pdf_step_static supports 0 only (LPDF_ERR_UNSUPPORTED). */
     int32_t moment_sums;
 } lpdf_params;
 
