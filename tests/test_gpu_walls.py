@@ -156,3 +156,29 @@ def test_hand_worked_moves_on_the_lshape(torch_cuda):
         j = k[row]
         assert (g.elem[j], g.x[j], g.y[j], g.u[j], g.v[j]) == (e1, x1, y1, u1, v1), row
     assert status[3] == sum(m[6] for m in LSHAPE_MOVES)
+
+
+def _three_triangle_mesh():
+    """The triangle (0,0), (2,0), (0,2) split at the interior point (0.5, 0.5) into three elements;
+    every boundary edge is a wall (the hypotenuse is off the sides of the bounding box). An odd
+    number of elements: the moments kernel's last warp has an element in one half only."""
+    xy = np.array([(0, 0), (2, 0), (0, 2), (0.5, 0.5)], dtype=np.float64)
+    tri = np.array([(0, 1, 3), (1, 2, 3), (2, 0, 3)], dtype=np.int32)
+    tag = np.zeros((3, 3), dtype=np.int32)
+    tag[:, 0] = wl.EDGE_WALL                          # edge 0 of each element is a boundary edge
+    return wl.Mesh(xy, tri, tag, 0.0, (0.0, 2.0, 0.0, 2.0), "tri3", 0, 0)
+
+
+def test_three_element_mesh_step_and_moments(torch_cuda):
+    torch = torch_cuda
+    mesh = _three_triangle_mesh()
+    om = oracle.OracleMesh(mesh)
+    assert om.edge_walls
+    params = lpdf.make_params(nu=1e-4, ns=2, seed=8)
+    st = wl.synthetic_state(mesh, 40, 2, seed=9)
+    F = wl.synthetic_node_fields(mesh, 2, seed=10)
+    ctx = lpdf.Context(lpdf.Mesh(mesh), params, st.n + 64)
+    g, S, rc, status = gc.gpu_step(ctx, torch.from_numpy(F).cuda(), st, 1)
+    assert rc == lpdf.LPDF_OK, status
+    gc.compare_step(mesh, om, params, F, st, 1, g)
+    gc.compare_moments(om, g, S, 2)
