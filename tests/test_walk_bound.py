@@ -73,12 +73,12 @@ def test_fast_walk_decisions_are_certified():
                     py = np.nextafter(py, np.float32(rng.choice([-1e9, 1e9])), dtype=np.float32)
                 signs = exact_signs(xy, px, py)
                 for fma in (False, True):
-                    verdict, a = fast(coef, px, py, fma)
+                    decision, a = fast(coef, px, py, fma)
                     checked += 1
-                    if verdict == "in":
+                    if decision == "in":
                         decided += 1
                         assert min(signs) > 0, (e, px, py, signs)
-                    elif verdict == "out":
+                    elif decision == "out":
                         decided += 1
                         assert signs[a] < 0, (e, px, py, signs, a)
             # and clearly interior points are decided
