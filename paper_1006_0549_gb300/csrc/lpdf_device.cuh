@@ -223,7 +223,10 @@ static __device__ __noinline__ int image_exit(const DevMesh& M, int e, float px,
 // (with edge walls a point on a wall edge is inside: those walls are closed). In a
 // periodic image frame the test only navigates. Out of line: the step calls it only when the
 // certified fast test is undecided, and its registers stay out of the step's hot loop.
-static __device__ __noinline__ bool walk_test(const DevMesh& M, int e, float px, float py, float lam[3], int& next)
+// the decision of walk_test: kWalkIn when (px, py) is in e (then lam, when given, receives the
+// barycentric weights), else the exit as walk_test's `next`
+constexpr int kWalkIn = 0x7fffffff;
+__device__ __forceinline__ int walk_decide(const DevMesh& M, int e, float px, float py, float* lam)
 {
     const float4 X = __ldg(&M.ex[e]);
     const float4 Y = __ldg(&M.ey[e]);
@@ -260,25 +263,43 @@ static __device__ __noinline__ bool walk_test(const DevMesh& M, int e, float px,
         }
         if (all_in) {
             // edge k = (v_k, v_k+1) is opposite vertex k+2: lambda_{k+2} = orient_k / (2 area)
-            lam[2] = vv[0] * Y.w;
-            lam[0] = vv[1] * Y.w;
-            lam[1] = vv[2] * Y.w;
-            return true;
+            if (lam) {
+                lam[2] = vv[0] * Y.w;
+                lam[0] = vv[1] * Y.w;
+                lam[1] = vv[2] * Y.w;
+            }
+            return kWalkIn;
         }
     } else {
         best = image_exit(M, e, px, py, sh);
     }
-    next = best == 0 ? N.x : (best == 1 ? N.y : N.z);
-    if (next < 0) next = -1 - best;   // a wall: -1 - (the exit edge)
+    const int next = best == 0 ? N.x : (best == 1 ? N.y : N.z);
+    return next < 0 ? -1 - best : next;   // a wall: -1 - (the exit edge)
+}
+
+static __device__ __noinline__ bool walk_test(const DevMesh& M, int e, float px, float py, float lam[3], int& next)
+{
+    const int c = walk_decide(M, e, px, py, lam);
+    if (c == kWalkIn) return true;
+    next = c;
     return false;
 }
 
+// walk_test without the weights, returning its decision (kWalkIn or the exit): the caller's
+// variables never have their address taken, so they stay in registers
+static __device__ __noinline__ int walk_test_code(const DevMesh& M, int e, float px, float py)
+{
+    return walk_decide(M, e, px, py, nullptr);
+}
+
 // The most negative lambda (vertex a) of the fast walk test lies across a wall: leave through the
-// most negative interior edge that is certainly crossed instead; the wall (next = -1 - its edge)
-// only when no interior edge can be crossed; -1 (undecided) when an interior edge is within its
-// rounding bound. Out of line: the step reaches it only at walls.
+// most negative interior edge that is certainly crossed instead; the wall (-1 - its edge) only
+// when no interior edge can be crossed; kWalkUndecided when an interior edge is within its
+// rounding bound. Returns the exit (the walk's `next`) or kWalkUndecided. Out of line: the step
+// reaches it only at walls.
+constexpr int kWalkUndecided = -0x7fffffff - 1;
 static __device__ __noinline__ int fast_wall_exit(float l0, float l1, float l2, float E0, float E1, float E2, int4 N,
-                                                  int a, int& next)
+                                                  int a)
 {
     const float lv[3] = {l0, l1, l2}, ev[3] = {E0, E1, E2};
     const int nv[3] = {N.y, N.z, N.x};
@@ -288,15 +309,11 @@ static __device__ __noinline__ int fast_wall_exit(float l0, float l1, float l2, 
         if (lv[q] < -ev[q]) {
             if (b < 0 || lv[q] < lv[b]) b = q;
         } else if (!(lv[q] > ev[q])) {
-            return -1;
+            return kWalkUndecided;
         }
     }
-    if (b >= 0) {
-        next = nv[b];
-        return 0;
-    }
-    next = -1 - (a == 2 ? 0 : a + 1);
-    return 0;
+    if (b >= 0) return nv[b];
+    return -1 - (a == 2 ? 0 : a + 1);
 }
 
 // The walk test in the affine barycentric form relative to vertex 0, with a certified error
@@ -336,7 +353,12 @@ __device__ __forceinline__ int walk_test_fast(const DevMesh& M, int e, float px,
     if (!(lm < -Ea)) return -1;
     next = a == 0 ? N.y : (a == 1 ? N.z : N.x);
     if (next >= 0) return 0;
-    if (kWalls) return fast_wall_exit(l0, l1, l2, E0, E1, E2, N, a, next);
+    if (kWalls) {
+        const int c = fast_wall_exit(l0, l1, l2, E0, E1, E2, N, a);
+        if (c == kWalkUndecided) return -1;
+        next = c;
+        return 0;
+    }
     next = -1 - (a == 2 ? 0 : a + 1);   // a wall: -1 - (the exit edge)
     return 0;
 }

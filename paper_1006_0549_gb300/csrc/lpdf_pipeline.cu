@@ -110,8 +110,9 @@ static __device__ __noinline__ int walk_mirroring(const DevMesh& M, float lid_u,
         }
         int r = walk_test_fast<true>(M, e, px, py, next);
         if (r < 0) {
-            float lam[3];
-            r = walk_test(M, e, px, py, lam, next) ? 1 : 0;
+            const int c = walk_test_code(M, e, px, py);
+            r = c == kWalkIn ? 1 : 0;
+            if (!r) next = c;
         }
         if (r == 1) return e;
     }
@@ -135,8 +136,9 @@ __device__ __forceinline__ void advance_store(const DevMesh& M, const DevState& 
         int next = -1;
         int r = walk_test_fast<kKind == 2>(M, e, p.x, p.y, next);
         if (r < 0) {
-            float lam[3];
-            r = walk_test(M, e, p.x, p.y, lam, next) ? 1 : 0;
+            const int c = walk_test_code(M, e, p.x, p.y);
+            r = c == kWalkIn ? 1 : 0;
+            if (!r) next = c;
         }
         if (r == 1) {
             ne = e;
@@ -144,7 +146,17 @@ __device__ __forceinline__ void advance_store(const DevMesh& M, const DevState& 
             break;
         }
         if (kKind == 2 && next < 0 && M.edge_walls) {
-            ne = walk_mirroring(M, P.lid_u, e, next, h, p.x, p.y, p.u, p.v, p.w);
+            // the mirroring walk writes through references: it gets copies, so that the state
+            // itself never has its address taken and stays in registers on the common path
+            float mx = p.x, my = p.y, mu = p.u, mv = p.v, mw = p.w;
+            int mh = h;
+            ne = walk_mirroring(M, P.lid_u, e, next, mh, mx, my, mu, mv, mw);
+            p.x = mx;
+            p.y = my;
+            p.u = mu;
+            p.v = mv;
+            p.w = mw;
+            h = mh;
             lost = ne < 0;
             hops += h;
             break;
