@@ -106,6 +106,24 @@ __device__ __forceinline__ int block_scan(int v, int* wsum, int& total)
     return off + incl - v;
 }
 
+// The exact walk test with its weights returned by value (a small struct travels through the
+// call's parameter space): the walk's own variables never have their address taken, so they are
+// not given a home in local memory.
+struct WalkLam {
+    int code;   // kWalkIn, or the exit as walk_test's `next`
+    float l0, l1, l2;
+};
+static __device__ __noinline__ WalkLam walk_test_lam(const DevMesh& M, int e, float px, float py)
+{
+    float lam[3] = {0.0f, 0.0f, 0.0f};
+    WalkLam r;
+    r.code = walk_decide(M, e, px, py, lam);
+    r.l0 = lam[0];
+    r.l1 = lam[1];
+    r.l2 = lam[2];
+    return r;
+}
+
 __device__ __forceinline__ unsigned hash_slot(int key) { return ((unsigned)key * 2654435761u) >> 24; }   // 8 bits
 static_assert(kHash == 256, "hash_slot gives 8 bits");
 
@@ -350,13 +368,17 @@ pdf_step_kernel(const __grid_constant__ DevMesh M, const __grid_constant__ DevSt
             start(B);
 #pragma unroll 1
             while (A.j >= 0 || B.j >= 0) {
-                float la[3], lb[3];
-                int na = -1, nb = -1;
-                bool fa = false, fb = false;
-                if (A.j >= 0) fa = walk_test(M, A.e, A.px, A.py, la, na);
-                if (B.j >= 0) fb = walk_test(M, B.e, B.px, B.py, lb, nb);
-                if (A.j >= 0) step(A, fa, na, la);
-                if (B.j >= 0) step(B, fb, nb, lb);
+                WalkLam ra = {kWalkIn, 0.0f, 0.0f, 0.0f}, rb = ra;
+                if (A.j >= 0) ra = walk_test_lam(M, A.e, A.px, A.py);
+                if (B.j >= 0) rb = walk_test_lam(M, B.e, B.px, B.py);
+                if (A.j >= 0) {
+                    float la[3] = {ra.l0, ra.l1, ra.l2};
+                    step(A, ra.code == kWalkIn, ra.code == kWalkIn ? -1 : ra.code, la);
+                }
+                if (B.j >= 0) {
+                    float lb[3] = {rb.l0, rb.l1, rb.l2};
+                    step(B, rb.code == kWalkIn, rb.code == kWalkIn ? -1 : rb.code, lb);
+                }
             }
         }
         // ---- 3a. insert the new elements into the bin hash (one insert per distinct key of a row)
